@@ -1,0 +1,307 @@
+"""Benchmark of the axion-coupled Yee step on GB300.
+
+Workload: the 2D weak-pulse conversion run -- 4096 x 2048 cells, dx = dy =
+lambda/32, CFL 0.95, Gaussian E_z pulse a0 = 0.01 (waist 4 lambda, FWHM 8
+lambda/c), B_ext along z, g = 1e-4, massless axion, PML on every edge (20
+cells, sigma_max dt = 0.2).  One bench step = one full time step of every
+coupled field on the whole grid.  Metric: cell-updates/s (one cell advanced
+one full step with all fields).  Inputs: synthetic (analytic pulse), all
+arrays far larger than L2.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|fp32]
+  python bench.py --impl reference ...   (the CPU oracle on the host cores)
+
+Multi-GPU: every rank runs its own replica of the workload (replicas only,
+weak scaling, no data-path collective); value = all ranks' cell-updates / max
+rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NX, NY = 4096, 2048
+METRIC = "cell-updates/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="axp", choices=["axp", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--nx", type=int, default=NX)
+    ap.add_argument("--ny", type=int, default=NY)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload(args, precision):
+    from paper_2406_16796_gb300 import workloads as W
+
+    w = W.pulse_2d(nx=args.nx, ny=args.ny, precision=precision)
+    return w
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.QUERY, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing
+# ---------------------------------------------------------------------------
+
+def oracle_rate(w, steps, rows=None):
+    """cell-updates/s of the CPU oracle on the workload (optionally a strip of `rows` rows)."""
+    import oracle
+
+    grid = w.grid
+    if rows is not None and rows < grid.n[1]:
+        grid = grid.replace(n=(grid.n[0], rows, 1))
+    og = oracle.OracleGrid(grid)
+    for L in w.lasers:
+        og.inject_laser(L)
+    t0 = time.perf_counter()
+    og.step(steps)
+    dt = time.perf_counter() - t0
+    return grid.cells * steps / dt, dt, grid
+
+
+def omp_threads():
+    v = os.environ.get("OMP_NUM_THREADS")
+    return int(v) if v else (os.cpu_count() or 1)
+
+
+def reference_arm(args):
+    rank, world, local = dist_env()
+    from paper_2406_16796_gb300 import workloads as W
+
+    w = workload(args, "fp64")
+    if rank != 0:
+        return 0
+    # each step: one oracle step on a 16-row strip of the 4096-wide grid (same
+    # boundaries and pulse), so the whole run stays within a few minutes
+    rows = 16
+    import oracle
+
+    grid = w.grid.replace(n=(w.grid.n[0], rows, 1))
+    og = oracle.OracleGrid(grid)
+    for L in w.lasers:
+        og.inject_laser(L)
+    og.step(args.warmup)
+    t0 = time.perf_counter()
+    og.step(args.steps)
+    el = time.perf_counter() - t0
+    value = grid.cells * args.steps / el
+    sample = "%d oracle steps of a %dx%d strip of the %dx%d grid" % (args.steps, grid.n[0], rows, w.grid.n[0],
+                                                                      w.grid.n[1])
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "cells": w.grid.cells, "precision": "fp64", "parallelism": "replicas"},
+            "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": omp_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def algorithmic_bytes_per_cell(grid_spec, active_arrays, phi_words):
+    """Each active array read once and written once; phi: phi_words reads/writes."""
+    e = 8 if grid_spec.precision == "fp64" else 4
+    return (2 * active_arrays + phi_words) * e
+
+
+def gpu_arm(args):
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    from paper_2406_16796_gb300 import axp
+
+    prec = args.precision
+    w = workload(args, prec)
+    g = axp.Grid(w.grid)
+    for L in w.lasers:
+        g.inject_laser(L)
+    stream = g.stream
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+
+    # warm-up
+    g.step(args.warmup)
+    g.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    l0 = g.launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    g.step(args.steps)
+    ev1.record(stream)
+    ev1.synchronize()
+    launches = g.launches() - l0
+    el = ev0.elapsed_time(ev1) / 1e3
+    barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([el], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        el = float(t.item())
+    cells = w.grid.cells
+    value = cells * args.steps * world / el
+    ms = el / args.steps * 1e3
+
+    # algorithmic bytes: 2D TM pulse -> E0z, B0x, B0y + six order-1 arrays + axion
+    active = 9
+    phi_words = 3 if prec == "fp64" else 4
+    bpc = algorithmic_bytes_per_cell(w.grid, active, phi_words)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    achieved = bpc * cells * args.steps / el / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                "traffic": None, "peak_source": peak_src, "kernel": "whole step",
+                "algorithmic_bytes_per_cell": bpc}
+
+    # e2e through the C ABI with pinned host buffers: upload the state, run the
+    # steps reading the diagnostics record back after each, download the state
+    e2e = None
+    if not args.no_e2e:
+        nbytes = axp.axp_state_bytes(g.h)
+        host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+        axp.axp_save_state(g.h, host.data_ptr(), nbytes)
+        k = max(1, min(args.steps, 50))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        axp.axp_load_state(g.h, host.data_ptr(), nbytes)
+        for _ in range(k):
+            g.step(1)
+            g.diagnostics()
+        axp.axp_save_state(g.h, host.data_ptr(), nbytes)
+        t1 = time.perf_counter()
+        diag_bytes = 88
+        e2e = {"value": cells * k / (t1 - t0), "unit": "cell-updates/s", "h2d_bytes_per_step": nbytes / k,
+               "d2h_bytes_per_step": nbytes / k + diag_bytes, "steps": k}
+    g.close()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        wb = workload(args, "fp64")
+        rate, sec, gsp = oracle_rate(wb, steps=2)
+        cpu = {"value": rate, "unit": "cell-updates/s", "cores": omp_threads(), "kind": "oracle",
+               "sample": "2 oracle steps of the full %dx%d grid (%.1f s)" % (gsp.n[0], gsp.n[1], sec)}
+    line = {"metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32", "data": "synthetic",
+            "config": {"workload": w.name, "cells": cells, "precision": prec, "parallelism": "replicas",
+                       "l2": "inputs larger than L2"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return gpu_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

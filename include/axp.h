@@ -1,0 +1,237 @@
+/*
+ * axp.h -- C ABI of the GB300 axion-coupled Yee field solver.
+ *
+ * Method: arXiv 2406.16796, "Modeling of axion and electromagnetic fields
+ * coupling in a particle-in-cell code", Sec. 2 (Simulation Methods).  One
+ * call of axp_step advances, per time step n -> n+1:
+ *   - the zeroth-order (laser) fields E0, B0 and the first-order perturbation
+ *     fields E1, B1 by the half-step Yee leapfrog of Sec. 2.3 (Eq. update_E,
+ *     the B half-steps and the second E half-step);
+ *   - the axion field phi by the leapfrog of Eq. update_axion, driven by
+ *     S = g E0 . B0 averaged to cell centres (Sec. 2.3);
+ *   - the axion current g[(D_t phi) B0 - E0 x grad phi] of Eq. update_E, which
+ *     drives E1 (field perturbation separation, Sec. 2.2);
+ *   - the axion boundary conditions of Sec. 2.4: periodic, reflect, outflow
+ *     and PML; E and B use periodic wrap, a zero-field closure, or an
+ *     absorbing layer with the PML's cubic profile.
+ * Units: natural units hbar = c = eps0 = 1 (Sec. 2.1), any length unit.
+ *
+ * Memory: the caller owns all device memory.  axp_workspace_bytes() says how
+ * much one grid needs; the caller allocates it (e.g. a torch uint8 tensor)
+ * and passes the pointer to axp_create_grid().  The library allocates no
+ * device memory of its own.  Host-side handles are small and freed by
+ * axp_destroy_grid().
+ *
+ * Layout in the workspace (each array 256-byte aligned, x fastest, element
+ * (i,j,k) at i + n0*(j + n1*k)): E0x E0y E0z B0x B0y B0z E1x E1y E1z B1x
+ * B1y B1z, then the axion arrays, the axion current J, outflow ghost planes,
+ * diagnostic scratch and the diagnostic ring.  With cell centres at
+ * lo + (i+1/2, j+1/2, k+1/2) d:  phi at the centre, E_a at centre + d_a/2,
+ * B_a at centre + (d - d_a)/2 (Yee staggering, Sec. 2.3 and Fig. 1).
+ * Time levels: E, B at integer n; phi at n+1/2 and n-1/2 (Sec. 2.3).
+ *
+ * Precision: AXP_FP64 stores and computes everything in double.
+ * AXP_FP32_SPLIT stores all arrays in float, keeps E0/B0 and E1/B1 apart as
+ * the paper's FPS method does (Sec. 2.2), holds phi as phi^{n+1/2} plus the
+ * increment phi^{n+1/2} - phi^{n-1/2}, takes the uniform background fields as
+ * double constants, and accumulates every diagnostic in double.
+ *
+ * Errors: every call returns an axp_status; nothing is thrown across the
+ * ABI.  Kernel launch errors are returned by the call that launched;
+ * asynchronous device errors are returned by the next synchronising call on
+ * the handle (axp_read_diagnostics, axp_read_field, axp_synchronize, ...).
+ * A handle is not thread-safe; distinct handles are independent.  All work of
+ * a handle runs on the stream given at creation, in call order.
+ */
+#ifndef AXP_H
+#define AXP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    AXP_OK = 0,
+    AXP_E_INVAL = 1,     /* bad argument, size or combination of options */
+    AXP_E_UNSTABLE = 2,  /* dt violates the Yee CFL or the axion leapfrog bound */
+    AXP_E_NOMEM = 3,     /* workspace too small / admission refused for lack of memory */
+    AXP_E_CUDA = 4,      /* a CUDA call failed; the handle should be destroyed */
+    AXP_E_TIMEOUT = 5,   /* a bounded device wait expired */
+    AXP_E_NONFINITE = 6, /* a diagnostic came out NaN or Inf */
+    AXP_E_STATE = 7      /* call not valid in the handle's present state */
+} axp_status;
+
+typedef enum { AXP_FP64 = 0, AXP_FP32_SPLIT = 1 } axp_precision;
+
+/* Boundary kinds.  Axion: all four (Sec. 2.4).  E/B: AXP_BC_PERIODIC,
+ * AXP_BC_PML (absorbing layer) or AXP_BC_REFLECT (fields are zero outside the
+ * grid).  Periodic must be set on both sides of an axis for both E/B and the
+ * axion; an axis with n = 1 must be periodic. */
+typedef enum { AXP_BC_PERIODIC = 0, AXP_BC_REFLECT = 1, AXP_BC_OUTFLOW = 2, AXP_BC_PML = 3 } axp_bc;
+
+typedef struct {
+    int64_t n[3];             /* cells per axis, >= 1 */
+    double d[3];              /* cell sizes, > 0 */
+    double lo[3];             /* position of the grid's low faces */
+    double dt;                /* time step */
+    double m;                 /* axion mass (natural units) */
+    double g;                 /* axion-photon coupling g_agg */
+    int32_t axion_bc[3][2];   /* [axis][0 = low side, 1 = high side] */
+    int32_t em_bc[3][2];
+    int32_t pml_cells;        /* absorbing layer thickness N (Sec. 3.1 uses 20) */
+    int32_t precision;        /* axp_precision */
+    double pml_sigma_max_dt;  /* sigma_max * dt (Sec. 3.1 uses 0.2) */
+    int32_t diag_every;       /* axp_step records diagnostics every K steps (0 = never) */
+    int32_t diag_capacity;    /* diagnostic ring entries (>= 1 when diag_every > 0) */
+} axp_grid_desc;
+
+/* Laser (order-0 field) initial placement at integer time 0.  E = A pol env
+ * cos(k.(x - centre) + phase) at the E locations; B is the discrete curl of
+ * pol F, F = (A/cos(theta/2)) env sin(...)/|K|, K_d = (2/d_d) sin(k_d d_d/2),
+ * sin(theta/2) = dt |K|/2, so a CW wave commensurate with a periodic box is an
+ * exact eigenmode of the scheme and B is divergence-free.  env is
+ * exp(-r_perp^2/waist^2) exp(-xi^2/L^2) with xi = khat.(x - centre) and
+ * L = duration/sqrt(2 ln 2) (duration = intensity FWHM); waist = 0 or
+ * duration = 0 drops that factor.  Fields are added to E0, B0. */
+typedef struct {
+    double amplitude;
+    double k[3];
+    double pol[3];
+    double centre[3];
+    double waist;
+    double duration;
+    double phase;
+} axp_laser_desc;
+
+/* Axion field at t = +dt/2 and t = -dt/2 (Sec. 3.1 sets its test pulse at two
+ * time levels): phi = A env(xi - speed t) sin(k.(x - centre) - w t + phase),
+ * with w from the discrete Klein-Gordon dispersion cos(w dt) =
+ * 1 - dt^2 (K^2 + m^2)/2.  env as for the laser with the longitudinal 1/e
+ * half-length `length`.  Added to phi; outflow ghosts receive the same
+ * profile at the ghost centres. */
+typedef struct {
+    double amplitude;
+    double k[3];
+    double centre[3];
+    double waist;
+    double length;
+    double speed;
+    double phase;
+} axp_axion_desc;
+
+/* Diagnostics at an integer time (Sec. 3.2-3.4), accumulated in double over
+ * the cells outside absorbing layers:
+ *   H_phi = sum (1/2)[(D_t phi)^2 + |grad phi|^2 + m^2 phi^2] dV  (forward
+ *           differences of phi^n, D_t phi^n = (phi^{n+1/2} - phi^{n-1/2})/dt)
+ *   H_g0  = sum (1/2)(E0^2 + B0^2) dV (laser part, background excluded)
+ *   H_g1  = sum (1/2)(E1^2 + B1^2) dV
+ *   P_g2a = H_phi / H_g0,  P_a2g = H_g1 / H_phi   (0 when the divisor is 0)
+ *   W     = H_phi + sum (E0.E1 + B0.B1) dV with the background included
+ *   sum_xB1z2 / sum_B1z2 = laser centroid along x of Sec. 3.4
+ *   gauss_l2 = sum R^2 dV, R = div E1 + g Bbar0 . grad_c phi^n (Sec. 2.2). */
+typedef struct {
+    int64_t step;
+    double t;
+    double H_phi, H_g0, H_g1;
+    double P_g2a, P_a2g;
+    double W;
+    double sum_xB1z2, sum_B1z2;
+    double gauss_l2;
+} axp_diag;
+
+/* Field identifiers for read/write.  Values are transferred as double. */
+typedef enum {
+    AXP_E0X = 0, AXP_E0Y, AXP_E0Z, AXP_B0X, AXP_B0Y, AXP_B0Z,
+    AXP_E1X, AXP_E1Y, AXP_E1Z, AXP_B1X, AXP_B1Y, AXP_B1Z,
+    AXP_PHI_CUR = 12, /* phi^{n+1/2} */
+    AXP_PHI_OLD = 13  /* phi^{n-1/2} */
+} axp_field;
+
+typedef struct axp_grid axp_grid;
+
+/* Human-readable name of a status code.  Never NULL. */
+const char *axp_status_str(axp_status s);
+
+/* Bytes of device workspace a grid with this descriptor needs.  Validates the
+ * descriptor: AXP_E_INVAL for bad sizes/boundaries, AXP_E_UNSTABLE when dt
+ * exceeds the Yee bound dt <= 1/sqrt(sum_a 1/d_a^2) (over axes with n > 1) or
+ * the axion bound dt^2 (sum_a 4/d_a^2 + m^2) <= 4. */
+axp_status axp_workspace_bytes(const axp_grid_desc *desc, size_t *bytes);
+
+/* Create a grid in caller-owned device memory `dev_workspace` (at least
+ * axp_workspace_bytes, 256-byte aligned) on the current CUDA device.
+ * `cuda_stream` is a cudaStream_t (NULL = legacy default stream).  Fields
+ * start at zero.  *out receives the handle (host memory owned by the
+ * library, released by axp_destroy_grid; the workspace stays the caller's). */
+axp_status axp_create_grid(const axp_grid_desc *desc, void *dev_workspace, size_t bytes, void *cuda_stream,
+                           axp_grid **out);
+axp_status axp_destroy_grid(axp_grid *grid);
+
+/* Uniform static background fields (Sec. 2.2 FPS: part of the order-0
+ * field, stored as constants, never in the arrays).  Either pointer may be
+ * NULL to leave that field unchanged. */
+axp_status axp_set_background_field(axp_grid *grid, const double B_ext[3], const double E_ext[3]);
+
+axp_status axp_inject_laser(axp_grid *grid, const axp_laser_desc *laser);
+axp_status axp_inject_axion(axp_grid *grid, const axp_axion_desc *axion);
+
+/* Advance nsteps >= 0 time steps, asynchronously on the grid's stream.  When
+ * diag_every > 0, a diagnostic record is appended to the device ring after
+ * every step whose new index is a multiple of diag_every (the oldest record
+ * is overwritten when the ring is full). */
+axp_status axp_step(axp_grid *grid, int64_t nsteps);
+
+/* Copy up to `max` unread ring records (oldest first) to host `out`; *n gets
+ * the count.  Synchronises the stream.  AXP_E_NONFINITE if any copied record
+ * holds NaN/Inf. */
+axp_status axp_read_diagnostics(axp_grid *grid, axp_diag *out, int64_t max, int64_t *n);
+
+/* Diagnostics of the present state, computed now.  Synchronises. */
+axp_status axp_compute_diagnostics(axp_grid *grid, axp_diag *out);
+
+/* Copy one field to/from host memory as n0*n1*n2 doubles (bytes must equal
+ * 8 * cells).  Synchronises.  Writing marks the cached axion current stale. */
+axp_status axp_read_field(axp_grid *grid, int32_t which, double *host_dst, size_t bytes);
+axp_status axp_write_field(axp_grid *grid, int32_t which, const double *host_src, size_t bytes);
+
+/* Outflow ghost planes of axis `axis`, side `side` (level 0 = phi^{n+1/2},
+ * 1 = phi^{n-1/2}) as doubles; plane index: axis 0 -> j + n1 k,
+ * axis 1 -> i + n0 k, axis 2 -> i + n0 j.  AXP_E_INVAL unless that face is
+ * an outflow face. */
+axp_status axp_read_ghost(axp_grid *grid, int32_t axis, int32_t side, int32_t level, double *host_dst,
+                          size_t bytes);
+axp_status axp_write_ghost(axp_grid *grid, int32_t axis, int32_t side, int32_t level, const double *host_src,
+                           size_t bytes);
+
+/* Complete checkpoint: all arrays, ghosts, step count and background, as an
+ * opaque byte image of axp_state_bytes() bytes.  Loading into a grid of the
+ * same descriptor resumes bit for bit.  Both synchronise. */
+axp_status axp_state_bytes(const axp_grid *grid, size_t *bytes);
+axp_status axp_save_state(axp_grid *grid, void *host_dst, size_t bytes);
+axp_status axp_load_state(axp_grid *grid, const void *host_src, size_t bytes);
+
+/* Current step index n, and a wait for all queued work of the handle. */
+axp_status axp_get_step(const axp_grid *grid, int64_t *step);
+axp_status axp_synchronize(axp_grid *grid);
+
+/* Kernel selection for axp_step.  AXP_KERNEL_AUTO (default) uses the fused
+ * single-pass kernel where one exists for the grid's shape, boundaries and
+ * active field components, else the general multi-pass kernels.
+ * AXP_KERNEL_GENERAL forces the general kernels (one pass per stage of the
+ * time scheme, in the oracle's operation order). */
+typedef enum { AXP_KERNEL_AUTO = 0, AXP_KERNEL_GENERAL = 1, AXP_KERNEL_FUSED = 2 } axp_kernel;
+axp_status axp_set_kernel(axp_grid *grid, int32_t kernel);
+/* Which path the next axp_step will take (AXP_KERNEL_GENERAL or _FUSED). */
+axp_status axp_get_kernel_path(axp_grid *grid, int32_t *path);
+
+/* Number of kernel launches issued by this handle since creation (for
+ * launch accounting in benchmarks). */
+axp_status axp_get_launch_count(const axp_grid *grid, int64_t *count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AXP_H */

@@ -1,0 +1,357 @@
+"""Python binding of the C ABI in include/axp.h (argument marshalling only).
+
+Every function of the header is exposed under the same name; all compute
+runs in libaxp.so's CUDA kernels.  PyTorch supplies device memory (the grid
+workspace is a torch uint8 tensor) and the CUDA stream.  There is no CPU
+fallback: importing this module on a machine where libaxp.so cannot be
+loaded raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import _build
+from .workloads import BC_CODE, AxionSpec, GridSpec, LaserSpec
+
+AXP_OK, AXP_E_INVAL, AXP_E_UNSTABLE, AXP_E_NOMEM, AXP_E_CUDA, AXP_E_TIMEOUT, AXP_E_NONFINITE, AXP_E_STATE = range(8)
+AXP_FP64, AXP_FP32_SPLIT = 0, 1
+AXP_KERNEL_AUTO, AXP_KERNEL_GENERAL, AXP_KERNEL_FUSED = 0, 1, 2
+FIELD_IDS = {n: i for i, n in enumerate(("E0x", "E0y", "E0z", "B0x", "B0y", "B0z",
+                                          "E1x", "E1y", "E1z", "B1x", "B1y", "B1z"))}
+FIELD_IDS["phi_cur"] = 12
+FIELD_IDS["phi_old"] = 13
+
+
+class AxpError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__("%s: %s (status %d)" % (where, axp_status_str(status), status))
+
+
+class axp_grid_desc(C.Structure):
+    _fields_ = [("n", C.c_int64 * 3), ("d", C.c_double * 3), ("lo", C.c_double * 3), ("dt", C.c_double),
+                ("m", C.c_double), ("g", C.c_double), ("axion_bc", (C.c_int32 * 2) * 3),
+                ("em_bc", (C.c_int32 * 2) * 3), ("pml_cells", C.c_int32), ("precision", C.c_int32),
+                ("pml_sigma_max_dt", C.c_double), ("diag_every", C.c_int32), ("diag_capacity", C.c_int32)]
+
+
+class axp_laser_desc(C.Structure):
+    _fields_ = [("amplitude", C.c_double), ("k", C.c_double * 3), ("pol", C.c_double * 3),
+                ("centre", C.c_double * 3), ("waist", C.c_double), ("duration", C.c_double),
+                ("phase", C.c_double)]
+
+
+class axp_axion_desc(C.Structure):
+    _fields_ = [("amplitude", C.c_double), ("k", C.c_double * 3), ("centre", C.c_double * 3),
+                ("waist", C.c_double), ("length", C.c_double), ("speed", C.c_double), ("phase", C.c_double)]
+
+
+class axp_diag(C.Structure):
+    _fields_ = [("step", C.c_int64)] + [(n, C.c_double) for n in (
+        "t", "H_phi", "H_g0", "H_g1", "P_g2a", "P_a2g", "W", "sum_xB1z2", "sum_B1z2", "gauss_l2")]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+_lib = None
+_P = C.c_void_p
+_D3 = C.c_double * 3
+
+
+def lib():
+    """Load libaxp.so (building it first if the sources are newer)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not _build.up_to_date():
+            path = _build.build()
+        L = C.CDLL(path)
+        sig = {
+            "axp_status_str": ([C.c_int], C.c_char_p),
+            "axp_workspace_bytes": ([C.POINTER(axp_grid_desc), C.POINTER(C.c_size_t)], C.c_int),
+            "axp_create_grid": ([C.POINTER(axp_grid_desc), _P, C.c_size_t, _P, C.POINTER(_P)], C.c_int),
+            "axp_destroy_grid": ([_P], C.c_int),
+            "axp_set_background_field": ([_P, C.POINTER(C.c_double), C.POINTER(C.c_double)], C.c_int),
+            "axp_inject_laser": ([_P, C.POINTER(axp_laser_desc)], C.c_int),
+            "axp_inject_axion": ([_P, C.POINTER(axp_axion_desc)], C.c_int),
+            "axp_step": ([_P, C.c_int64], C.c_int),
+            "axp_read_diagnostics": ([_P, C.POINTER(axp_diag), C.c_int64, C.POINTER(C.c_int64)], C.c_int),
+            "axp_compute_diagnostics": ([_P, C.POINTER(axp_diag)], C.c_int),
+            "axp_read_field": ([_P, C.c_int32, C.POINTER(C.c_double), C.c_size_t], C.c_int),
+            "axp_write_field": ([_P, C.c_int32, C.POINTER(C.c_double), C.c_size_t], C.c_int),
+            "axp_read_ghost": ([_P, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_double), C.c_size_t], C.c_int),
+            "axp_write_ghost": ([_P, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_double), C.c_size_t], C.c_int),
+            "axp_state_bytes": ([_P, C.POINTER(C.c_size_t)], C.c_int),
+            "axp_save_state": ([_P, _P, C.c_size_t], C.c_int),
+            "axp_load_state": ([_P, _P, C.c_size_t], C.c_int),
+            "axp_get_step": ([_P, C.POINTER(C.c_int64)], C.c_int),
+            "axp_synchronize": ([_P], C.c_int),
+            "axp_set_kernel": ([_P, C.c_int32], C.c_int),
+            "axp_get_kernel_path": ([_P, C.POINTER(C.c_int32)], C.c_int),
+            "axp_get_launch_count": ([_P, C.POINTER(C.c_int64)], C.c_int),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    """Names of the functions declared in include/axp.h."""
+    hdr = open(os.path.join(_build.INCLUDE, "axp.h")).read()
+    import re
+
+    return sorted(set(re.findall(r"\b(axp_[a-z_]+)\s*\(", hdr)))
+
+
+def _check(st, where):
+    if st != AXP_OK:
+        raise AxpError(st, where)
+
+
+# ---- same-name wrappers (marshalling only) ----
+
+def axp_status_str(st):
+    return lib().axp_status_str(int(st)).decode()
+
+
+def axp_workspace_bytes(desc):
+    n = C.c_size_t()
+    _check(lib().axp_workspace_bytes(C.byref(desc), C.byref(n)), "axp_workspace_bytes")
+    return n.value
+
+
+def axp_create_grid(desc, dev_ptr, nbytes, stream_ptr):
+    h = _P()
+    _check(lib().axp_create_grid(C.byref(desc), _P(dev_ptr), nbytes, _P(stream_ptr), C.byref(h)), "axp_create_grid")
+    return h
+
+
+def axp_destroy_grid(h):
+    _check(lib().axp_destroy_grid(h), "axp_destroy_grid")
+
+
+def axp_set_background_field(h, B_ext=None, E_ext=None):
+    b = _D3(*B_ext) if B_ext is not None else None
+    e = _D3(*E_ext) if E_ext is not None else None
+    _check(lib().axp_set_background_field(h, b, e), "axp_set_background_field")
+
+
+def axp_inject_laser(h, laser: axp_laser_desc):
+    _check(lib().axp_inject_laser(h, C.byref(laser)), "axp_inject_laser")
+
+
+def axp_inject_axion(h, ax: axp_axion_desc):
+    _check(lib().axp_inject_axion(h, C.byref(ax)), "axp_inject_axion")
+
+
+def axp_step(h, nsteps):
+    _check(lib().axp_step(h, int(nsteps)), "axp_step")
+
+
+def axp_read_diagnostics(h, max_records=4096):
+    buf = (axp_diag * max(1, max_records))()
+    n = C.c_int64()
+    _check(lib().axp_read_diagnostics(h, buf, int(max_records), C.byref(n)), "axp_read_diagnostics")
+    return [buf[i].as_dict() for i in range(n.value)]
+
+
+def axp_compute_diagnostics(h):
+    d = axp_diag()
+    _check(lib().axp_compute_diagnostics(h, C.byref(d)), "axp_compute_diagnostics")
+    return d.as_dict()
+
+
+def axp_read_field(h, which, ncells):
+    out = np.empty(ncells, dtype=np.float64)
+    _check(lib().axp_read_field(h, int(which), out.ctypes.data_as(C.POINTER(C.c_double)), out.nbytes),
+           "axp_read_field")
+    return out
+
+
+def axp_write_field(h, which, values):
+    a = np.ascontiguousarray(values, dtype=np.float64).ravel()
+    _check(lib().axp_write_field(h, int(which), a.ctypes.data_as(C.POINTER(C.c_double)), a.nbytes),
+           "axp_write_field")
+
+
+def axp_read_ghost(h, axis, side, level, nplane):
+    out = np.empty(nplane, dtype=np.float64)
+    _check(lib().axp_read_ghost(h, axis, side, level, out.ctypes.data_as(C.POINTER(C.c_double)), out.nbytes),
+           "axp_read_ghost")
+    return out
+
+
+def axp_write_ghost(h, axis, side, level, values):
+    a = np.ascontiguousarray(values, dtype=np.float64).ravel()
+    _check(lib().axp_write_ghost(h, axis, side, level, a.ctypes.data_as(C.POINTER(C.c_double)), a.nbytes),
+           "axp_write_ghost")
+
+
+def axp_state_bytes(h):
+    n = C.c_size_t()
+    _check(lib().axp_state_bytes(h, C.byref(n)), "axp_state_bytes")
+    return n.value
+
+
+def axp_save_state(h, host_ptr, nbytes):
+    _check(lib().axp_save_state(h, _P(host_ptr), nbytes), "axp_save_state")
+
+
+def axp_load_state(h, host_ptr, nbytes):
+    _check(lib().axp_load_state(h, _P(host_ptr), nbytes), "axp_load_state")
+
+
+def axp_get_step(h):
+    n = C.c_int64()
+    _check(lib().axp_get_step(h, C.byref(n)), "axp_get_step")
+    return n.value
+
+
+def axp_synchronize(h):
+    _check(lib().axp_synchronize(h), "axp_synchronize")
+
+
+def axp_set_kernel(h, k):
+    _check(lib().axp_set_kernel(h, int(k)), "axp_set_kernel")
+
+
+def axp_get_kernel_path(h):
+    p = C.c_int32()
+    _check(lib().axp_get_kernel_path(h, C.byref(p)), "axp_get_kernel_path")
+    return p.value
+
+
+def axp_get_launch_count(h):
+    n = C.c_int64()
+    _check(lib().axp_get_launch_count(h, C.byref(n)), "axp_get_launch_count")
+    return n.value
+
+
+# ---- descriptors from the workload specs ----
+
+def desc_of(grid: GridSpec, diag_every=0, diag_capacity=0) -> axp_grid_desc:
+    d = axp_grid_desc()
+    for a in range(3):
+        d.n[a] = int(grid.n[a])
+        d.d[a] = float(grid.d[a])
+        d.lo[a] = float(grid.lo[a])
+        for s in range(2):
+            d.axion_bc[a][s] = BC_CODE[grid.axion_bc[a][s]]
+            d.em_bc[a][s] = BC_CODE[grid.em_bc[a][s]]
+    d.dt, d.m, d.g = float(grid.dt), float(grid.m), float(grid.g)
+    d.pml_cells = int(grid.pml_cells)
+    d.precision = AXP_FP32_SPLIT if grid.precision == "fp32" else AXP_FP64
+    d.pml_sigma_max_dt = float(grid.pml_sigma_max_dt)
+    d.diag_every = int(diag_every)
+    d.diag_capacity = int(diag_capacity if diag_capacity else (1 if diag_every else 0))
+    return d
+
+
+def laser_of(L: LaserSpec) -> axp_laser_desc:
+    return axp_laser_desc(L.amplitude, _D3(*L.k), _D3(*L.pol), _D3(*L.centre), L.waist, L.duration, L.phase)
+
+
+def axion_of(A: AxionSpec) -> axp_axion_desc:
+    return axp_axion_desc(A.amplitude, _D3(*A.k), _D3(*A.centre), A.waist, A.length, A.speed, A.phase)
+
+
+class Grid:
+    """A grid whose workspace is a torch CUDA tensor; a thin owner of one handle."""
+
+    def __init__(self, grid: GridSpec, diag_every=0, diag_capacity=0, stream=None, device=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("axp needs a CUDA device; there is no CPU fallback")
+        self.spec = grid
+        self.desc = desc_of(grid, diag_every, diag_capacity)
+        self.nbytes = axp_workspace_bytes(self.desc)
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            self.workspace = torch.empty(self.nbytes, dtype=torch.uint8, device=self.device)
+            self.h = axp_create_grid(self.desc, self.workspace.data_ptr(), self.nbytes, self.stream.cuda_stream)
+        axp_set_background_field(self.h, grid.B_ext, grid.E_ext)
+        self.cells = grid.cells
+        self.shape = (grid.n[2], grid.n[1], grid.n[0])
+
+    def close(self):
+        if getattr(self, "h", None):
+            axp_destroy_grid(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def inject_laser(self, L: LaserSpec):
+        axp_inject_laser(self.h, laser_of(L))
+
+    def inject_axion(self, A: AxionSpec):
+        axp_inject_axion(self.h, axion_of(A))
+
+    def step(self, n=1):
+        axp_step(self.h, n)
+
+    def synchronize(self):
+        axp_synchronize(self.h)
+
+    def diagnostics(self):
+        return axp_compute_diagnostics(self.h)
+
+    def read_diagnostics(self, max_records=4096):
+        return axp_read_diagnostics(self.h, max_records)
+
+    def read(self, name):
+        return axp_read_field(self.h, FIELD_IDS[name], self.cells).reshape(self.shape)
+
+    def write(self, name, values):
+        axp_write_field(self.h, FIELD_IDS[name], values)
+
+    def load(self, state: dict):
+        for k, v in state.items():
+            self.write(k, v)
+
+    def fields(self):
+        return {k: self.read(k) for k in FIELD_IDS}
+
+    def plane(self, a):
+        nx, ny, nz = self.spec.n
+        return {0: ny * nz, 1: nx * nz, 2: nx * ny}[a]
+
+    def read_ghost(self, axis, side, level):
+        return axp_read_ghost(self.h, axis, side, level, self.plane(axis))
+
+    def write_ghost(self, axis, side, level, values):
+        axp_write_ghost(self.h, axis, side, level, values)
+
+    def set_kernel(self, k):
+        axp_set_kernel(self.h, k)
+
+    def kernel_path(self):
+        return axp_get_kernel_path(self.h)
+
+    def launches(self):
+        return axp_get_launch_count(self.h)
+
+    @property
+    def step_count(self):
+        return axp_get_step(self.h)
+
+    def save_state(self):
+        n = axp_state_bytes(self.h)
+        buf = np.empty(n, dtype=np.uint8)
+        axp_save_state(self.h, buf.ctypes.data, n)
+        return buf
+
+    def load_state(self, buf: np.ndarray):
+        axp_load_state(self.h, buf.ctypes.data, buf.nbytes)

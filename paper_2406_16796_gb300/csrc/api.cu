@@ -1,0 +1,708 @@
+// api.cu -- host side of the C ABI declared in include/axp.h.
+//
+// Validation, workspace layout in caller-owned device memory, handle state,
+// host<->device transfers and checkpointing.  No device memory is allocated
+// here: every array lives in the caller's workspace.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "axp_internal.h"
+
+using namespace axp;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr uint64_t kStateMagic = 0x31505841u;  // "AXP1"
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+int64_t cells(const axp_grid_desc &d) { return d.n[0] * d.n[1] * d.n[2]; }
+
+int64_t plane_size(const axp_grid_desc &d, int a)
+{
+    return a == 0 ? d.n[1] * d.n[2] : (a == 1 ? d.n[0] * d.n[2] : d.n[0] * d.n[1]);
+}
+
+axp_status validate(const axp_grid_desc *d)
+{
+    if (!d) return AXP_E_INVAL;
+    if (d->precision != AXP_FP64 && d->precision != AXP_FP32_SPLIT) return AXP_E_INVAL;
+    if (!(d->dt > 0) || !std::isfinite(d->dt) || !std::isfinite(d->m) || !std::isfinite(d->g)) return AXP_E_INVAL;
+    if (d->pml_cells < 0 || !(d->pml_sigma_max_dt >= 0)) return AXP_E_INVAL;
+    if (d->diag_every < 0 || (d->diag_every > 0 && d->diag_capacity < 1) || d->diag_capacity < 0) return AXP_E_INVAL;
+    double inv2 = 0.0;
+    for (int a = 0; a < 3; a++) {
+        if (d->n[a] < 1 || !(d->d[a] > 0) || !std::isfinite(d->lo[a])) return AXP_E_INVAL;
+        for (int s = 0; s < 2; s++) {
+            const int ab = d->axion_bc[a][s], eb = d->em_bc[a][s];
+            if (ab < AXP_BC_PERIODIC || ab > AXP_BC_PML) return AXP_E_INVAL;
+            if (eb != AXP_BC_PERIODIC && eb != AXP_BC_REFLECT && eb != AXP_BC_PML) return AXP_E_INVAL;
+            if ((ab == AXP_BC_PERIODIC) != (eb == AXP_BC_PERIODIC)) return AXP_E_INVAL;
+            if ((ab == AXP_BC_PML || eb == AXP_BC_PML) && d->pml_cells > d->n[a]) return AXP_E_INVAL;
+        }
+        if ((d->em_bc[a][0] == AXP_BC_PERIODIC) != (d->em_bc[a][1] == AXP_BC_PERIODIC)) return AXP_E_INVAL;
+        if (d->n[a] == 1 && d->em_bc[a][0] != AXP_BC_PERIODIC) return AXP_E_INVAL;
+        if (d->n[a] > 1) inv2 += 1.0 / (d->d[a] * d->d[a]);
+    }
+    if (cells(*d) > ((int64_t)1 << 40)) return AXP_E_INVAL;
+    if (inv2 > 0) {
+        // Yee: dt <= 1/sqrt(sum 1/d^2); axion leapfrog: dt^2 (sum 4/d^2 + m^2) <= 4
+        if (d->dt * std::sqrt(inv2) > 1.0) return AXP_E_UNSTABLE;
+        if (d->dt * d->dt * (4.0 * inv2 + d->m * d->m) > 4.0) return AXP_E_UNSTABLE;
+    } else if (d->dt * d->dt * d->m * d->m > 4.0) {
+        return AXP_E_UNSTABLE;
+    }
+    return AXP_OK;
+}
+
+template <typename T>
+void sigma_tables(const axp_grid_desc &d, bool axion, std::vector<T> out[3])
+{
+    const double smax = d.pml_sigma_max_dt / d.dt;
+    const int64_t N = d.pml_cells;
+    for (int a = 0; a < 3; a++) {
+        out[a].assign(d.n[a], T(0));
+        const int32_t *bc = axion ? d.axion_bc[a] : d.em_bc[a];
+        if (N <= 0) continue;
+        for (int64_t c = 0; c < d.n[a]; c++) {
+            double s = 0.0;
+            if (bc[0] == AXP_BC_PML && c < N) {
+                const double r = 1.0 - (double)c / (double)N;
+                s = r * r * r * smax;
+            }
+            if (bc[1] == AXP_BC_PML && c >= d.n[a] - N) {
+                const double r = 1.0 - (double)(d.n[a] - 1 - c) / (double)N;
+                const double v = r * r * r * smax;
+                if (v > s) s = v;
+            }
+            out[a][c] = (T)s;
+        }
+    }
+}
+
+axp_status cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess) return AXP_OK;
+    fprintf(stderr, "axp: CUDA error %s\n", cudaGetErrorString(e));
+    return AXP_E_CUDA;
+}
+
+bool finite_diag(const axp_diag &d)
+{
+    const double v[] = {d.t, d.H_phi, d.H_g0, d.H_g1, d.P_g2a, d.P_a2g, d.W, d.sum_xB1z2, d.sum_B1z2, d.gauss_l2};
+    for (double x : v)
+        if (!std::isfinite(x)) return false;
+    return true;
+}
+
+bool is_fp32(const axp_grid *g) { return g->desc.precision == AXP_FP32_SPLIT; }
+
+struct StateHeader {
+    uint64_t magic;
+    uint64_t bytes;
+    axp_grid_desc desc;
+    double B_ext[3], E_ext[3];
+    int64_t step;
+    int32_t J_valid;
+    uint32_t active;
+    int32_t phi_active;
+    int32_t pad;
+};
+
+}  // namespace
+
+namespace axp {
+
+size_t elem_size(const axp_grid_desc &d) { return d.precision == AXP_FP32_SPLIT ? 4 : 8; }
+
+bool compute_layout(const axp_grid_desc &d, Workspace *w)
+{
+    std::memset(w, 0, sizeof(*w));
+    const size_t e = elem_size(d);
+    const size_t arr = align_up((size_t)cells(d) * e);
+    size_t off = 0;
+    w->off_flag = off;
+    off += kAlign;
+    for (int set = 0; set < 2; set++)
+        for (int f = 0; f < kFields; f++) {
+            w->off_fields[set][f] = off;
+            off += arr;
+        }
+    const int nphi = d.precision == AXP_FP32_SPLIT ? 4 : 3;
+    for (int p = 0; p < 4; p++) {
+        if (p < nphi) {
+            w->off_phi[p] = off;
+            off += arr;
+        }
+    }
+    for (int a = 0; a < 3; a++) {
+        w->off_J[a] = off;
+        off += arr;
+    }
+    for (int a = 0; a < 3; a++)
+        for (int s = 0; s < 2; s++)
+            for (int l = 0; l < 3; l++) {
+                if (d.axion_bc[a][s] != AXP_BC_OUTFLOW) continue;
+                w->off_ghost[a][s][l] = off;
+                off += align_up((size_t)plane_size(d, a) * e);
+            }
+    for (int a = 0; a < 3; a++) {
+        w->off_sig_em[a] = off;
+        off += align_up((size_t)d.n[a] * e);
+        w->off_sig_ax[a] = off;
+        off += align_up((size_t)d.n[a] * e);
+    }
+    int64_t nb = (cells(d) + 255) / 256;
+    if (nb > 1024) nb = 1024;
+    if (nb < 1) nb = 1;
+    w->diag_blocks = (int)nb;
+    w->off_partials = off;
+    off += align_up((size_t)nb * 7 * sizeof(double));
+    w->off_ring = off;
+    off += align_up((size_t)(d.diag_capacity + 1) * sizeof(axp_diag));
+    w->total = off;
+    w->elem = e;
+    return true;
+}
+
+axp_diag *ring_slot(axp_grid *g, int64_t index)
+{
+    const int64_t cap = g->desc.diag_capacity > 0 ? g->desc.diag_capacity : 1;
+    return (axp_diag *)(g->ws + g->layout.off_ring) + (index % cap);
+}
+
+static axp_diag *scratch_slot(axp_grid *g)
+{
+    return (axp_diag *)(g->ws + g->layout.off_ring) + g->desc.diag_capacity;
+}
+
+template <typename T>
+View<T> make_view_eset(axp_grid *g, int eset)
+{
+    View<T> v;
+    std::memset(&v, 0, sizeof(v));
+    const axp_grid_desc &d = g->desc;
+    const Workspace &w = g->layout;
+    for (int f = 0; f < kFields; f++) {
+        const bool is_e = (f >= kE0 && f < kE0 + 3) || (f >= kE1 && f < kE1 + 3);
+        v.f[f] = (T *)(g->ws + w.off_fields[is_e ? eset : g->fset][f]);
+    }
+    v.phi_cur = (T *)(g->ws + w.off_phi[g->phi_cur_slot]);
+    v.phi_b = (T *)(g->ws + w.off_phi[g->phi_b_slot]);
+    v.phi_next = (T *)(g->ws + w.off_phi[g->phi_next_slot]);
+    for (int a = 0; a < 3; a++) {
+        v.J[a] = (T *)(g->ws + w.off_J[a]);
+        for (int s = 0; s < 2; s++)
+            for (int l = 0; l < 3; l++) {
+                const size_t off = w.off_ghost[a][s][g->ghost_level_slot[l]];
+                v.gh[a][s][l] = off ? (T *)(g->ws + off) : nullptr;
+            }
+        v.sig_em[a] = (const T *)(g->ws + w.off_sig_em[a]);
+        v.sig_ax[a] = (const T *)(g->ws + w.off_sig_ax[a]);
+        v.n[a] = d.n[a];
+        v.d[a] = (T)d.d[a];
+        v.lo[a] = (T)d.lo[a];
+        v.Bext[a] = (T)g->B_ext[a];
+        v.Eext[a] = (T)g->E_ext[a];
+        v.periodic[a] = d.em_bc[a][0] == AXP_BC_PERIODIC;
+        for (int s = 0; s < 2; s++) v.axbc[a][s] = d.axion_bc[a][s];
+        int rlo = 0, rhi = (int)d.n[a];
+        if (d.n[a] > 1 && !v.periodic[a]) {
+            if (d.em_bc[a][0] == AXP_BC_PML || d.axion_bc[a][0] == AXP_BC_PML) rlo = d.pml_cells;
+            if (d.em_bc[a][1] == AXP_BC_PML || d.axion_bc[a][1] == AXP_BC_PML) rhi = (int)d.n[a] - d.pml_cells;
+        }
+        v.region_lo[a] = rlo;
+        v.region_hi[a] = rhi;
+    }
+    v.N = cells(d);
+    v.dt = (T)d.dt;
+    v.h = (T)(d.dt / 2.0);
+    v.g = (T)d.g;
+    v.m2 = (T)(d.m * d.m);
+    return v;
+}
+
+template <typename T>
+View<T> make_view(axp_grid *g)
+{
+    return make_view_eset<T>(g, g->fset);
+}
+
+template View<double> make_view<double>(axp_grid *);
+template View<float> make_view<float>(axp_grid *);
+template View<double> make_view_eset<double>(axp_grid *, int);
+template View<float> make_view_eset<float>(axp_grid *, int);
+
+cudaError_t ensure_integer(axp_grid *g)
+{
+    if (!g->staggered) return cudaSuccess;
+    return g->desc.precision == AXP_FP32_SPLIT ? exit_staggered<float>(g, true) : exit_staggered<double>(g, true);
+}
+
+// Which order-0 components can become non-zero: the injected/written ones and
+// everything the discrete curls couple them to along the grid's active axes.
+uint32_t order0_closure(const axp_grid *g)
+{
+    uint32_t m = (g->active & 7u) | (((g->active >> kB0) & 7u) << 3);
+    bool ax[3];
+    for (int a = 0; a < 3; a++) ax[a] = g->desc.n[a] > 1;
+    for (int it = 0; it < 6; it++) {
+        uint32_t nm = m;
+        for (int a = 0; a < 3; a++) {
+            const int b = (a + 1) % 3, c = (a + 2) % 3;
+            // (curl E)_a = D_b E_c - D_c E_b feeds B_a; (curl B)_a likewise feeds E_a
+            if ((ax[b] && (m >> c & 1)) || (ax[c] && (m >> b & 1))) nm |= 1u << (3 + a);
+            if ((ax[b] && (m >> (3 + c) & 1)) || (ax[c] && (m >> (3 + b) & 1))) nm |= 1u << a;
+        }
+        m = nm;
+    }
+    return m;
+}
+
+}  // namespace axp
+
+extern "C" {
+
+const char *axp_status_str(axp_status s)
+{
+    switch (s) {
+    case AXP_OK: return "ok";
+    case AXP_E_INVAL: return "invalid argument";
+    case AXP_E_UNSTABLE: return "time step violates the stability bound";
+    case AXP_E_NOMEM: return "not enough memory";
+    case AXP_E_CUDA: return "CUDA error";
+    case AXP_E_TIMEOUT: return "bounded device wait expired";
+    case AXP_E_NONFINITE: return "non-finite diagnostic";
+    case AXP_E_STATE: return "call not valid in this state";
+    }
+    return "unknown status";
+}
+
+axp_status axp_workspace_bytes(const axp_grid_desc *desc, size_t *bytes)
+{
+    if (!bytes) return AXP_E_INVAL;
+    const axp_status st = validate(desc);
+    if (st != AXP_OK) return st;
+    Workspace w;
+    compute_layout(*desc, &w);
+    *bytes = w.total;
+    return AXP_OK;
+}
+
+axp_status axp_create_grid(const axp_grid_desc *desc, void *dev_workspace, size_t bytes, void *cuda_stream,
+                           axp_grid **out)
+{
+    if (!out || !dev_workspace) return AXP_E_INVAL;
+    *out = nullptr;
+    axp_status st = validate(desc);
+    if (st != AXP_OK) return st;
+    if ((uintptr_t)dev_workspace % kAlign) return AXP_E_INVAL;
+    Workspace w;
+    compute_layout(*desc, &w);
+    if (bytes < w.total) return AXP_E_NOMEM;
+    axp_grid *g = new (std::nothrow) axp_grid();
+    if (!g) return AXP_E_NOMEM;
+    g->desc = *desc;
+    g->stream = (cudaStream_t)cuda_stream;
+    if (cudaGetDevice(&g->device) != cudaSuccess) {
+        delete g;
+        return AXP_E_CUDA;
+    }
+    g->ws = (char *)dev_workspace;
+    g->ws_bytes = bytes;
+    g->layout = w;
+    g->phi_cur_slot = 0;
+    g->phi_b_slot = 1;
+    g->phi_next_slot = 2;
+    g->phi_next_b_slot = 3;
+    g->fset = 0;
+    g->staggered = false;
+    for (int l = 0; l < 3; l++) g->ghost_level_slot[l] = l;
+    g->J_valid = false;
+    g->kernel_choice = AXP_KERNEL_AUTO;
+    cudaError_t e = cudaMemsetAsync(g->ws, 0, w.total, g->stream);
+    if (e == cudaSuccess) {
+        // absorbing-layer profiles, computed once on the host
+        if (desc->precision == AXP_FP32_SPLIT) {
+            std::vector<float> em[3], ax[3];
+            sigma_tables<float>(*desc, false, em);
+            sigma_tables<float>(*desc, true, ax);
+            for (int a = 0; a < 3 && e == cudaSuccess; a++) {
+                e = cudaMemcpyAsync(g->ws + w.off_sig_em[a], em[a].data(), em[a].size() * 4, cudaMemcpyHostToDevice,
+                                    g->stream);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(g->ws + w.off_sig_ax[a], ax[a].data(), ax[a].size() * 4,
+                                        cudaMemcpyHostToDevice, g->stream);
+            }
+            if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+        } else {
+            std::vector<double> em[3], ax[3];
+            sigma_tables<double>(*desc, false, em);
+            sigma_tables<double>(*desc, true, ax);
+            for (int a = 0; a < 3 && e == cudaSuccess; a++) {
+                e = cudaMemcpyAsync(g->ws + w.off_sig_em[a], em[a].data(), em[a].size() * 8, cudaMemcpyHostToDevice,
+                                    g->stream);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(g->ws + w.off_sig_ax[a], ax[a].data(), ax[a].size() * 8,
+                                        cudaMemcpyHostToDevice, g->stream);
+            }
+            if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+        }
+    }
+    if (e != cudaSuccess) {
+        delete g;
+        return cuda_status(e);
+    }
+    *out = g;
+    return AXP_OK;
+}
+
+axp_status axp_destroy_grid(axp_grid *grid)
+{
+    if (!grid) return AXP_E_INVAL;
+    delete grid;
+    return AXP_OK;
+}
+
+axp_status axp_set_background_field(axp_grid *g, const double B_ext[3], const double E_ext[3])
+{
+    if (!g) return AXP_E_INVAL;
+    for (int a = 0; a < 3; a++) {
+        if (B_ext && !std::isfinite(B_ext[a])) return AXP_E_INVAL;
+        if (E_ext && !std::isfinite(E_ext[a])) return AXP_E_INVAL;
+    }
+    const cudaError_t e = ensure_integer(g);
+    if (e != cudaSuccess) return cuda_status(e);
+    for (int a = 0; a < 3; a++) {
+        if (B_ext) g->B_ext[a] = B_ext[a];
+        if (E_ext) g->E_ext[a] = E_ext[a];
+    }
+    g->J_valid = false;
+    return AXP_OK;
+}
+
+axp_status axp_inject_laser(axp_grid *g, const axp_laser_desc *L)
+{
+    if (!g || !L) return AXP_E_INVAL;
+    double kk = 0;
+    for (int a = 0; a < 3; a++) {
+        if (!std::isfinite(L->k[a]) || !std::isfinite(L->pol[a]) || !std::isfinite(L->centre[a])) return AXP_E_INVAL;
+        kk += L->k[a] * L->k[a];
+    }
+    if (!(kk > 0) || !std::isfinite(L->amplitude) || L->waist < 0 || L->duration < 0) return AXP_E_INVAL;
+    cudaError_t e = ensure_integer(g);
+    if (e == cudaSuccess) e = is_fp32(g) ? inject_laser<float>(g, *L) : inject_laser<double>(g, *L);
+    g->J_valid = false;
+    for (int a = 0; a < 3; a++) {
+        const int b = (a + 1) % 3, c = (a + 2) % 3;
+        if (L->pol[a] != 0) g->active |= 1u << (kE0 + a);
+        // B = curl(pol F): B_a = D_b F_c - D_c F_b along the grid's active axes
+        if ((g->desc.n[b] > 1 && L->pol[c] != 0) || (g->desc.n[c] > 1 && L->pol[b] != 0)) g->active |= 1u << (kB0 + a);
+    }
+    return cuda_status(e);
+}
+
+axp_status axp_inject_axion(axp_grid *g, const axp_axion_desc *A)
+{
+    if (!g || !A) return AXP_E_INVAL;
+    for (int a = 0; a < 3; a++)
+        if (!std::isfinite(A->k[a]) || !std::isfinite(A->centre[a])) return AXP_E_INVAL;
+    if (!std::isfinite(A->amplitude) || A->waist < 0 || A->length < 0) return AXP_E_INVAL;
+    cudaError_t e = ensure_integer(g);
+    if (e == cudaSuccess) e = is_fp32(g) ? inject_axion<float>(g, *A) : inject_axion<double>(g, *A);
+    g->J_valid = false;
+    g->phi_active = true;
+    return cuda_status(e);
+}
+
+axp_status axp_step(axp_grid *g, int64_t nsteps)
+{
+    if (!g || nsteps < 0) return AXP_E_INVAL;
+    if (nsteps == 0) return AXP_OK;
+    cudaError_t e;
+    bool handled = false;
+    if (g->kernel_choice != AXP_KERNEL_GENERAL) {
+        e = is_fp32(g) ? fused_step<float>(g, nsteps, &handled) : fused_step<double>(g, nsteps, &handled);
+        if (e != cudaSuccess) return cuda_status(e);
+        if (!handled && g->kernel_choice == AXP_KERNEL_FUSED) return AXP_E_STATE;
+    }
+    if (!handled) {
+        e = ensure_integer(g);
+        if (e == cudaSuccess) e = is_fp32(g) ? general_step<float>(g, nsteps) : general_step<double>(g, nsteps);
+    } else {
+        e = cudaSuccess;
+    }
+    return cuda_status(e);
+}
+
+axp_status axp_synchronize(axp_grid *g)
+{
+    if (!g) return AXP_E_INVAL;
+    return cuda_status(cudaStreamSynchronize(g->stream));
+}
+
+axp_status axp_read_diagnostics(axp_grid *g, axp_diag *out, int64_t max, int64_t *n)
+{
+    if (!g || !n || max < 0 || (max > 0 && !out)) return AXP_E_INVAL;
+    *n = 0;
+    cudaError_t e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    const int64_t cap = g->desc.diag_capacity;
+    if (cap <= 0) return AXP_OK;
+    if (g->ring_written - g->ring_read > cap) g->ring_read = g->ring_written - cap;
+    int64_t cnt = g->ring_written - g->ring_read;
+    if (cnt > max) cnt = max;
+    bool finite = true;
+    for (int64_t r = 0; r < cnt; r++) {
+        e = cudaMemcpy(out + r, ring_slot(g, g->ring_read + r), sizeof(axp_diag), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_status(e);
+        finite = finite && finite_diag(out[r]);
+    }
+    g->ring_read += cnt;
+    *n = cnt;
+    return finite ? AXP_OK : AXP_E_NONFINITE;
+}
+
+axp_status axp_compute_diagnostics(axp_grid *g, axp_diag *out)
+{
+    if (!g || !out) return AXP_E_INVAL;
+    axp_diag *dst = scratch_slot(g);
+    cudaError_t e = is_fp32(g) ? diag_compute<float>(g, dst) : diag_compute<double>(g, dst);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, dst, sizeof(axp_diag), cudaMemcpyDeviceToHost, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    return finite_diag(*out) ? AXP_OK : AXP_E_NONFINITE;
+}
+
+static void *field_ptr(axp_grid *g, int which)
+{
+    if (which >= 0 && which < kFields) return g->ws + g->layout.off_fields[g->fset][which];
+    if (which == AXP_PHI_CUR) return g->ws + g->layout.off_phi[g->phi_cur_slot];
+    return g->ws + g->layout.off_phi[g->phi_b_slot];
+}
+
+axp_status axp_read_field(axp_grid *g, int32_t which, double *dst, size_t bytes)
+{
+    if (!g || !dst || which < 0 || which > AXP_PHI_OLD) return AXP_E_INVAL;
+    const int64_t N = cells(g->desc);
+    if (bytes != (size_t)N * 8) return AXP_E_INVAL;
+    cudaError_t e = ensure_integer(g);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (!is_fp32(g)) return cuda_status(cudaMemcpy(dst, field_ptr(g, which), bytes, cudaMemcpyDeviceToHost));
+    std::vector<float> tmp(N), inc;
+    e = cudaMemcpy(tmp.data(), field_ptr(g, which == AXP_PHI_OLD ? AXP_PHI_CUR : which), N * 4,
+                   cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && which == AXP_PHI_OLD) {
+        inc.resize(N);
+        e = cudaMemcpy(inc.data(), g->ws + g->layout.off_phi[g->phi_b_slot], N * 4, cudaMemcpyDeviceToHost);
+    }
+    if (e != cudaSuccess) return cuda_status(e);
+    for (int64_t c = 0; c < N; c++) dst[c] = which == AXP_PHI_OLD ? (double)tmp[c] - (double)inc[c] : (double)tmp[c];
+    return AXP_OK;
+}
+
+axp_status axp_write_field(axp_grid *g, int32_t which, const double *src, size_t bytes)
+{
+    if (!g || !src || which < 0 || which > AXP_PHI_OLD) return AXP_E_INVAL;
+    const int64_t N = cells(g->desc);
+    if (bytes != (size_t)N * 8) return AXP_E_INVAL;
+    cudaError_t e = ensure_integer(g);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    g->J_valid = false;
+    bool nonzero = false;
+    for (int64_t c = 0; c < N && !nonzero; c++) nonzero = src[c] != 0.0;
+    if (nonzero) {
+        if (which < kFields) g->active |= 1u << which;
+        else g->phi_active = true;
+    }
+    if (!is_fp32(g)) return cuda_status(cudaMemcpy(field_ptr(g, which), src, bytes, cudaMemcpyHostToDevice));
+    std::vector<float> tmp(N);
+    if (which < kFields) {
+        for (int64_t c = 0; c < N; c++) tmp[c] = (float)src[c];
+        return cuda_status(cudaMemcpy(field_ptr(g, which), tmp.data(), N * 4, cudaMemcpyHostToDevice));
+    }
+    // increment storage: keep the other level, recompute pi = phi_cur - phi_old
+    std::vector<double> cur(N), old(N);
+    axp_status st = axp_read_field(g, AXP_PHI_CUR, cur.data(), N * 8);
+    if (st == AXP_OK) st = axp_read_field(g, AXP_PHI_OLD, old.data(), N * 8);
+    if (st != AXP_OK) return st;
+    if (which == AXP_PHI_CUR) cur.assign(src, src + N);
+    else old.assign(src, src + N);
+    std::vector<float> inc(N);
+    for (int64_t c = 0; c < N; c++) {
+        tmp[c] = (float)cur[c];
+        inc[c] = (float)(cur[c] - old[c]);
+    }
+    e = cudaMemcpy(g->ws + g->layout.off_phi[g->phi_cur_slot], tmp.data(), N * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(g->ws + g->layout.off_phi[g->phi_b_slot], inc.data(), N * 4, cudaMemcpyHostToDevice);
+    return cuda_status(e);
+}
+
+static axp_status ghost_io(axp_grid *g, int32_t axis, int32_t side, int32_t level, double *dst, const double *src,
+                           size_t bytes)
+{
+    if (!g || axis < 0 || axis > 2 || side < 0 || side > 1 || level < 0 || level > 1) return AXP_E_INVAL;
+    if (g->desc.axion_bc[axis][side] != AXP_BC_OUTFLOW) return AXP_E_INVAL;
+    const int64_t P = plane_size(g->desc, axis);
+    if (bytes != (size_t)P * 8) return AXP_E_INVAL;
+    cudaError_t e = ensure_integer(g);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    char *dev = g->ws + g->layout.off_ghost[axis][side][g->ghost_level_slot[level]];
+    if (!is_fp32(g)) {
+        if (dst) return cuda_status(cudaMemcpy(dst, dev, bytes, cudaMemcpyDeviceToHost));
+        g->J_valid = false;
+        return cuda_status(cudaMemcpy(dev, src, bytes, cudaMemcpyHostToDevice));
+    }
+    std::vector<float> tmp(P);
+    if (dst) {
+        e = cudaMemcpy(tmp.data(), dev, P * 4, cudaMemcpyDeviceToHost);
+        for (int64_t c = 0; c < P; c++) dst[c] = tmp[c];
+        return cuda_status(e);
+    }
+    for (int64_t c = 0; c < P; c++) tmp[c] = (float)src[c];
+    g->J_valid = false;
+    return cuda_status(cudaMemcpy(dev, tmp.data(), P * 4, cudaMemcpyHostToDevice));
+}
+
+axp_status axp_read_ghost(axp_grid *g, int32_t axis, int32_t side, int32_t level, double *dst, size_t bytes)
+{
+    if (!dst) return AXP_E_INVAL;
+    return ghost_io(g, axis, side, level, dst, nullptr, bytes);
+}
+
+axp_status axp_write_ghost(axp_grid *g, int32_t axis, int32_t side, int32_t level, const double *src, size_t bytes)
+{
+    if (!src) return AXP_E_INVAL;
+    return ghost_io(g, axis, side, level, nullptr, src, bytes);
+}
+
+// Checkpoint image: header, then the integer-time state packed by role -- the
+// 12 field arrays, phi^{n+1/2}, the second axion level, the cached current J
+// and the outflow ghost planes of levels n+1/2 and n-1/2.
+static void state_regions(axp_grid *g, std::vector<std::pair<char *, size_t>> *out)
+{
+    const size_t arr = (size_t)cells(g->desc) * g->layout.elem;
+    for (int f = 0; f < kFields; f++) out->push_back({g->ws + g->layout.off_fields[g->fset][f], arr});
+    out->push_back({g->ws + g->layout.off_phi[g->phi_cur_slot], arr});
+    out->push_back({g->ws + g->layout.off_phi[g->phi_b_slot], arr});
+    for (int a = 0; a < 3; a++) out->push_back({g->ws + g->layout.off_J[a], arr});
+    for (int a = 0; a < 3; a++)
+        for (int sd = 0; sd < 2; sd++)
+            for (int l = 0; l < 2; l++) {
+                const size_t off = g->layout.off_ghost[a][sd][g->ghost_level_slot[l]];
+                if (off) out->push_back({g->ws + off, (size_t)plane_size(g->desc, a) * g->layout.elem});
+            }
+}
+
+axp_status axp_state_bytes(const axp_grid *g, size_t *bytes)
+{
+    if (!g || !bytes) return AXP_E_INVAL;
+    std::vector<std::pair<char *, size_t>> r;
+    state_regions(const_cast<axp_grid *>(g), &r);
+    size_t total = sizeof(StateHeader);
+    for (auto &x : r) total += x.second;
+    *bytes = total;
+    return AXP_OK;
+}
+
+axp_status axp_save_state(axp_grid *g, void *dst, size_t bytes)
+{
+    size_t need;
+    if (!g || !dst || axp_state_bytes(g, &need) != AXP_OK || bytes != need) return AXP_E_INVAL;
+    cudaError_t e = ensure_integer(g);
+    if (e != cudaSuccess) return cuda_status(e);
+    StateHeader h;
+    std::memset(&h, 0, sizeof(h));
+    h.magic = kStateMagic;
+    h.bytes = need;
+    h.desc = g->desc;
+    for (int a = 0; a < 3; a++) {
+        h.B_ext[a] = g->B_ext[a];
+        h.E_ext[a] = g->E_ext[a];
+    }
+    h.step = g->step;
+    h.J_valid = g->J_valid;
+    h.active = g->active;
+    h.phi_active = g->phi_active;
+    std::memcpy(dst, &h, sizeof(h));
+    std::vector<std::pair<char *, size_t>> r;
+    state_regions(g, &r);
+    char *p = (char *)dst + sizeof(h);
+    for (auto &x : r) {
+        if (e == cudaSuccess) e = cudaMemcpyAsync(p, x.first, x.second, cudaMemcpyDeviceToHost, g->stream);
+        p += x.second;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    return cuda_status(e);
+}
+
+axp_status axp_load_state(axp_grid *g, const void *src, size_t bytes)
+{
+    size_t need;
+    if (!g || !src || axp_state_bytes(g, &need) != AXP_OK || bytes != need) return AXP_E_INVAL;
+    StateHeader h;
+    std::memcpy(&h, src, sizeof(h));
+    if (h.magic != kStateMagic || h.bytes != need || std::memcmp(&h.desc, &g->desc, sizeof(axp_grid_desc)) != 0)
+        return AXP_E_INVAL;
+    cudaError_t e = cudaStreamSynchronize(g->stream);
+    g->staggered = false;
+    std::vector<std::pair<char *, size_t>> r;
+    state_regions(g, &r);
+    const char *p = (const char *)src + sizeof(h);
+    for (auto &x : r) {
+        if (e == cudaSuccess) e = cudaMemcpyAsync(x.first, p, x.second, cudaMemcpyHostToDevice, g->stream);
+        p += x.second;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    for (int a = 0; a < 3; a++) {
+        g->B_ext[a] = h.B_ext[a];
+        g->E_ext[a] = h.E_ext[a];
+    }
+    g->step = h.step;
+    g->J_valid = h.J_valid != 0;
+    g->active = h.active;
+    g->phi_active = h.phi_active != 0;
+    g->ring_read = g->ring_written;
+    return AXP_OK;
+}
+
+axp_status axp_get_step(const axp_grid *g, int64_t *step)
+{
+    if (!g || !step) return AXP_E_INVAL;
+    *step = g->step;
+    return AXP_OK;
+}
+
+axp_status axp_set_kernel(axp_grid *g, int32_t kernel)
+{
+    if (!g || kernel < AXP_KERNEL_AUTO || kernel > AXP_KERNEL_FUSED) return AXP_E_INVAL;
+    g->kernel_choice = kernel;
+    return AXP_OK;
+}
+
+axp_status axp_get_kernel_path(axp_grid *g, int32_t *path)
+{
+    if (!g || !path) return AXP_E_INVAL;
+    bool fused = false;
+    if (g->kernel_choice != AXP_KERNEL_GENERAL) fused = is_fp32(g) ? fused_supported<float>(g) : fused_supported<double>(g);
+    *path = fused ? AXP_KERNEL_FUSED : AXP_KERNEL_GENERAL;
+    return AXP_OK;
+}
+
+axp_status axp_get_launch_count(const axp_grid *g, int64_t *count)
+{
+    if (!g || !count) return AXP_E_INVAL;
+    *count = g->launches;
+    return AXP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,119 @@
+// axp_internal.h -- definitions shared by the CUDA translation units of libaxp.
+//
+// Method: arXiv 2406.16796 Sec. 2.3-2.4.  This header holds the grid handle,
+// the by-value kernel view of a grid, and the boundary-aware index helpers
+// used by the general (multi-pass) kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "axp.h"
+
+namespace axp {
+
+constexpr int kFields = 12;  // E0xyz B0xyz E1xyz B1xyz
+constexpr int kE0 = 0, kB0 = 3, kE1 = 6, kB1 = 9;
+constexpr int kDiagSlots = 10;  // per-cell accumulators of the diagnostics kernel
+
+// Per-grid parameters in the arithmetic type T, passed to kernels by value.
+template <typename T>
+struct View {
+    T *f[kFields];
+    T *phi_cur;   // phi^{n+1/2}
+    T *phi_b;     // FP64: phi^{n-1/2};  FP32 split: increment pi^n = phi^{n+1/2} - phi^{n-1/2}
+    T *phi_next;  // FP32 split: buffer that receives phi^{n+3/2}; unused for FP64
+    T *J[3];      // axion current (without g) at the E locations
+    T *gh[3][2][3];  // outflow ghost planes [axis][side][level: 0 = n+1/2, 1 = n-1/2, 2 = n+3/2]
+    const T *sig_em[3];  // absorbing-layer profile per axis (E/B), length n[a]
+    const T *sig_ax[3];  // PML profile per axis (axion)
+    int64_t n[3];
+    int64_t N;
+    T d[3];
+    T lo[3];
+    T dt, h;     // h = dt / 2
+    T g, m2;
+    T Bext[3], Eext[3];
+    int periodic[3];
+    int axbc[3][2];
+    int region_lo[3], region_hi[3];  // diagnostics region [lo, hi) per axis
+};
+
+struct Workspace {
+    size_t off_fields[2][kFields];  // two field sets: the fused step reads one and writes the other
+    size_t off_phi[4];              // axion buffers; roles are tracked by the handle
+    size_t off_J[3];
+    size_t off_ghost[3][2][3];
+    size_t off_sig_em[3], off_sig_ax[3];
+    size_t off_partials;
+    size_t off_ring;
+    size_t off_flag;
+    size_t total;
+    int diag_blocks;
+    size_t elem;
+};
+
+}  // namespace axp
+
+struct axp_grid {
+    axp_grid_desc desc;
+    double B_ext[3], E_ext[3];
+    cudaStream_t stream;
+    int device;
+    char *ws;
+    size_t ws_bytes;
+    axp::Workspace layout;
+    // current roles of the axion buffers (indices into off_phi): phi^{n+1/2}, the
+    // second level (phi^{n-1/2} or the increment), and two spares
+    int phi_cur_slot, phi_b_slot, phi_next_slot, phi_next_b_slot;
+    int fset;         // field set holding the present state
+    bool staggered;   // E arrays hold E^{n+1/2} (fused-path state) instead of E^n
+    int ghost_level_slot[3];  // which stored plane currently holds level 0/1/2
+    int64_t step;
+    bool J_valid;       // J holds J^n of the present state
+    int32_t kernel_choice;
+    int64_t ring_written;  // records appended since creation
+    int64_t ring_read;     // records returned to the caller
+    int64_t launches;
+    uint32_t active;       // bit per field array that may be non-zero
+    bool phi_active;
+};
+
+namespace axp {
+
+size_t elem_size(const axp_grid_desc &d);
+bool compute_layout(const axp_grid_desc &d, Workspace *w);
+
+template <typename T>
+View<T> make_view(axp_grid *g);
+// view whose E0/E1 arrays are taken from field set `eset` (B and the rest from the present set)
+template <typename T>
+View<T> make_view_eset(axp_grid *g, int eset);
+
+// launchers implemented in the .cu files (return cudaGetLastError())
+template <typename T>
+cudaError_t general_step(axp_grid *g, int64_t nsteps);
+template <typename T>
+cudaError_t general_current(axp_grid *g);  // J^n of the present state
+template <typename T>
+cudaError_t diag_compute(axp_grid *g, axp_diag *dev_dst);
+template <typename T>
+cudaError_t inject_laser(axp_grid *g, const axp_laser_desc &L);
+template <typename T>
+cudaError_t inject_axion(axp_grid *g, const axp_axion_desc &A);
+template <typename T>
+cudaError_t fused_step(axp_grid *g, int64_t nsteps, bool *handled);
+template <typename T>
+bool fused_supported(const axp_grid *g);
+// staggered <-> integer-time conversion of E (E^{n+1/2} = E^n + h (curl B^n - g J^n))
+template <typename T>
+cudaError_t enter_staggered(axp_grid *g);
+template <typename T>
+cudaError_t exit_staggered(axp_grid *g, bool in_place);
+// mask of E0/B0 components that can become non-zero (bits 0-2 E0xyz, 3-5 B0xyz)
+uint32_t order0_closure(const axp_grid *g);
+cudaError_t ensure_integer(axp_grid *g);
+
+axp_diag *ring_slot(axp_grid *g, int64_t index);
+
+}  // namespace axp

@@ -1,0 +1,206 @@
+// kernels_fused.cu -- host side of the fused single-pass step: eligibility,
+// parameter setup, launch geometry and the per-step buffer rotation.
+#include <cmath>
+#include <utility>
+
+#include "kernels_fused.cuh"
+
+namespace axp {
+
+cudaError_t fused_dispatch_f64(int mode, int set, const fused::Params<double> &P, int nchunks, cudaStream_t s,
+                               int *occ);
+cudaError_t fused_dispatch_f32(int mode, int set, const fused::Params<float> &P, int nchunks, cudaStream_t s,
+                               int *occ);
+
+namespace {
+
+constexpr uint32_t kSets[4] = {0u, (4u) | (3u << 3), (3u) | (4u << 3), 63u};
+
+int grid_mode(const axp_grid *g)
+{
+    const int64_t *n = g->desc.n;
+    if (n[0] < 2) return 0;
+    if (n[1] == 1 && n[2] == 1) return 1;
+    if (n[2] == 1) return 2;
+    if (n[1] > 1 && n[2] > 1) return 3;
+    return 0;
+}
+
+int pick_set(const axp_grid *g)
+{
+    const uint32_t m = order0_closure(g);
+    for (int s = 0; s < 4; s++)
+        if ((m & ~kSets[s]) == 0) return s;
+    return 3;
+}
+
+template <typename T>
+cudaError_t dispatch(int mode, int set, const fused::Params<T> &P, int nchunks, cudaStream_t s, int *occ);
+template <>
+cudaError_t dispatch<double>(int mode, int set, const fused::Params<double> &P, int nchunks, cudaStream_t s, int *occ)
+{
+    return fused_dispatch_f64(mode, set, P, nchunks, s, occ);
+}
+template <>
+cudaError_t dispatch<float>(int mode, int set, const fused::Params<float> &P, int nchunks, cudaStream_t s, int *occ)
+{
+    return fused_dispatch_f32(mode, set, P, nchunks, s, occ);
+}
+
+template <typename T>
+fused::Params<T> make_params(axp_grid *g)
+{
+    fused::Params<T> P;
+    const axp_grid_desc &d = g->desc;
+    const Workspace &w = g->layout;
+    const int in = g->fset, out = 1 - g->fset;
+    for (int q = 0; q < 6; q++) {
+        const int fe = q < 3 ? kE0 + q : kE1 + (q - 3);
+        const int fb = q < 3 ? kB0 + q : kB1 + (q - 3);
+        P.Ein[q] = (const T *)(g->ws + w.off_fields[in][fe]);
+        P.Bin[q] = (const T *)(g->ws + w.off_fields[in][fb]);
+        P.Eout[q] = (T *)(g->ws + w.off_fields[out][fe]);
+        P.Bout[q] = (T *)(g->ws + w.off_fields[out][fb]);
+    }
+    P.phi = (const T *)(g->ws + w.off_phi[g->phi_cur_slot]);
+    P.phib = (const T *)(g->ws + w.off_phi[g->phi_b_slot]);
+    P.phi_out = (T *)(g->ws + w.off_phi[g->phi_next_slot]);
+    P.phib_out = d.precision == AXP_FP32_SPLIT ? (T *)(g->ws + w.off_phi[g->phi_next_b_slot]) : nullptr;
+    double s_idx2 = 0.0;
+    bool pml = false;
+    for (int a = 0; a < 3; a++) {
+        P.sig_em[a] = (const T *)(g->ws + w.off_sig_em[a]);
+        P.sig_ax[a] = (const T *)(g->ws + w.off_sig_ax[a]);
+        P.n[a] = (int)d.n[a];
+        P.per[a] = d.em_bc[a][0] == AXP_BC_PERIODIC;
+        for (int s = 0; s < 2; s++) {
+            P.axbc[a][s] = d.axion_bc[a][s];
+            if (d.axion_bc[a][s] == AXP_BC_PML || d.em_bc[a][s] == AXP_BC_PML) pml = true;
+        }
+        const double inv = 1.0 / d.d[a];
+        P.idx[a] = (T)inv;
+        P.hidx[a] = (T)(0.5 * inv);
+        P.idx2[a] = (T)(inv * inv);
+        P.lap_c[a] = (T)(d.dt * d.dt * inv * inv);
+        if (d.n[a] > 1) s_idx2 += inv * inv;
+        P.Bext[a] = (T)g->B_ext[a];
+    }
+    P.has_pml = pml && d.pml_cells > 0 && d.pml_sigma_max_dt > 0;
+    const double base = -d.dt * d.dt * (d.m * d.m + 2.0 * s_idx2);
+    P.lap_0 = (T)(d.precision == AXP_FP32_SPLIT ? base : 2.0 + base);
+    P.dt2g = (T)(d.dt * d.dt * d.g);
+    P.h = (T)(d.dt / 2.0);
+    P.dt = (T)d.dt;
+    P.dt2 = (T)(d.dt * d.dt);
+    P.inv_dt = (T)(1.0 / d.dt);
+    P.g = (T)d.g;
+    P.m2 = (T)(d.m * d.m);
+    P.chunk = 1;
+    return P;
+}
+
+template <typename T, int MODE>
+size_t ring_bytes(int set)
+{
+    static const int planes[4] = {fused::Lay<MODE, 0, 0>::PLANES, fused::Lay<MODE, 4, 3>::PLANES,
+                                  fused::Lay<MODE, 3, 4>::PLANES, fused::Lay<MODE, 7, 7>::PLANES};
+    return (size_t)planes[set] * fused::Tile<T, MODE>::NT * sizeof(T);
+}
+
+template <typename T>
+size_t smem_need(int mode, int set)
+{
+    if (mode == 1) return ring_bytes<T, 1>(set);
+    if (mode == 2) return ring_bytes<T, 2>(set);
+    return ring_bytes<T, 3>(set);
+}
+
+}  // namespace
+
+template <typename T>
+bool fused_supported(const axp_grid *g)
+{
+    const int mode = grid_mode(g);
+    if (mode == 0) return false;
+    int optin = 0;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, g->device) != cudaSuccess) return false;
+    if (smem_need<T>(mode, pick_set(g)) > (size_t)optin) return false;
+    for (int a = 0; a < 3; a++) {
+        if (g->E_ext[a] != 0.0) return false;
+        if (g->desc.n[a] > (1 << 30)) return false;
+        for (int s = 0; s < 2; s++)
+            if (g->desc.axion_bc[a][s] == AXP_BC_OUTFLOW) return false;
+    }
+    if (mode >= 2 && g->desc.n[mode == 3 ? 2 : 1] < 1) return false;
+    return true;
+}
+
+template <typename T>
+cudaError_t fused_step(axp_grid *g, int64_t nsteps, bool *handled)
+{
+    *handled = false;
+    if (!fused_supported<T>(g)) return cudaSuccess;
+    *handled = true;
+    const int mode = grid_mode(g);
+    const int set = pick_set(g);
+    cudaError_t e = enter_staggered<T>(g);
+    if (e != cudaSuccess) return e;
+    // launch geometry: as many march chunks as keep every resident CTA slot busy
+    int occ = 0;
+    fused::Params<T> P = make_params<T>(g);
+    e = dispatch<T>(mode, set, P, 0, g->stream, &occ);
+    if (e != cudaSuccess) return e;
+    int nchunks = 1;
+    if (mode >= 2) {
+        int sms = 152;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
+        const int VX = mode == 3 ? fused::Tile<T, 3>::VX : fused::Tile<T, 2>::VX;
+        const int VY = mode == 3 ? fused::Tile<T, 3>::VY : 1;
+        const int64_t strips = ((g->desc.n[0] + VX - 1) / VX) * (mode == 3 ? (g->desc.n[1] + VY - 1) / VY : 1);
+        const int64_t nm = g->desc.n[mode == 3 ? 2 : 1];
+        const int64_t slots = (int64_t)sms * (occ > 0 ? occ : 1);
+        int64_t nc = slots / strips;
+        if (nc < 1) nc = 1;
+        const int64_t min_chunk = 16;
+        if (nm / nc < min_chunk) nc = nm / min_chunk > 0 ? nm / min_chunk : 1;
+        int64_t chunk = (nm + nc - 1) / nc;
+        nchunks = (int)((nm + chunk - 1) / chunk);
+        P.chunk = (int)chunk;
+    }
+    for (int64_t it = 0; it < nsteps; it++) {
+        if (it > 0) {
+            const int ch = P.chunk;
+            P = make_params<T>(g);
+            P.chunk = ch;
+        }
+        e = dispatch<T>(mode, set, P, nchunks, g->stream, nullptr);
+        if (e != cudaSuccess) return e;
+        g->launches++;
+        // rotate: the output field set becomes current; axion buffers shift roles
+        g->fset = 1 - g->fset;
+        if (g->desc.precision == AXP_FP32_SPLIT) {
+            std::swap(g->phi_cur_slot, g->phi_next_slot);
+            std::swap(g->phi_b_slot, g->phi_next_b_slot);
+        } else {
+            const int old = g->phi_b_slot;
+            g->phi_b_slot = g->phi_cur_slot;
+            g->phi_cur_slot = g->phi_next_slot;
+            g->phi_next_slot = old;
+        }
+        g->step++;
+        if (g->desc.diag_every > 0 && g->step % g->desc.diag_every == 0) {
+            axp_diag *dst = ring_slot(g, g->ring_written);
+            if ((e = diag_compute<T>(g, dst)) != cudaSuccess) return e;
+            g->ring_written++;
+        }
+    }
+    g->J_valid = false;
+    return cudaGetLastError();
+}
+
+template bool fused_supported<double>(const axp_grid *);
+template bool fused_supported<float>(const axp_grid *);
+template cudaError_t fused_step<double>(axp_grid *, int64_t, bool *);
+template cudaError_t fused_step<float>(axp_grid *, int64_t, bool *);
+
+}  // namespace axp

@@ -1,0 +1,398 @@
+// kernels_general.cu -- the general multi-pass step (arXiv 2406.16796 Sec. 2.3-2.4).
+//
+// One kernel per stage of the half-step scheme, one thread per cell, every
+// stencil access through the boundary-aware accessors of device_common.cuh.
+// Covers every dimension, boundary kind and field component.  Each stage
+// evaluates its expressions in the order the scheme states them; this
+// translation unit is compiled without multiply-add contraction, so the FP64
+// instantiation reproduces a literal double-precision evaluation of the scheme.
+//
+// Stage order of one step n -> n+1 (order 0 always before order 1):
+//   [J^n if not cached] -> E half (both orders, J^n) -> B half (both orders)
+//   -> S^{n+1/2} and phi^{n+3/2} (PML form in the layer) -> outflow ghosts
+//   -> B half (both orders) -> E0 half -> J^{n+1} -> E1 half (J^{n+1}).
+#include "device_common.cuh"
+
+namespace axp {
+namespace {
+
+constexpr int kThreads = 256;
+
+inline int grid_for(int64_t work)
+{
+    int64_t b = (work + kThreads - 1) / kThreads;
+    if (b > 152 * 16) b = 152 * 16;
+    return (int)(b < 1 ? 1 : b);
+}
+
+// P_a = (D_t phi) Bbar0_a - (Ebar0 x grad_c phi)_a at one cell centre, (a, b, c) cyclic.
+template <typename T, bool INCR>
+__device__ T p_comp(const View<T> &v, const PhiPair<T, INCR> &q, int a, int64_t i, int64_t j, int64_t k)
+{
+    const int b = (a + 1) % 3, c = (a + 2) % 3;
+    int64_t ub[3], uc[3];
+    unit(b, ub);
+    unit(c, uc);
+    T mid, Dt;
+    phi_mid_dt<T, INCR>(v, q, i, j, k, &mid, &Dt);
+    const T dphi_c = (phi_mid<T, INCR>(v, q, i + uc[0], j + uc[1], k + uc[2]) -
+                      phi_mid<T, INCR>(v, q, i - uc[0], j - uc[1], k - uc[2])) /
+                     (T(2) * v.d[c]);
+    const T dphi_b = (phi_mid<T, INCR>(v, q, i + ub[0], j + ub[1], k + ub[2]) -
+                      phi_mid<T, INCR>(v, q, i - ub[0], j - ub[1], k - ub[2])) /
+                     (T(2) * v.d[b]);
+    const T cross = e0_bar(v, b, i, j, k) * dphi_c - e0_bar(v, c, i, j, k) * dphi_b;
+    return Dt * b0_bar(v, a, i, j, k) - cross;
+}
+
+// J_a(c + a/2) = (P_a(c) + P_a(c + a)) / 2, all three components.
+template <typename T, bool INCR>
+__global__ void __launch_bounds__(kThreads) k_current(View<T> v, PhiPair<T, INCR> q)
+{
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < v.N; c += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i, j, k;
+        cell_of(c, v.n, &i, &j, &k);
+        for (int a = 0; a < 3; a++) {
+            int64_t u[3];
+            unit(a, u);
+            const T p0 = p_comp<T, INCR>(v, q, a, i, j, k);
+            const T p1 = p_comp<T, INCR>(v, q, a, i + u[0], j + u[1], k + u[2]);
+            v.J[a][c] = T(0.5) * (p0 + p1);
+        }
+    }
+}
+
+// (curl B)_a at the E_a location: backward differences.
+template <typename T>
+__device__ __forceinline__ T curl_b(const View<T> &v, T *const B[3], int a, int64_t i, int64_t j, int64_t k)
+{
+    if (a == 0)
+        return (ld(v, B[2], i, j, k) - ld(v, B[2], i, j - 1, k)) / v.d[1] -
+               (ld(v, B[1], i, j, k) - ld(v, B[1], i, j, k - 1)) / v.d[2];
+    if (a == 1)
+        return (ld(v, B[0], i, j, k) - ld(v, B[0], i, j, k - 1)) / v.d[2] -
+               (ld(v, B[2], i, j, k) - ld(v, B[2], i - 1, j, k)) / v.d[0];
+    return (ld(v, B[1], i, j, k) - ld(v, B[1], i - 1, j, k)) / v.d[0] -
+           (ld(v, B[0], i, j, k) - ld(v, B[0], i, j - 1, k)) / v.d[1];
+}
+
+// (curl E)_a at the B_a location: forward differences.
+template <typename T>
+__device__ __forceinline__ T curl_e(const View<T> &v, T *const E[3], int a, int64_t i, int64_t j, int64_t k)
+{
+    if (a == 0)
+        return (ld(v, E[2], i, j + 1, k) - ld(v, E[2], i, j, k)) / v.d[1] -
+               (ld(v, E[1], i, j, k + 1) - ld(v, E[1], i, j, k)) / v.d[2];
+    if (a == 1)
+        return (ld(v, E[0], i, j, k + 1) - ld(v, E[0], i, j, k)) / v.d[2] -
+               (ld(v, E[2], i + 1, j, k) - ld(v, E[2], i, j, k)) / v.d[0];
+    return (ld(v, E[1], i + 1, j, k) - ld(v, E[1], i, j, k)) / v.d[0] -
+           (ld(v, E[0], i, j + 1, k) - ld(v, E[0], i, j, k)) / v.d[1];
+}
+
+// E half-step: orders selected by the mask (bit 0 = order 0, bit 1 = order 1);
+// order 1 includes the axion current: X = curl B1 - g J.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_e_half(View<T> v, int orders)
+{
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < v.N; c += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i, j, k;
+        cell_of(c, v.n, &i, &j, &k);
+        const T sig = sigma_of<T>(v.sig_em, i, j, k);
+        if (orders & 1) {
+            T *const B[3] = {v.f[kB0], v.f[kB0 + 1], v.f[kB0 + 2]};
+            for (int a = 0; a < 3; a++) {
+                const T X = curl_b(v, B, a, i, j, k);
+                v.f[kE0 + a][c] = half_update(v.f[kE0 + a][c], X, sig, v.h);
+            }
+        }
+        if (orders & 2) {
+            T *const B[3] = {v.f[kB1], v.f[kB1 + 1], v.f[kB1 + 2]};
+            for (int a = 0; a < 3; a++) {
+                T X = curl_b(v, B, a, i, j, k);
+                X = X - v.g * v.J[a][c];
+                v.f[kE1 + a][c] = half_update(v.f[kE1 + a][c], X, sig, v.h);
+            }
+        }
+    }
+}
+
+// B half-step of both orders: B <- B - h curl E.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_b_half(View<T> v)
+{
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < v.N; c += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i, j, k;
+        cell_of(c, v.n, &i, &j, &k);
+        const T sig = sigma_of<T>(v.sig_em, i, j, k);
+        T *const E0[3] = {v.f[kE0], v.f[kE0 + 1], v.f[kE0 + 2]};
+        T *const E1[3] = {v.f[kE1], v.f[kE1 + 1], v.f[kE1 + 2]};
+        for (int a = 0; a < 3; a++) v.f[kB0 + a][c] = half_update(v.f[kB0 + a][c], -curl_e(v, E0, a, i, j, k), sig, v.h);
+        for (int a = 0; a < 3; a++) v.f[kB1 + a][c] = half_update(v.f[kB1 + a][c], -curl_e(v, E1, a, i, j, k), sig, v.h);
+    }
+}
+
+// Axion leapfrog (Eq. update_axion) with the source S^{n+1/2} = g Ebar0 . Bbar0,
+// and the damped form of Sec. 2.4 item 4 inside the PML.
+//   FP64 (two levels): phi^{n+3/2} is written over phi^{n-1/2}.
+//   FP32 split: pi^{n+1} = phi^{n+3/2} - phi^{n+1/2} replaces pi^n in place and
+//   phi^{n+3/2} = phi^{n+1/2} + pi^{n+1} goes to phi_next.
+template <typename T, bool INCR>
+__global__ void __launch_bounds__(kThreads) k_axion(View<T> v, Ghosts<T> gcur)
+{
+    const T dt2 = v.dt * v.dt;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < v.N; c += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i, j, k;
+        cell_of(c, v.n, &i, &j, &k);
+        const T S = source_at(v, i, j, k);
+        const T ph = v.phi_cur[c];
+        T lap = T(0);
+        for (int a = 0; a < 3; a++) {
+            int64_t u[3];
+            unit(a, u);
+            const T up = ld_phi(v, v.phi_cur, gcur, i + u[0], j + u[1], k + u[2]);
+            const T dn = ld_phi(v, v.phi_cur, gcur, i - u[0], j - u[1], k - u[2]);
+            lap = lap + ((up + dn) - T(2) * ph) / (v.d[a] * v.d[a]);
+        }
+        const T sig = sigma_of<T>(v.sig_ax, i, j, k);
+        if (!INCR) {
+            const T old = v.phi_b[c];
+            T nw;
+            if (sig == T(0)) {
+                nw = T(2) * ph - old + dt2 * ((lap - v.m2 * ph) + S);
+            } else {
+                const T Y = ((S - v.m2 * ph) + lap) - sig * sig * ph;
+                nw = (dt2 * Y + sig * v.dt * old + T(2) * ph - old) / (T(1) + sig * v.dt);
+            }
+            v.phi_b[c] = nw;
+        } else {
+            const T inc = v.phi_b[c];
+            T nin;
+            if (sig == T(0)) {
+                nin = inc + dt2 * ((lap - v.m2 * ph) + S);
+            } else {
+                const T Y = ((S - v.m2 * ph) + lap) - sig * sig * ph;
+                nin = (dt2 * Y + (T(1) - sig * v.dt) * inc) / (T(1) + sig * v.dt);
+            }
+            v.phi_b[c] = nin;
+            v.phi_next[c] = ph + nin;
+        }
+    }
+}
+
+// Outflow ghosts at the new level for one face (Sec. 2.4 item 3): solve the
+// one-way wave equation and the wave equation at the ghost for
+// V = phi^{cur}_{-3/2} and U = phi^{new}_{-1/2}.
+template <typename T>
+__global__ void k_outflow(View<T> v, int ax, int side, const T *g_cur, const T *g_old, T *g_new)
+{
+    const int b = (ax + 1) % 3, cc = (ax + 2) % 3;
+    const int64_t nb = v.n[b], nc = v.n[cc];
+    const T r = v.dt / v.d[ax];
+    const T r2 = (v.dt * v.dt) / (v.d[ax] * v.d[ax]);
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nb * nc; t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t ca[3];
+        ca[b] = t % nb;
+        ca[cc] = t / nb;
+        ca[ax] = side ? v.n[ax] : -1;
+        const int64_t pi = ax == 0 ? ca[1] + v.n[1] * ca[2] : (ax == 1 ? ca[0] + v.n[0] * ca[2] : ca[0] + v.n[0] * ca[1]);
+        const T Sg = source_at(v, ca[0], ca[1], ca[2]);
+        int64_t ci[3] = {ca[0], ca[1], ca[2]};
+        ci[ax] = side ? v.n[ax] - 1 : 0;
+        const T p0 = v.phi_cur[lin3(v.n, ci[0], ci[1], ci[2])];
+        const T gc = g_cur[pi], go = g_old[pi];
+        const T rhs = T(-2) * gc + T(2) * go - (v.dt * v.dt) * (Sg - v.m2 * gc) + r * p0 - r2 * (p0 - T(2) * gc);
+        const T V = rhs / (r + r2);
+        g_new[pi] = go + r * (p0 - V);
+    }
+}
+
+// Inverse of half_update: the field a half-step h earlier, given X.
+template <typename T>
+__device__ __forceinline__ T half_inverse(T Fh, T X, T sig, T h)
+{
+    if (sig == T(0)) return Fh - h * X;
+    return ((T(1) + sig * h / T(2)) * Fh - h * X) / (T(1) - sig * h / T(2));
+}
+
+template <typename T>
+struct EOut {
+    T *p[3];
+};
+
+// E^n from E^{n+1/2} of one order: E^n = E^{n+1/2} - h (curl B^n - g J^n) (order 1)
+// or - h curl B^n (order 0), written to `out` (which may alias the input).
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_e_unhalf(View<T> v, int order, EOut<T> out)
+{
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < v.N; c += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i, j, k;
+        cell_of(c, v.n, &i, &j, &k);
+        const T sig = sigma_of<T>(v.sig_em, i, j, k);
+        const int fb = order ? kB1 : kB0, fe = order ? kE1 : kE0;
+        T *const B[3] = {v.f[fb], v.f[fb + 1], v.f[fb + 2]};
+        for (int a = 0; a < 3; a++) {
+            T X = curl_b(v, B, a, i, j, k);
+            if (order) X = X - v.g * v.J[a][c];
+            out.p[a][c] = half_inverse(v.f[fe + a][c], X, sig, v.h);
+        }
+    }
+}
+
+}  // namespace
+
+template <typename T>
+static Ghosts<T> ghosts_at(axp_grid *g, int level)
+{
+    Ghosts<T> G;
+    for (int a = 0; a < 3; a++)
+        for (int s = 0; s < 2; s++) {
+            const size_t off = g->layout.off_ghost[a][s][g->ghost_level_slot[level]];
+            G.p[a][s] = off ? (T *)(g->ws + off) : nullptr;
+        }
+    return G;
+}
+
+template <typename T, bool INCR>
+static cudaError_t launch_current(axp_grid *g, const View<T> &v, const T *hi, const T *b, int lev_hi, int lev_lo)
+{
+    PhiPair<T, INCR> q;
+    q.hi = hi;
+    q.b = b;
+    q.ghi = ghosts_at<T>(g, lev_hi);
+    q.glo = ghosts_at<T>(g, lev_lo);
+    k_current<T, INCR><<<grid_for(v.N), kThreads, 0, g->stream>>>(v, q);
+    g->launches++;
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t general_current(axp_grid *g)
+{
+    View<T> v = make_view<T>(g);
+    if (g->desc.precision == AXP_FP32_SPLIT) return launch_current<T, true>(g, v, v.phi_cur, v.phi_b, 0, 1);
+    return launch_current<T, false>(g, v, v.phi_cur, v.phi_b, 0, 1);
+}
+
+template <typename T>
+cudaError_t general_step(axp_grid *g, int64_t nsteps)
+{
+    const bool incr = g->desc.precision == AXP_FP32_SPLIT;
+    const int nb = grid_for(g->layout.total ? (int64_t)(g->desc.n[0] * g->desc.n[1] * g->desc.n[2]) : 1);
+    for (int64_t it = 0; it < nsteps; it++) {
+        cudaError_t e;
+        if (!g->J_valid) {
+            if ((e = general_current<T>(g)) != cudaSuccess) return e;
+            g->J_valid = true;
+        }
+        View<T> v = make_view<T>(g);
+        k_e_half<T><<<nb, kThreads, 0, g->stream>>>(v, 3);
+        k_b_half<T><<<nb, kThreads, 0, g->stream>>>(v);
+        Ghosts<T> gcur = ghosts_at<T>(g, 0);
+        if (incr)
+            k_axion<T, true><<<nb, kThreads, 0, g->stream>>>(v, gcur);
+        else
+            k_axion<T, false><<<nb, kThreads, 0, g->stream>>>(v, gcur);
+        g->launches += 3;
+        Ghosts<T> gold = ghosts_at<T>(g, 1), gnew = ghosts_at<T>(g, 2);
+        for (int a = 0; a < 3; a++)
+            for (int s = 0; s < 2; s++) {
+                if (g->desc.axion_bc[a][s] != AXP_BC_OUTFLOW) continue;
+                const int b = (a + 1) % 3, c = (a + 2) % 3;
+                const int64_t plane = g->desc.n[b] * g->desc.n[c];
+                k_outflow<T><<<grid_for(plane), kThreads, 0, g->stream>>>(v, a, s, gcur.p[a][s], gold.p[a][s],
+                                                                           gnew.p[a][s]);
+                g->launches++;
+            }
+        k_b_half<T><<<nb, kThreads, 0, g->stream>>>(v);
+        k_e_half<T><<<nb, kThreads, 0, g->stream>>>(v, 1);
+        g->launches += 2;
+        // J^{n+1} from phi^{n+3/2} (hi) and phi^{n+1/2}
+        if (incr) {
+            e = launch_current<T, true>(g, v, v.phi_next, v.phi_b, 2, 0);
+        } else {
+            e = launch_current<T, false>(g, v, v.phi_b, v.phi_cur, 2, 0);
+        }
+        if (e != cudaSuccess) return e;
+        k_e_half<T><<<nb, kThreads, 0, g->stream>>>(v, 2);
+        g->launches++;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        // rotate the axion levels and the ghost planes
+        if (incr) {
+            const int t = g->phi_cur_slot;
+            g->phi_cur_slot = g->phi_next_slot;
+            g->phi_next_slot = t;
+        } else {
+            const int t = g->phi_cur_slot;
+            g->phi_cur_slot = g->phi_b_slot;
+            g->phi_b_slot = t;
+        }
+        const int s0 = g->ghost_level_slot[0], s1 = g->ghost_level_slot[1], s2 = g->ghost_level_slot[2];
+        g->ghost_level_slot[0] = s2;
+        g->ghost_level_slot[1] = s0;
+        g->ghost_level_slot[2] = s1;
+        g->step++;
+        if (g->desc.diag_every > 0 && g->step % g->desc.diag_every == 0) {
+            axp_diag *dst = ring_slot(g, g->ring_written);
+            if ((e = diag_compute<T>(g, dst)) != cudaSuccess) return e;
+            g->ring_written++;
+        }
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t enter_staggered(axp_grid *g)
+{
+    if (g->staggered) return cudaSuccess;
+    cudaError_t e = general_current<T>(g);
+    if (e != cudaSuccess) return e;
+    View<T> v = make_view<T>(g);
+    const int nb = grid_for(v.N);
+    k_e_half<T><<<nb, kThreads, 0, g->stream>>>(v, 3);
+    g->launches++;
+    g->staggered = true;
+    g->J_valid = false;
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t exit_staggered(axp_grid *g, bool in_place)
+{
+    if (!g->staggered) return cudaSuccess;
+    const int oset = in_place ? g->fset : 1 - g->fset;
+    View<T> vin = make_view<T>(g);
+    View<T> vout = make_view_eset<T>(g, oset);
+    const int nb = grid_for(vin.N);
+    EOut<T> o0{{vout.f[kE0], vout.f[kE0 + 1], vout.f[kE0 + 2]}};
+    k_e_unhalf<T><<<nb, kThreads, 0, g->stream>>>(vin, 0, o0);
+    g->launches++;
+    cudaError_t e;
+    // J^n from E0^n (in vout), B0^n and the axion levels
+    if (g->desc.precision == AXP_FP32_SPLIT)
+        e = launch_current<T, true>(g, vout, vout.phi_cur, vout.phi_b, 0, 1);
+    else
+        e = launch_current<T, false>(g, vout, vout.phi_cur, vout.phi_b, 0, 1);
+    if (e != cudaSuccess) return e;
+    EOut<T> o1{{vout.f[kE1], vout.f[kE1 + 1], vout.f[kE1 + 2]}};
+    k_e_unhalf<T><<<nb, kThreads, 0, g->stream>>>(vin, 1, o1);
+    g->launches++;
+    if (in_place) {
+        g->staggered = false;
+        g->J_valid = true;
+    } else {
+        g->J_valid = false;
+    }
+    return cudaGetLastError();
+}
+
+template cudaError_t enter_staggered<double>(axp_grid *);
+template cudaError_t enter_staggered<float>(axp_grid *);
+template cudaError_t exit_staggered<double>(axp_grid *, bool);
+template cudaError_t exit_staggered<float>(axp_grid *, bool);
+template cudaError_t general_step<double>(axp_grid *, int64_t);
+template cudaError_t general_step<float>(axp_grid *, int64_t);
+template cudaError_t general_current<double>(axp_grid *);
+template cudaError_t general_current<float>(axp_grid *);
+
+}  // namespace axp

@@ -1,0 +1,280 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI.
+
+Tolerances:
+  * general FP64 kernels (one pass per stage, no multiply-add contraction,
+    the oracle's operation order): bit-identical fields;
+  * fused FP64 kernels: normwise relative <= 1e-12 after N steps;
+  * FP32 split: normwise relative <= 1e-4 on the fields and <= 1e-3 on the
+    conversion probability;
+  * diagnostics (different summation order): relative <= 1e-12 in FP64.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2406_16796_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+NAMES = list(W.FIELD_NAMES) + ["phi_cur", "phi_old"]
+
+
+def axp_mod():
+    from paper_2406_16796_gb300 import axp
+
+    return axp
+
+
+def periodic_grid(n, d=(0.05, 0.07, 0.06), cfl=0.5, **kw):
+    nd = [a for a in range(3) if n[a] > 1]
+    dt = cfl / math.sqrt(sum(1.0 / d[a] ** 2 for a in nd))
+    return W.GridSpec(n=tuple(n), d=tuple(d), dt=dt, **kw)
+
+
+def make_pair(grid, state, ghosts=None, kernel=None):
+    axp = axp_mod()
+    og = oracle.OracleGrid(grid)
+    og.load(state)
+    g = axp.Grid(grid)
+    if kernel is not None:
+        g.set_kernel(kernel)
+    g.load(state)
+    if ghosts:
+        for (a, s), (cur, old) in ghosts.items():
+            og.set_ghost(a, s, cur, old)
+            g.write_ghost(a, s, 0, cur)
+            g.write_ghost(a, s, 1, old)
+    return og, g
+
+
+def rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def random_ghosts(grid, seed):
+    rng = np.random.default_rng(seed)
+    out = {}
+    for a in range(3):
+        for s in range(2):
+            if grid.axion_bc[a][s] == "outflow":
+                shape = oracle.plane_shape(grid, a)
+                out[(a, s)] = (rng.uniform(-1e-2, 1e-2, shape), rng.uniform(-1e-2, 1e-2, shape))
+    return out
+
+
+CASES = {
+    "1d_periodic": dict(n=(64, 1, 1), B_ext=(0.0, 1.0, 0.2)),
+    "2d_periodic": dict(n=(40, 24, 1), B_ext=(0.3, 0.0, 1.0)),
+    "3d_periodic": dict(n=(12, 10, 8), B_ext=(0.2, -0.5, 0.7), E_ext=(0.05, 0.0, -0.1)),
+    "2d_pml": dict(n=(48, 40, 1), B_ext=(0.0, 0.0, 1.0), axion_bc=W._bcs("pml", "pml"),
+                   em_bc=W._bcs("pml", "pml"), pml_cells=6),
+    "2d_outflow_reflect": dict(n=(36, 30, 1), B_ext=(0.0, 0.4, 1.0), axion_bc=W._bcs("outflow", ("reflect", "pml")),
+                               em_bc=W._bcs("pml", ("reflect", "pml")), pml_cells=5),
+    "3d_mixed": dict(n=(14, 12, 10), B_ext=(0.5, 0.2, 0.3), axion_bc=W._bcs("outflow", "periodic", "pml"),
+                     em_bc=W._bcs("pml", "periodic", "reflect"), pml_cells=3),
+}
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_general_fp64_bitwise_vs_oracle(case):
+    axp = axp_mod()
+    grid = periodic_grid(g=0.7, m=1.1, **CASES[case])
+    st = W.random_state(grid, seed=101)
+    og, g = make_pair(grid, st, random_ghosts(grid, 7), kernel=axp.AXP_KERNEL_GENERAL)
+    og.step(6)
+    g.step(6)
+    ref = og.fields()
+    got = g.fields()
+    for k in NAMES:
+        assert np.array_equal(got[k], ref[k]), (case, k, rel(got[k], ref[k]))
+    for (a, s) in random_ghosts(grid, 7):
+        assert np.array_equal(g.read_ghost(a, s, 0).reshape(og.ghost[a][s][0].shape), og.ghost[a][s][0])
+    d, dr = g.diagnostics(), og.diagnostics()
+    for key in ("H_phi", "H_g0", "H_g1", "W", "sum_B1z2", "gauss_l2"):
+        assert d[key] == pytest.approx(dr[key], rel=1e-11, abs=1e-300), key
+    g.close()
+
+
+@pytest.mark.parametrize("case", ["1d_periodic", "2d_pml", "3d_mixed"])
+def test_fp32_split_vs_oracle(case):
+    grid = periodic_grid(g=0.7, m=1.1, **CASES[case])
+    st = W.random_state(grid, seed=102)
+    og = oracle.OracleGrid(grid)
+    og.load(st)
+    for (a, s), (cur, old) in random_ghosts(grid, 8).items():
+        og.set_ghost(a, s, cur, old)
+    g32 = axp_mod().Grid(grid.replace(precision="fp32"))
+    g32.load(st)
+    for (a, s), (cur, old) in random_ghosts(grid, 8).items():
+        g32.write_ghost(a, s, 0, cur)
+        g32.write_ghost(a, s, 1, old)
+    og.step(10)
+    g32.step(10)
+    ref, got = og.fields(), g32.fields()
+    for k in NAMES:
+        assert rel(got[k], ref[k]) < 1e-4, (case, k, rel(got[k], ref[k]))
+    g32.close()
+
+
+def test_inject_laser_and_axion_match_oracle():
+    w = W.pulse_2d(nx=128, ny=64, m=0.3)
+    grid = w.grid.replace(pml_cells=8, axion_bc=W._bcs("outflow", "pml"))
+    og = oracle.OracleGrid(grid)
+    g = axp_mod().Grid(grid)
+    L = w.lasers[0]
+    A = W.AxionSpec(amplitude=0.3, k=(-W.K0, 0.5, 0.0), centre=(1.0, 0.2, 0.0), waist=0.8, length=0.6, speed=0.9,
+                    phase=0.4)
+    for x in (og, g):
+        x.inject_laser(L)
+        x.inject_axion(A)
+    ref, got = og.fields(), g.fields()
+    for k in ("E0z", "B0x", "B0y", "phi_cur", "phi_old"):
+        assert rel(got[k], ref[k]) < 1e-13, k
+    for s in range(2):
+        for lev in range(2):
+            gg = g.read_ghost(0, s, lev).reshape(og.ghost[0][s][lev].shape)
+            assert rel(gg, og.ghost[0][s][lev]) < 1e-13
+    g.close()
+
+
+def test_1d_conversion_run_matches_oracle_fp64_and_fp32():
+    """The 1D photon->axion workload (Nx = 4096, dx = lambda/32, CFL 0.95, g = 1e-4,
+    B0 = 1, amplitude 1e-3) for 2000 steps."""
+    w = W.vacuum_1d(nx=4096)
+    og = oracle.run_workload(w, steps=2000)
+    ref = og.fields()
+    P_ref = og.diagnostics()["P_g2a"]
+    for prec in ("fp64", "fp32"):
+        g = axp_mod().Grid(w.grid.replace(precision=prec))
+        g.inject_laser(w.lasers[0])
+        g.step(2000)
+        got = g.fields()
+        P = g.diagnostics()["P_g2a"]
+        ftol = 1e-12 if prec == "fp64" else 1e-3
+        for k in ("E0y", "B0z", "E1y", "E1z", "B1y", "B1z", "phi_cur"):
+            assert rel(got[k], ref[k]) < ftol, (prec, k, rel(got[k], ref[k]))
+        assert abs(P / P_ref - 1) < (1e-12 if prec == "fp64" else 1e-3), (prec, P, P_ref)
+        g.close()
+
+
+def test_diagnostics_ring_records_every_k_steps():
+    axp = axp_mod()
+    w = W.vacuum_1d(nx=256)
+    g = axp.Grid(w.grid, diag_every=10, diag_capacity=8)
+    g.inject_laser(w.lasers[0])
+    g.step(50)
+    recs = g.read_diagnostics()
+    assert [r["step"] for r in recs] == [10, 20, 30, 40, 50]
+    og = oracle.OracleGrid(w.grid)
+    og.inject_laser(w.lasers[0])
+    og.step(50)
+    assert recs[-1]["P_g2a"] == pytest.approx(og.diagnostics()["P_g2a"], rel=1e-10)
+    g.step(100)  # ring of 8 overwrites; the 8 newest survive
+    recs = g.read_diagnostics()
+    assert [r["step"] for r in recs] == list(range(80, 151, 10))
+    g.close()
+
+
+def test_checkpoint_resume_is_bitwise():
+    w = W.pulse_2d(nx=96, ny=48, m=0.5 * W.K0, g=1e-2)
+    grid = w.grid.replace(pml_cells=8)
+    for prec in ("fp64", "fp32"):
+        gs = grid.replace(precision=prec)
+        a = axp_mod().Grid(gs)
+        a.inject_laser(w.lasers[0])
+        a.step(30)
+        img = a.save_state()
+        a.step(30)
+        ref = a.fields()
+        b = axp_mod().Grid(gs)
+        b.load_state(img)
+        b.step(30)
+        got = b.fields()
+        for k in NAMES:
+            assert np.array_equal(got[k], ref[k]), (prec, k)
+        assert b.step_count == 60
+        a.close()
+        b.close()
+
+
+def test_zero_steps_and_empty_work_are_noops():
+    w = W.vacuum_1d(nx=64)
+    g = axp_mod().Grid(w.grid)
+    g.inject_laser(w.lasers[0])
+    before = g.fields()
+    g.step(0)
+    after = g.fields()
+    for k in NAMES:
+        assert np.array_equal(before[k], after[k])
+    g.close()
+
+
+FUSED_CASES = {
+    "1d_periodic": dict(n=(300, 1, 1), B_ext=(0.0, 1.0, 0.2)),
+    "2d_periodic": dict(n=(300, 40, 1), B_ext=(0.3, 0.0, 1.0)),
+    "2d_pml": dict(n=(260, 70, 1), B_ext=(0.0, 0.0, 1.0), axion_bc=W._bcs("pml", "pml"),
+                   em_bc=W._bcs("pml", "pml"), pml_cells=6),
+    "2d_reflect_pml": dict(n=(140, 90, 1), B_ext=(0.0, 0.4, 1.0), axion_bc=W._bcs("reflect", ("pml", "reflect")),
+                           em_bc=W._bcs("reflect", ("pml", "reflect")), pml_cells=5),
+    "3d_periodic": dict(n=(40, 30, 20), B_ext=(0.2, -0.5, 0.7)),
+    "3d_pml_reflect": dict(n=(36, 24, 22), B_ext=(0.5, 0.2, 0.3), axion_bc=W._bcs("reflect", "periodic", "pml"),
+                           em_bc=W._bcs("reflect", "periodic", "pml"), pml_cells=4),
+}
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("case", sorted(FUSED_CASES))
+def test_fused_vs_oracle(case, prec):
+    """The single-pass kernel against the oracle on random states (several tiles
+    and march chunks with ragged tails), all fields after 12 steps."""
+    axp = axp_mod()
+    grid = periodic_grid(g=0.7, m=1.1, **FUSED_CASES[case]).replace(precision=prec)
+    # 3D in FP64: order-1 fields and the axion only (the order-0 ring of a 3D FP64
+    # tile does not fit in shared memory; such grids run on the general kernels)
+    active = None
+    if case.startswith("3d") and prec == "fp64":
+        active = [n for n in W.FIELD_NAMES if n[1] == "1"]
+    st = W.random_state(grid, seed=303, active=active)
+    og = oracle.OracleGrid(grid.replace(precision="fp64"))
+    og.load(st)
+    g = axp.Grid(grid)
+    g.set_kernel(axp.AXP_KERNEL_FUSED)
+    g.load(st)
+    assert g.kernel_path() == axp.AXP_KERNEL_FUSED
+    og.step(12)
+    g.step(12)
+    ref, got = og.fields(), g.fields()
+    tol = 1e-12 if prec == "fp64" else 1e-4
+    for k in NAMES:
+        assert rel(got[k], ref[k]) < tol, (case, prec, k, rel(got[k], ref[k]))
+    d, dr = g.diagnostics(), og.diagnostics()
+    for key in ("H_phi", "H_g0", "H_g1"):
+        assert d[key] == pytest.approx(dr[key], rel=1e-10 if prec == "fp64" else 1e-4), key
+    g.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_fused_matches_general_over_many_steps(prec):
+    """2D pulse through B_ext with PML: fused and general paths agree after 300 steps,
+    including the in-step diagnostics ring."""
+    axp = axp_mod()
+    w = W.pulse_2d(nx=384, ny=160, m=0.5 * W.K0, g=1e-2, precision=prec)
+    grid = w.grid.replace(pml_cells=10)
+    out = {}
+    for kern in (axp.AXP_KERNEL_GENERAL, axp.AXP_KERNEL_FUSED):
+        g = axp.Grid(grid, diag_every=50, diag_capacity=16)
+        g.set_kernel(kern)
+        g.inject_laser(w.lasers[0])
+        g.step(300)
+        out[kern] = (g.fields(), g.read_diagnostics())
+        g.close()
+    (fa, da), (fb, db) = out[axp.AXP_KERNEL_GENERAL], out[axp.AXP_KERNEL_FUSED]
+    tol = 1e-12 if prec == "fp64" else 2e-4
+    for k in NAMES:
+        assert rel(fb[k], fa[k]) < tol, (prec, k, rel(fb[k], fa[k]))
+    assert [r["step"] for r in da] == [r["step"] for r in db] == [50, 100, 150, 200, 250, 300]
+    for ra, rb in zip(da, db):
+        assert rb["P_g2a"] == pytest.approx(ra["P_g2a"], rel=1e-10 if prec == "fp64" else 1e-3)
