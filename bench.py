@@ -37,7 +37,7 @@ METRIC = "cell-updates/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="axp", choices=["axp", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--ny", type=int, default=NY)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp32", action="store_true")
     return ap.parse_args()
 
 
@@ -179,10 +180,49 @@ def reference_arm(args):
 # GPU arm
 # ---------------------------------------------------------------------------
 
-def algorithmic_bytes_per_cell(grid_spec, active_arrays, phi_words):
-    """Each active array read once and written once; phi: phi_words reads/writes."""
-    e = 8 if grid_spec.precision == "fp64" else 4
-    return (2 * active_arrays + phi_words) * e
+# Algorithmic work of one cell-update of the 2D pulse workload (E0z, B0x, B0y
+# laser; all six order-1 components; axion):
+#  * HBM bytes: every active array read once and written once: 9 field arrays
+#    plus the axion (FP64: phi^{n+1/2}, phi^{n-1/2} read, phi^{n+3/2} written;
+#    FP32 split: phi and its increment read and written).
+#  * FLOPs (FMA = 2): 110 per cell-update, counted from the operations of the
+#    fused scheme for this component set (B update 33, axion + E0 22, axion
+#    current 17, E update 38).
+ACTIVE_ARRAYS = 9
+FLOPS_PER_CELL = 110
+
+
+def bytes_per_cell(prec):
+    e = 8 if prec == "fp64" else 4
+    phi_words = 3 if prec == "fp64" else 4
+    return (2 * ACTIVE_ARRAYS + phi_words) * e
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# FP64 ALU peak of GB300: 2 FP64 FMA per clock per SM (1.25 TFLOP/s nominal,
+# 152 SMs at 2.07 GHz): 2 x 2 x 152 x 2.07e9.
+FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12
+
+
+def timed_run(g, steps, warmup, stream):
+    import torch
+
+    g.step(warmup)
+    g.synchronize()
+    torch.cuda.synchronize()
+    l0 = g.launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    g.step(steps)
+    ev1.record(stream)
+    ev1.synchronize()
+    return ev0.elapsed_time(ev1) / 1e3, g.launches() - l0
 
 
 def gpu_arm(args):
@@ -196,20 +236,21 @@ def gpu_arm(args):
     torch.cuda.set_device(local)
     from paper_2406_16796_gb300 import axp
 
-    prec = args.precision
-    w = workload(args, prec)
-    g = axp.Grid(w.grid)
-    for L in w.lasers:
-        g.inject_laser(L)
-    stream = g.stream
-
     def barrier():
         if world > 1:
             import torch.distributed as dist
 
             dist.barrier()
 
-    # warm-up
+    prec = args.precision
+    w = workload(args, prec)
+    g = axp.Grid(w.grid)
+    for L in w.lasers:
+        g.inject_laser(L)
+    cells = w.grid.cells
+    path = g.kernel_path()
+
+    # headline: K steps of the requested precision, clocks sampled meanwhile
     g.step(args.warmup)
     g.synchronize()
     barrier()
@@ -217,14 +258,7 @@ def gpu_arm(args):
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
-    l0 = g.launches()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    g.step(args.steps)
-    ev1.record(stream)
-    ev1.synchronize()
-    launches = g.launches() - l0
-    el = ev0.elapsed_time(ev1) / 1e3
+    el, launches = timed_run(g, args.steps, 0, g.stream)
     barrier()
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -234,25 +268,28 @@ def gpu_arm(args):
         t = torch.tensor([el], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         el = float(t.item())
-    cells = w.grid.cells
     value = cells * args.steps * world / el
     ms = el / args.steps * 1e3
+    per_launch = el / max(1, launches)  # the fused path launches one kernel per step
 
-    # algorithmic bytes: 2D TM pulse -> E0z, B0x, B0y + six order-1 arrays + axion
-    active = 9
-    phi_words = 3 if prec == "fp64" else 4
-    bpc = algorithmic_bytes_per_cell(w.grid, active, phi_words)
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
+    peaks = load_peaks()
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    achieved = bpc * cells * args.steps / el / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                "traffic": None, "peak_source": peak_src, "kernel": "whole step",
-                "algorithmic_bytes_per_cell": bpc}
+    hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    bpc = bytes_per_cell(prec)
+    hbm_achieved = bpc * cells / per_launch / 1e9
+    hbm = {"achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_achieved / hbm_peak,
+           "peak_source": hbm_src, "algorithmic_bytes_per_cell": bpc}
+    flops = FLOPS_PER_CELL * cells / per_launch / 1e12
+    kern = "k_fused (one launch per step)" if path == axp.AXP_KERNEL_FUSED else "general kernels (7 launches per step)"
+    if prec == "fp64":
+        roofline = {"bound": "alu", "achieved": flops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": flops / FP64_PEAK_TFLOPS, "traffic": None, "kernel": kern,
+                    "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2.07 GHz",
+                    "algorithmic_flops_per_cell": FLOPS_PER_CELL, "hbm": hbm}
+    else:
+        roofline = {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": hbm_achieved / hbm_peak, "traffic": None, "kernel": kern, "peak_source": hbm_src,
+                    "algorithmic_bytes_per_cell": bpc}
 
     # e2e through the C ABI with pinned host buffers: upload the state, run the
     # steps reading the diagnostics record back after each, download the state
@@ -271,9 +308,28 @@ def gpu_arm(args):
         axp.axp_save_state(g.h, host.data_ptr(), nbytes)
         t1 = time.perf_counter()
         diag_bytes = 88
-        e2e = {"value": cells * k / (t1 - t0), "unit": "cell-updates/s", "h2d_bytes_per_step": nbytes / k,
-               "d2h_bytes_per_step": nbytes / k + diag_bytes, "steps": k}
+        e2e = {"value": cells * k * world / (t1 - t0), "unit": "cell-updates/s", "h2d_bytes_per_step": nbytes / k,
+               "d2h_bytes_per_step": nbytes / k + diag_bytes, "steps": k,
+               "what": "state upload from pinned host, k steps each followed by a diagnostics read-back, state download"}
     g.close()
+
+    # the FP32 split storage on the same workload, as a second measurement
+    other = None
+    if prec == "fp64" and not args.no_fp32:
+        w32 = workload(args, "fp32")
+        g32 = axp.Grid(w32.grid)
+        for L in w32.lasers:
+            g32.inject_laser(L)
+        k32 = 4 * args.steps
+        el32, l32 = timed_run(g32, k32, args.warmup, g32.stream)
+        per32 = el32 / max(1, l32)
+        ach = bytes_per_cell("fp32") * cells / per32 / 1e9
+        other = {"precision": "fp32_split", "value": cells * k32 * world / el32, "unit": "cell-updates/s",
+                 "steps": k32, "ms_per_step": el32 / k32 * 1e3,
+                 "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                              "frac": ach / hbm_peak, "peak_source": hbm_src,
+                              "algorithmic_bytes_per_cell": bytes_per_cell("fp32")}}
+        g32.close()
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -287,6 +343,8 @@ def gpu_arm(args):
             "config": {"workload": w.name, "cells": cells, "precision": prec, "parallelism": "replicas",
                        "l2": "inputs larger than L2"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
+    if other:
+        line["fp32_split"] = other
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -75,7 +75,9 @@ fused::Params<T> make_params(axp_grid *g)
         P.per[a] = d.em_bc[a][0] == AXP_BC_PERIODIC;
         for (int s = 0; s < 2; s++) {
             P.axbc[a][s] = d.axion_bc[a][s];
-            if (d.axion_bc[a][s] == AXP_BC_PML || d.em_bc[a][s] == AXP_BC_PML) pml = true;
+            const bool abs = d.axion_bc[a][s] == AXP_BC_PML || d.em_bc[a][s] == AXP_BC_PML;
+            if (abs) pml = true;
+            P.lay[a][s] = abs ? d.pml_cells : 0;
         }
         const double inv = 1.0 / d.d[a];
         P.idx[a] = (T)inv;
@@ -104,7 +106,7 @@ size_t ring_bytes(int set)
 {
     static const int planes[4] = {fused::Lay<MODE, 0, 0>::PLANES, fused::Lay<MODE, 4, 3>::PLANES,
                                   fused::Lay<MODE, 3, 4>::PLANES, fused::Lay<MODE, 7, 7>::PLANES};
-    return (size_t)planes[set] * fused::Tile<T, MODE>::NT * sizeof(T);
+    return ((size_t)planes[set] * fused::Tile<T, MODE>::NT + 4 * fused::Tile<T, MODE>::TX) * sizeof(T);
 }
 
 template <typename T>

@@ -30,6 +30,9 @@
 // general kernels.
 #pragma once
 
+#include <type_traits>
+#include <utility>
+
 #include "device_common.cuh"
 
 namespace axp {
@@ -53,7 +56,7 @@ __host__ __device__ constexpr bool axis_on(int MODE, int a) { return a == 0 || (
 template <int MODE, int E0M, int B0M>
 struct Lay {
     static constexpr bool M = MODE >= 2;
-    static constexpr int DE = M ? 5 : 1, DB = M ? 2 : 1, DPHI = M ? 4 : 1, DPB = M ? 3 : 1, DBH = M ? 3 : 1,
+    static constexpr int DE = M ? 6 : 1, DB = M ? 2 : 1, DPHI = M ? 4 : 1, DPB = M ? 3 : 1, DBH = M ? 3 : 1,
                          DBN = M ? 5 : 1, DMID = M ? 3 : 1, DDT = M ? 3 : 1, DE0N = M ? 3 : 1, DP = M ? 2 : 1;
     __host__ __device__ static constexpr bool e_on(int q) { return q >= 3 || ((E0M >> q) & 1); }  // q: 0-2 order 0, 3-5 order 1
     __host__ __device__ static constexpr bool b_on(int q) { return q >= 3 || ((B0M >> q) & 1); }
@@ -107,6 +110,7 @@ struct Params {
     int axbc[3][2];
     int chunk;
     int has_pml;
+    int lay[3][2];  // cells of absorbing layer at each side (0 where none)
     T idx[3], hidx[3], idx2[3];  // 1/d, 1/(2d), 1/d^2
     T lap_c[3];                  // dt^2/d^2
     T lap_0;                     // two levels: 2 - dt^2 (m^2 + 2 sum 1/d^2); increment: -dt^2 (m^2 + 2 sum 1/d^2)
@@ -114,6 +118,18 @@ struct Params {
     T h, dt, dt2, inv_dt, g, m2;
     T Bext[3];
 };
+
+// Compile-time loop: f(integral_constant<int, I>) for I = 0 .. N-1.
+template <class F, int... I>
+__device__ __forceinline__ void sfor_impl(F &&f, std::integer_sequence<int, I...>)
+{
+    (f(std::integral_constant<int, I>{}), ...);
+}
+template <int N, class F>
+__device__ __forceinline__ void sfor(F &&f)
+{
+    sfor_impl(f, std::make_integer_sequence<int, N>{});
+}
 
 template <int D>
 __device__ __forceinline__ int slot(int p)
@@ -141,23 +157,28 @@ struct Kernel {
     __device__ static constexpr int oy(int, int dy, int) { return MODE == 3 ? dy : 0; }
     __device__ static constexpr int op(int, int dy, int dz) { return MODE == 2 ? dy : (MODE == 3 ? dz : 0); }
 
-    template <int D>
+    // Ring access.  Away from the grid edges (E = false) neighbour offsets stay
+    // within one cell of the tile and land in the guard band around the ring,
+    // so no clamping is needed; near edges (E = true) indices are clamped.
+    template <int D, bool E = true>
     __device__ __forceinline__ T &at(int base, int p, int x, int y)
     {
-        return sm[(base + slot<D>(p)) * NT + clampi(y, 0, TY - 1) * TX + clampi(x, 0, TX - 1)];
+        if (E) return sm[(base + slot<D>(p)) * NT + clampi(y, 0, TY - 1) * TX + clampi(x, 0, TX - 1)];
+        return sm[(base + slot<D>(p)) * NT + y * TX + x];
     }
 
     // plain ring read (E/B-type quantities) at generic offset
-    template <int D>
+    template <int D, bool E = true>
     __device__ __forceinline__ T rd(int base, int p, int dx, int dy, int dz)
     {
-        return at<D>(base, p + op(dx, dy, dz), tx + ox(dx, dy, dz), ty + oy(dx, dy, dz));
+        return at<D, E>(base, p + op(dx, dy, dz), tx + ox(dx, dy, dz), ty + oy(dx, dy, dz));
     }
 
-    // axion-type ring read with the ghost rules applied at read time
-    template <int D>
+    // axion-type ring read; near edges the ghost rules are applied at read time
+    template <int D, bool E = true>
     __device__ __forceinline__ T rdphi(int base, int p, int dx, int dy, int dz)
     {
+        if (!E) return rd<D, false>(base, p, dx, dy, dz);
         int c[3] = {gx + ox(dx, dy, dz), gy + oy(dx, dy, dz), p + op(dx, dy, dz)};
         const int ax_of[3] = {0, 1, MA};
         const int lim[3] = {P.n[0], MODE == 3 ? P.n[1] : 1, nm};
@@ -232,72 +253,91 @@ struct Kernel {
         return ((T(1) - sig * P.h / T(2)) * F + P.h * X) / (T(1) + sig * P.h / T(2));
     }
 
-    // 4-point average of an order-0 B component to the cell centre (Sec. 2.3),
-    // invariant axes folded (their two samples coincide), plus the background.
-    template <int D>
-    __device__ __forceinline__ T bbar(int base_of_a, bool on, int a, int p)
+    // 4-point average of order-0 B component A to the cell centre (Sec. 2.3);
+    // an invariant axis folds its two coinciding samples.  Plus the background.
+    template <int D, bool E, int A>
+    __device__ __forceinline__ T bbar_c(int base, int p)
     {
-        if (!on) return P.Bext[a];
-        const int b = (a + 1) % 3, c = (a + 2) % 3;
-        const bool ab = axis_on(MODE, b), ac = axis_on(MODE, c);
-        const int ub[3] = {b == 0, b == 1, b == 2}, uc[3] = {c == 0, c == 1, c == 2};
-        const T B0 = rd<D>(base_of_a, p, 0, 0, 0);
+        constexpr int b = (A + 1) % 3, c = (A + 2) % 3;
+        constexpr bool ab = axis_on(MODE, b), ac = axis_on(MODE, c);
+        constexpr int bx = b == 0, by = b == 1, bz = b == 2, cx = c == 0, cy = c == 1, cz = c == 2;
+        const T B0 = rd<D, E>(base, p, 0, 0, 0);
         T s;
-        if (ab && ac) {
-            s = T(0.25) * (((B0 + rd<D>(base_of_a, p, -uc[0], -uc[1], -uc[2])) +
-                            rd<D>(base_of_a, p, -ub[0], -ub[1], -ub[2])) +
-                           rd<D>(base_of_a, p, -ub[0] - uc[0], -ub[1] - uc[1], -ub[2] - uc[2]));
-        } else if (ab) {
-            s = T(0.5) * (B0 + rd<D>(base_of_a, p, -ub[0], -ub[1], -ub[2]));
-        } else if (ac) {
-            s = T(0.5) * (B0 + rd<D>(base_of_a, p, -uc[0], -uc[1], -uc[2]));
-        } else {
+        if constexpr (ab && ac)
+            s = T(0.25) * (((B0 + rd<D, E>(base, p, -cx, -cy, -cz)) + rd<D, E>(base, p, -bx, -by, -bz)) +
+                           rd<D, E>(base, p, -bx - cx, -by - cy, -bz - cz));
+        else if constexpr (ab)
+            s = T(0.5) * (B0 + rd<D, E>(base, p, -bx, -by, -bz));
+        else if constexpr (ac)
+            s = T(0.5) * (B0 + rd<D, E>(base, p, -cx, -cy, -cz));
+        else
             s = B0;
-        }
-        return s + P.Bext[a];
+        return s + P.Bext[A];
     }
 
-    // 2-point average of an order-0 E component to the cell centre
-    template <int D>
-    __device__ __forceinline__ T ebar(int base_of_a, int a, int p)
+    // 2-point average of order-0 E component A to the cell centre
+    template <int D, bool E, int A>
+    __device__ __forceinline__ T ebar_c(int base, int p)
     {
-        const T E0 = rd<D>(base_of_a, p, 0, 0, 0);
-        if (!axis_on(MODE, a)) return E0;
-        return T(0.5) * (E0 + rd<D>(base_of_a, p, -(a == 0), -(a == 1), -(a == 2)));
+        const T E0 = rd<D, E>(base, p, 0, 0, 0);
+        if constexpr (!axis_on(MODE, A)) return E0;
+        else return T(0.5) * (E0 + rd<D, E>(base, p, -(A == 0), -(A == 1), -(A == 2)));
     }
 
-    // (curl B)_a at the E_a location from the B^{n+1} ring, backward differences;
-    // `o` selects the order.  Returns false when the component has no term.
-    __device__ __forceinline__ bool curl_b_new(int o, int a, int p, T *out)
+    // (curl B)_A at the E_A location from the B^{n+1} ring of order O (backward differences)
+    template <int O, int A>
+    __host__ __device__ static constexpr bool curl_b_t1()
     {
-        const int b = (a + 1) % 3, c = (a + 2) % 3;
-        bool any = false;
+        return axis_on(MODE, (A + 1) % 3) && L::b_on(3 * O + (A + 2) % 3);
+    }
+    template <int O, int A>
+    __host__ __device__ static constexpr bool curl_b_t2()
+    {
+        return axis_on(MODE, (A + 2) % 3) && L::b_on(3 * O + (A + 1) % 3);
+    }
+    template <bool E, int O, int A>
+    __device__ __forceinline__ T curl_b_new(int p)
+    {
+        constexpr int b = (A + 1) % 3, c = (A + 2) % 3;
         T v = T(0);
-        if (axis_on(MODE, b) && L::b_on(3 * o + c)) {
-            const int base = L::base_BN(3 * o + c);
-            v = (rd<L::DBN>(base, p, 0, 0, 0) - rd<L::DBN>(base, p, -(b == 0), -(b == 1), -(b == 2))) * P.idx[b];
-            any = true;
+        if constexpr (curl_b_t1<O, A>()) {
+            constexpr int base = L::base_BN(3 * O + c);
+            v = (rd<L::DBN, E>(base, p, 0, 0, 0) - rd<L::DBN, E>(base, p, -(b == 0), -(b == 1), -(b == 2))) * P.idx[b];
         }
-        if (axis_on(MODE, c) && L::b_on(3 * o + b)) {
-            const int base = L::base_BN(3 * o + b);
-            const T t = (rd<L::DBN>(base, p, 0, 0, 0) - rd<L::DBN>(base, p, -(c == 0), -(c == 1), -(c == 2))) * P.idx[c];
-            v = any ? v - t : -t;
-            any = true;
+        if constexpr (curl_b_t2<O, A>()) {
+            constexpr int base = L::base_BN(3 * O + b);
+            const T t = (rd<L::DBN, E>(base, p, 0, 0, 0) - rd<L::DBN, E>(base, p, -(c == 0), -(c == 1), -(c == 2))) * P.idx[c];
+            if constexpr (curl_b_t1<O, A>()) v = v - t;
+            else v = -t;
         }
-        *out = v;
-        return any;
+        return v;
     }
 
-    __device__ void load(int t)
+    // Inputs of one plane: fetched into registers one iteration ahead (so the
+    // HBM latency overlaps the compute stages), then committed to the rings.
+    T pre[14];
+
+    __device__ __forceinline__ void prefetch(int t)
     {
         const int64_t gi = gidx(t);
-#pragma unroll
-        for (int q = 0; q < 6; q++) {
-            if (L::e_on(q)) at<L::DE>(L::base_E(q), t, tx, ty) = gi >= 0 ? P.Ein[q][gi] : T(0);
-            if (L::b_on(q)) at<L::DB>(L::base_B(q), t, tx, ty) = gi >= 0 ? P.Bin[q][gi] : T(0);
-        }
-        at<L::DPHI>(L::PHI, t, tx, ty) = gi >= 0 ? P.phi[gi] : T(0);
-        at<L::DPB>(L::PB, t, tx, ty) = gi >= 0 ? P.phib[gi] : T(0);
+        sfor<6>([&](auto Q) {
+            constexpr int q = decltype(Q)::value;
+            if constexpr (L::e_on(q)) pre[q] = gi >= 0 ? __ldg(P.Ein[q] + gi) : T(0);
+            if constexpr (L::b_on(q)) pre[6 + q] = gi >= 0 ? __ldg(P.Bin[q] + gi) : T(0);
+        });
+        pre[12] = gi >= 0 ? __ldg(P.phi + gi) : T(0);
+        pre[13] = gi >= 0 ? __ldg(P.phib + gi) : T(0);
+    }
+
+    __device__ __forceinline__ void commit(int t)
+    {
+        sfor<6>([&](auto Q) {
+            constexpr int q = decltype(Q)::value;
+            if constexpr (L::e_on(q)) at<L::DE, false>(L::base_E(q), t, tx, ty) = pre[q];
+            if constexpr (L::b_on(q)) at<L::DB, false>(L::base_B(q), t, tx, ty) = pre[6 + q];
+        });
+        at<L::DPHI, false>(L::PHI, t, tx, ty) = pre[12];
+        at<L::DPB, false>(L::PB, t, tx, ty) = pre[13];
     }
 
     __device__ __forceinline__ bool out_ok(int p, int m0, int m1) const
@@ -311,84 +351,96 @@ struct Kernel {
     }
 
     // Stage 1: B^{n+1/2}, B^{n+1} on plane p
+    // Stage 1: B^{n+1/2}, B^{n+1} on plane p
+    template <bool E>
     __device__ void stage1(int p, int m0, int m1)
     {
-        const bool in = inside(p);
-        const T sig = (in && P.has_pml) ? sigma(P.sig_em, p) : T(0);
+        const bool in = !E || inside(p);
+        const T sig = (E && in && P.has_pml) ? sigma(P.sig_em, p) : T(0);
         const bool wr = out_ok(p, m0, m1);
         const int64_t gi = wr ? gidx(p) : -1;
-#pragma unroll
-        for (int o = 0; o < 2; o++)
-#pragma unroll
-            for (int a = 0; a < 3; a++) {
-                const int q = 3 * o + a;
-                if (!L::b_on(q)) continue;
-                const int b = (a + 1) % 3, c = (a + 2) % 3;
+        sfor<6>([&](auto Q) {
+            constexpr int q = decltype(Q)::value;
+            if constexpr (L::b_on(q)) {
+                constexpr int o = q / 3, a = q % 3, b = (a + 1) % 3, c = (a + 2) % 3;
                 // (curl E)_a = D_b E_c - D_c E_b, forward differences
-                bool any = false;
+                constexpr bool t1 = axis_on(MODE, b) && L::e_on(3 * o + c);
+                constexpr bool t2 = axis_on(MODE, c) && L::e_on(3 * o + b);
                 T cE = T(0);
-                if (axis_on(MODE, b) && L::e_on(3 * o + c)) {
-                    const int base = L::base_E(3 * o + c);
-                    cE = (rd<L::DE>(base, p, b == 0, b == 1, b == 2) - rd<L::DE>(base, p, 0, 0, 0)) * P.idx[b];
-                    any = true;
+                if constexpr (t1) {
+                    constexpr int base = L::base_E(3 * o + c);
+                    cE = (rd<L::DE, E>(base, p, b == 0, b == 1, b == 2) - rd<L::DE, E>(base, p, 0, 0, 0)) * P.idx[b];
                 }
-                if (axis_on(MODE, c) && L::e_on(3 * o + b)) {
-                    const int base = L::base_E(3 * o + b);
-                    const T t = (rd<L::DE>(base, p, c == 0, c == 1, c == 2) - rd<L::DE>(base, p, 0, 0, 0)) * P.idx[c];
-                    cE = any ? cE - t : -t;
-                    any = true;
+                if constexpr (t2) {
+                    constexpr int base = L::base_E(3 * o + b);
+                    const T t = (rd<L::DE, E>(base, p, c == 0, c == 1, c == 2) - rd<L::DE, E>(base, p, 0, 0, 0)) * P.idx[c];
+                    if constexpr (t1) cE = cE - t;
+                    else cE = -t;
                 }
-                const T Bv = rd<L::DB>(L::base_B(q), p, 0, 0, 0);
+                const T Bv = rd<L::DB, E>(L::base_B(q), p, 0, 0, 0);
                 T Bh, Bn;
                 if (!in) {
                     Bh = T(0);
                     Bn = T(0);
                 } else if (sig == T(0)) {
-                    Bh = any ? fma(-P.h, cE, Bv) : Bv;
-                    Bn = any ? fma(-P.h, cE, Bh) : Bh;
+                    if constexpr (t1 || t2) {
+                        Bh = fma(-P.h, cE, Bv);
+                        Bn = fma(-P.h, cE, Bh);
+                    } else {
+                        Bh = Bv;
+                        Bn = Bv;
+                    }
                 } else {
                     Bh = half(Bv, -cE, sig);
                     Bn = half(Bh, -cE, sig);
                 }
-                if (o == 0) at<L::DBH>(L::base_BH(a), p, tx, ty) = Bh;
-                at<L::DBN>(L::base_BN(q), p, tx, ty) = Bn;
+                if constexpr (o == 0) at<L::DBH, false>(L::base_BH(a), p, tx, ty) = Bh;
+                at<L::DBN, false>(L::base_BN(q), p, tx, ty) = Bn;
                 if (gi >= 0) P.Bout[q][gi] = Bn;
             }
+        });
     }
 
     // Stage 2: source, axion leapfrog, phi^{n+1}, D_t phi^{n+1}, E0^{n+1} on plane p
+    template <bool E>
     __device__ void stage2(int p, int m0, int m1)
     {
-        const bool in = inside(p);
+        const bool in = !E || inside(p);
         // S^{n+1/2} / g = Ebar0 . Bbar0 with B0^{n+1/2}
+        constexpr bool hasS = E0M != 0;
         T S = T(0);
-        bool hasS = false;
-#pragma unroll
-        for (int a = 0; a < 3; a++) {
-            if (!((E0M >> a) & 1)) continue;
-            const T e = ebar<L::DE>(L::base_E(a), a, p);
-            const T bb = bbar<L::DBH>(((B0M >> a) & 1) ? L::base_BH(a) : 0, (B0M >> a) & 1, a, p);
-            S = hasS ? fma(e, bb, S) : e * bb;
-            hasS = true;
-        }
-        const T ph = rdphi<L::DPHI>(L::PHI, p, 0, 0, 0);
-        const T pb = rd<L::DPB>(L::PB, p, 0, 0, 0);
+        sfor<3>([&](auto A) {
+            constexpr int a = decltype(A)::value;
+            if constexpr ((E0M >> a) & 1) {
+                const T e = ebar_c<L::DE, E, a>(L::base_E(a), p);
+                T bb;
+                if constexpr ((B0M >> a) & 1) bb = bbar_c<L::DBH, E, a>(L::base_BH(a), p);
+                else bb = P.Bext[a];
+                if constexpr ((E0M & ((1 << a) - 1)) == 0) S = e * bb;
+                else S = fma(e, bb, S);
+            }
+        });
+        const T ph = rdphi<L::DPHI, E>(L::PHI, p, 0, 0, 0);
+        const T pb = rd<L::DPB, E>(L::PB, p, 0, 0, 0);
         T sp[3];
-#pragma unroll
-        for (int a = 0; a < 3; a++) {
-            sp[a] = T(0);
-            if (!axis_on(MODE, a)) continue;
-            sp[a] = rdphi<L::DPHI>(L::PHI, p, a == 0, a == 1, a == 2) + rdphi<L::DPHI>(L::PHI, p, -(a == 0), -(a == 1), -(a == 2));
-        }
-        const T sig = (in && P.has_pml) ? sigma(P.sig_ax, p) : T(0);
+        sfor<3>([&](auto A) {
+            constexpr int a = decltype(A)::value;
+            if constexpr (axis_on(MODE, a))
+                sp[a] = rdphi<L::DPHI, E>(L::PHI, p, a == 0, a == 1, a == 2) +
+                        rdphi<L::DPHI, E>(L::PHI, p, -(a == 0), -(a == 1), -(a == 2));
+            else
+                sp[a] = T(0);
+        });
+        const T sig = (E && in && P.has_pml) ? sigma(P.sig_ax, p) : T(0);
         T nw, pin = T(0);
         if (sig == T(0)) {
             T acc = INCR ? fma(P.lap_0, ph, pb) : fma(P.lap_0, ph, -pb);
-#pragma unroll
-            for (int a = 0; a < 3; a++)
-                if (axis_on(MODE, a)) acc = fma(P.lap_c[a], sp[a], acc);
-            if (hasS) acc = fma(P.dt2g, S, acc);
-            if (INCR) {
+            sfor<3>([&](auto A) {
+                constexpr int a = decltype(A)::value;
+                if constexpr (axis_on(MODE, a)) acc = fma(P.lap_c[a], sp[a], acc);
+            });
+            if constexpr (hasS) acc = fma(P.dt2g, S, acc);
+            if constexpr (INCR) {
                 pin = acc;
                 nw = ph + pin;
             } else {
@@ -396,11 +448,12 @@ struct Kernel {
             }
         } else {
             T lap = T(0);
-#pragma unroll
-            for (int a = 0; a < 3; a++)
-                if (axis_on(MODE, a)) lap = lap + (sp[a] - T(2) * ph) * P.idx2[a];
+            sfor<3>([&](auto A) {
+                constexpr int a = decltype(A)::value;
+                if constexpr (axis_on(MODE, a)) lap = lap + (sp[a] - T(2) * ph) * P.idx2[a];
+            });
             const T Y = ((P.g * S - P.m2 * ph) + lap) - sig * sig * ph;
-            if (INCR) {
+            if constexpr (INCR) {
                 pin = (P.dt2 * Y + (T(1) - sig * P.dt) * pb) / (T(1) + sig * P.dt);
                 nw = ph + pin;
             } else {
@@ -408,97 +461,123 @@ struct Kernel {
             }
         }
         T mid, dtv;
-        if (INCR) {
+        if constexpr (INCR) {
             mid = fma(T(0.5), pin, ph);
             dtv = pin * P.inv_dt;
         } else {
             mid = T(0.5) * (nw + ph);
             dtv = (nw - ph) * P.inv_dt;
         }
-        at<L::DMID>(L::MID, p, tx, ty) = mid;
-        at<L::DDT>(L::DTQ, p, tx, ty) = dtv;
+        at<L::DMID, false>(L::MID, p, tx, ty) = mid;
+        at<L::DDT, false>(L::DTQ, p, tx, ty) = dtv;
         if (out_ok(p, m0, m1)) {
             const int64_t gi = gidx(p);
             P.phi_out[gi] = nw;
-            if (INCR) P.phib_out[gi] = pin;
+            if constexpr (INCR) P.phib_out[gi] = pin;
         }
         // E0^{n+1}
-        const T sg = (in && P.has_pml) ? sigma(P.sig_em, p) : T(0);
-#pragma unroll
-        for (int a = 0; a < 3; a++) {
-            if (!((E0M >> a) & 1)) continue;
-            T cB;
-            const bool any = curl_b_new(0, a, p, &cB);
-            const T Eh = rd<L::DE>(L::base_E(a), p, 0, 0, 0);
-            T En;
-            if (!in) En = T(0);
-            else if (sg == T(0)) En = any ? fma(P.h, cB, Eh) : Eh;
-            else En = half(Eh, cB, sg);
-            at<L::DE0N>(L::base_E0N(a), p, tx, ty) = En;
-        }
+        const T sg = (E && in && P.has_pml) ? sigma(P.sig_em, p) : T(0);
+        sfor<3>([&](auto A) {
+            constexpr int a = decltype(A)::value;
+            if constexpr ((E0M >> a) & 1) {
+                constexpr bool any = curl_b_t1<0, a>() || curl_b_t2<0, a>();
+                const T cB = curl_b_new<E, 0, a>(p);
+                const T Eh = rd<L::DE, E>(L::base_E(a), p, 0, 0, 0);
+                T En;
+                if (!in) En = T(0);
+                else if (sg == T(0)) En = any ? fma(P.h, cB, Eh) : Eh;
+                else En = half(Eh, cB, sg);
+                at<L::DE0N, false>(L::base_E0N(a), p, tx, ty) = En;
+            }
+        });
     }
 
     // Stage 3: P^{n+1} at cell centres on plane p
+    template <bool E>
     __device__ void stage3(int p)
     {
-        const T Dt = rdphi<L::DDT>(L::DTQ, p, 0, 0, 0);
-#pragma unroll
-        for (int a = 0; a < 3; a++) {
-            const int b = (a + 1) % 3, c = (a + 2) % 3;
-            const bool bon = (B0M >> a) & 1;
-            T Pa = Dt * bbar<L::DBN>(bon ? L::base_BN(a) : 0, bon, a, p);
+        const T Dt = rdphi<L::DDT, E>(L::DTQ, p, 0, 0, 0);
+        sfor<3>([&](auto A) {
+            constexpr int a = decltype(A)::value, b = (a + 1) % 3, c = (a + 2) % 3;
+            T Pa;
+            if constexpr ((B0M >> a) & 1) Pa = Dt * bbar_c<L::DBN, E, a>(L::base_BN(a), p);
+            else Pa = Dt * P.Bext[a];
             // -(Ebar_b dphi_c - Ebar_c dphi_b)
-            if (((E0M >> b) & 1) && axis_on(MODE, c)) {
-                const T eb = ebar<L::DE0N>(L::base_E0N(b), b, p);
-                const T dc = (rdphi<L::DMID>(L::MID, p, c == 0, c == 1, c == 2) -
-                              rdphi<L::DMID>(L::MID, p, -(c == 0), -(c == 1), -(c == 2))) * P.hidx[c];
+            if constexpr (((E0M >> b) & 1) && axis_on(MODE, c)) {
+                const T eb = ebar_c<L::DE0N, E, b>(L::base_E0N(b), p);
+                const T dc = (rdphi<L::DMID, E>(L::MID, p, c == 0, c == 1, c == 2) -
+                              rdphi<L::DMID, E>(L::MID, p, -(c == 0), -(c == 1), -(c == 2))) * P.hidx[c];
                 Pa = fma(-eb, dc, Pa);
             }
-            if (((E0M >> c) & 1) && axis_on(MODE, b)) {
-                const T ec = ebar<L::DE0N>(L::base_E0N(c), c, p);
-                const T db = (rdphi<L::DMID>(L::MID, p, b == 0, b == 1, b == 2) -
-                              rdphi<L::DMID>(L::MID, p, -(b == 0), -(b == 1), -(b == 2))) * P.hidx[b];
+            if constexpr (((E0M >> c) & 1) && axis_on(MODE, b)) {
+                const T ec = ebar_c<L::DE0N, E, c>(L::base_E0N(c), p);
+                const T db = (rdphi<L::DMID, E>(L::MID, p, b == 0, b == 1, b == 2) -
+                              rdphi<L::DMID, E>(L::MID, p, -(b == 0), -(b == 1), -(b == 2))) * P.hidx[b];
                 Pa = fma(ec, db, Pa);
             }
-            at<L::DP>(L::base_P(a), p, tx, ty) = Pa;
-        }
+            at<L::DP, false>(L::base_P(a), p, tx, ty) = Pa;
+        });
     }
 
     // Stage 4: J^{n+1} and E^{n+3/2} on plane p
+    template <bool E>
     __device__ void stage4(int p, int m0, int m1)
     {
-        const bool in = inside(p);
-        const bool wr = out_ok(p, m0, m1);
+        const bool in = !E || inside(p);
+        const bool wr = out_ok(p, m0, m1) && in;
         const int64_t gi = wr ? gidx(p) : -1;
-        const T sg = (in && P.has_pml) ? sigma(P.sig_em, p) : T(0);
-#pragma unroll
-        for (int a = 0; a < 3; a++) {
-            const int base = L::base_P(a);
-            T J = rd<L::DP>(base, p, 0, 0, 0);
-            if (axis_on(MODE, a)) J = T(0.5) * (J + rd<L::DP>(base, p, a == 0, a == 1, a == 2));
-            T cB;
-            const bool any = curl_b_new(1, a, p, &cB);
-            const T X = any ? fma(-P.g, J, cB) : -P.g * J;
-            const T Eh = rd<L::DE>(L::base_E(3 + a), p, 0, 0, 0);
-            T E;
-            if (sg == T(0)) {
-                E = fma(P.h, X, fma(P.h, X, Eh));
-            } else {
-                E = half(half(Eh, X, sg), X, sg);
+        const T sg = (E && in && P.has_pml) ? sigma(P.sig_em, p) : T(0);
+        sfor<3>([&](auto A) {
+            constexpr int a = decltype(A)::value;
+            constexpr int base = L::base_P(a);
+            T J = rd<L::DP, E>(base, p, 0, 0, 0);
+            if constexpr (axis_on(MODE, a)) J = T(0.5) * (J + rd<L::DP, E>(base, p, a == 0, a == 1, a == 2));
+            constexpr bool any = curl_b_t1<1, a>() || curl_b_t2<1, a>();
+            T X;
+            if constexpr (any) X = fma(-P.g, J, curl_b_new<E, 1, a>(p));
+            else X = -P.g * J;
+            const T Eh = rd<L::DE, E>(L::base_E(3 + a), p, 0, 0, 0);
+            T Enew;
+            if (sg == T(0)) Enew = fma(P.h, X, fma(P.h, X, Eh));
+            else Enew = half(half(Eh, X, sg), X, sg);
+            if (gi >= 0) P.Eout[3 + a][gi] = Enew;
+        });
+        sfor<3>([&](auto A) {
+            constexpr int a = decltype(A)::value;
+            if constexpr ((E0M >> a) & 1) {
+                constexpr bool any = curl_b_t1<0, a>() || curl_b_t2<0, a>();
+                const T cB = curl_b_new<E, 0, a>(p);
+                const T En = rd<L::DE0N, E>(L::base_E0N(a), p, 0, 0, 0);
+                T Enew;
+                if (sg == T(0)) Enew = any ? fma(P.h, cB, En) : En;
+                else Enew = half(En, cB, sg);
+                if (gi >= 0) P.Eout[a][gi] = Enew;
             }
-            if (gi >= 0 && in) P.Eout[3 + a][gi] = E;
+        });
+    }
+
+    // Does the transverse tile keep one cell clear of the grid edges and of
+    // every absorbing layer (so that no boundary rule applies inside it)?
+    __device__ bool tile_interior() const
+    {
+        const int gx0 = gx - tx, gx1 = gx0 + TX - 1;
+        if (!P.per[0] && (gx0 - 1 < P.lay[0][0] || gx1 + 1 > P.n[0] - 1 - P.lay[0][1])) return false;
+        if (MODE == 3) {
+            const int gy0 = gy - ty, gy1 = gy0 + TY - 1;
+            if (!P.per[1] && (gy0 - 1 < P.lay[1][0] || gy1 + 1 > P.n[1] - 1 - P.lay[1][1])) return false;
         }
-#pragma unroll
-        for (int a = 0; a < 3; a++) {
-            if (!((E0M >> a) & 1)) continue;
-            T cB;
-            const bool any = curl_b_new(0, a, p, &cB);
-            const T En = rd<L::DE0N>(L::base_E0N(a), p, 0, 0, 0);
-            T E;
-            if (sg == T(0)) E = any ? fma(P.h, cB, En) : En;
-            else E = half(En, cB, sg);
-            if (gi >= 0 && in) P.Eout[a][gi] = E;
-        }
+        return true;
+    }
+
+    template <bool E>
+    __device__ __forceinline__ void stages(int t, int m0, int m1)
+    {
+        if (t - 1 >= m0 - 2) stage1<E>(t - 1, m0, m1);
+        __syncthreads();
+        if (t - 2 >= m0 - 1) stage2<E>(t - 2, m0, m1);
+        __syncthreads();
+        if (t - 3 >= m0) stage3<E>(t - 3);
+        __syncthreads();
     }
 
     __device__ void run()
@@ -509,30 +588,39 @@ struct Kernel {
         gy = MODE == 3 ? (int)blockIdx.y * TL::VY - HL + ty : 0;
         nm = MODE == 3 ? P.n[2] : (MODE == 2 ? P.n[1] : 1);
         if (!TL::MARCH) {
-            load(0);
+            prefetch(0);
+            commit(0);
             __syncthreads();
-            stage1(0, 0, 1);
+            stage1<true>(0, 0, 1);
             __syncthreads();
-            stage2(0, 0, 1);
+            stage2<true>(0, 0, 1);
             __syncthreads();
-            stage3(0);
+            stage3<true>(0);
             __syncthreads();
-            stage4(0, 0, 1);
+            stage4<true>(0, 0, 1);
             return;
         }
         const int chunk_id = MODE == 3 ? blockIdx.z : blockIdx.y;
         const int m0 = chunk_id * P.chunk;
         const int m1 = min(nm, m0 + P.chunk);
-        for (int t = m0 - 2; t <= m1 + 3; ++t) {
-            load(t);
-            __syncthreads();
-            if (t - 1 >= m0 - 2) stage1(t - 1, m0, m1);
-            __syncthreads();
-            if (t - 2 >= m0 - 1) stage2(t - 2, m0, m1);
-            __syncthreads();
-            if (t - 3 >= m0) stage3(t - 3);
-            __syncthreads();
-            if (t - 4 >= m0 && t - 4 < m1) stage4(t - 4, m0, m1);
+        const bool tin = tile_interior();
+        const bool mper = P.per[MA];
+        const int mlo = P.lay[MA][0], mhi = nm - 1 - P.lay[MA][1];
+        const int t0 = m0 - 2, t1 = m1 + 3;
+        prefetch(t0);
+        commit(t0);
+        __syncthreads();
+        for (int t = t0; t <= t1; ++t) {
+            if (t + 1 <= t1) prefetch(t + 1);
+            // this iteration reads planes t-5 .. t; interior iff all of them are
+            const bool edge = !tin || (!mper && (t - 5 - 1 < mlo || t + 1 > mhi));
+            if (edge) stages<true>(t, m0, m1);
+            else stages<false>(t, m0, m1);
+            if (t + 1 <= t1) commit(t + 1);
+            if (t - 4 >= m0 && t - 4 < m1) {
+                if (edge) stage4<true>(t - 4, m0, m1);
+                else stage4<false>(t - 4, m0, m1);
+            }
             __syncthreads();
         }
     }
@@ -542,14 +630,17 @@ template <typename T, bool INCR, int MODE, int E0M, int B0M>
 __global__ void __launch_bounds__(Tile<T, MODE>::NT) k_fused(Params<T> P)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    T *sm = reinterpret_cast<T *>(smraw);
+    // the rings sit between two guard bands of kGuard elements, which absorb the
+    // one-cell neighbour reads of the tile's outermost cells
+    constexpr int guard = 2 * Tile<T, MODE>::TX;
+    constexpr int total = Lay<MODE, E0M, B0M>::PLANES * Tile<T, MODE>::NT + 2 * guard;
+    T *base = reinterpret_cast<T *>(smraw);
     // start from a defined ring: slots read before their first write only feed
     // halo/warm-up cells, which must still hold finite values
-    constexpr int total = Lay<MODE, E0M, B0M>::PLANES * Tile<T, MODE>::NT;
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-    for (int i = tid; i < total; i += Tile<T, MODE>::NT) sm[i] = T(0);
+    for (int i = tid; i < total; i += Tile<T, MODE>::NT) base[i] = T(0);
     __syncthreads();
-    Kernel<T, INCR, MODE, E0M, B0M> K(P, sm);
+    Kernel<T, INCR, MODE, E0M, B0M> K(P, base + guard);
     K.run();
 }
 
@@ -558,7 +649,7 @@ template <typename T, bool INCR, int MODE, int E0M, int B0M>
 cudaError_t launch(const Params<T> &P, int nchunks, cudaStream_t stream, int *occupancy)
 {
     using TL = Tile<T, MODE>;
-    constexpr size_t smem = (size_t)Lay<MODE, E0M, B0M>::PLANES * TL::NT * sizeof(T);
+    constexpr size_t smem = ((size_t)Lay<MODE, E0M, B0M>::PLANES * TL::NT + 4 * TL::TX) * sizeof(T);
     static bool configured = false;
     static int occ = 0;
     auto kern = k_fused<T, INCR, MODE, E0M, B0M>;
