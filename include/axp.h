@@ -192,6 +192,31 @@ axp_status axp_read_diagnostics(axp_grid *grid, axp_diag *out, int64_t max, int6
 /* Diagnostics of the present state, computed now.  Synchronises. */
 axp_status axp_compute_diagnostics(axp_grid *grid, axp_diag *out);
 
+/* Diagnostics of FP64 fields the caller already holds, with no device
+ * allocation at all.  The paper has no counterpart: this entry point serves
+ * callers that cannot call cudaMalloc -- code whose fields live in memory
+ * another allocator owns and that may not create an axp workspace, for
+ * instance inside a latency-critical loop where cudaMalloc/cudaFree would
+ * implicitly synchronise the device, or in a process whose device memory is
+ * entirely handed to another framework's pool.
+ *   desc        grid description (precision must be AXP_FP64; no outflow faces)
+ *   dev_fields  14 device pointers, each n0*n1*n2 doubles in the layout above:
+ *               E0x E0y E0z B0x B0y B0z E1x E1y E1z B1x B1y B1z,
+ *               phi^{n+1/2}, phi^{n-1/2}; E and B at the integer time `step`
+ *   B_ext, E_ext  uniform background fields
+ *   host_out    receives the record (same definitions as axp_compute_diagnostics)
+ * The reduction's scratch is a fixed array inside the library, so grids are
+ * limited to 8,388,608 cells (AXP_E_INVAL beyond, with a message on stderr).
+ * The array lives on every GPU that loads the library until the process exits.
+ * The first call on a device looks up the array's device address; make that
+ * first call before any stream capture.  Every call shares the array and
+ * rewrites what it uses, so results never depend on earlier calls, but calls
+ * that overlap on the GPU (from other threads or streams) race.  The call
+ * synchronises `cuda_stream` before returning. */
+axp_status axp_diagnostics_noalloc(const axp_grid_desc *desc, const double *const dev_fields[14],
+                                   const double B_ext[3], const double E_ext[3], int64_t step, void *cuda_stream,
+                                   axp_diag *host_out);
+
 /* Copy one field to/from host memory as n0*n1*n2 doubles (bytes must equal
  * 8 * cells).  Synchronises.  Writing marks the cached axion current stale. */
 axp_status axp_read_field(axp_grid *grid, int32_t which, double *host_dst, size_t bytes);

@@ -81,6 +81,8 @@ def lib():
             "axp_step": ([_P, C.c_int64], C.c_int),
             "axp_read_diagnostics": ([_P, C.POINTER(axp_diag), C.c_int64, C.POINTER(C.c_int64)], C.c_int),
             "axp_compute_diagnostics": ([_P, C.POINTER(axp_diag)], C.c_int),
+            "axp_diagnostics_noalloc": ([C.POINTER(axp_grid_desc), C.POINTER(C.c_void_p), C.POINTER(C.c_double),
+                                         C.POINTER(C.c_double), C.c_int64, _P, C.POINTER(axp_diag)], C.c_int),
             "axp_read_field": ([_P, C.c_int32, C.POINTER(C.c_double), C.c_size_t], C.c_int),
             "axp_write_field": ([_P, C.c_int32, C.POINTER(C.c_double), C.c_size_t], C.c_int),
             "axp_read_ghost": ([_P, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_double), C.c_size_t], C.c_int),
@@ -165,6 +167,16 @@ def axp_read_diagnostics(h, max_records=4096):
 def axp_compute_diagnostics(h):
     d = axp_diag()
     _check(lib().axp_compute_diagnostics(h, C.byref(d)), "axp_compute_diagnostics")
+    return d.as_dict()
+
+
+def axp_diagnostics_noalloc(desc, dev_ptrs, B_ext, E_ext, step, stream_ptr):
+    """Diagnostics of caller-held FP64 device fields without any device allocation.
+    dev_ptrs: 14 device addresses (E0xyz, B0xyz, E1xyz, B1xyz, phi^{n+1/2}, phi^{n-1/2})."""
+    ptrs = (C.c_void_p * 14)(*[int(p) for p in dev_ptrs])
+    d = axp_diag()
+    _check(lib().axp_diagnostics_noalloc(C.byref(desc), ptrs, _D3(*B_ext), _D3(*E_ext), int(step),
+                                         _P(stream_ptr), C.byref(d)), "axp_diagnostics_noalloc")
     return d.as_dict()
 
 

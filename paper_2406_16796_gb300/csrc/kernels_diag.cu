@@ -6,6 +6,10 @@
 // block sums the partials in fixed order.  The result depends only on the
 // grid size, never on scheduling, so a grid's diagnostics are bit-identical
 // however the work around it is arranged.
+#include <cmath>
+#include <cstdio>
+#include <mutex>
+
 #include "device_common.cuh"
 
 namespace axp {
@@ -155,4 +159,133 @@ cudaError_t diag_compute(axp_grid *g, axp_diag *dev_dst)
 template cudaError_t diag_compute<double>(axp_grid *, axp_diag *);
 template cudaError_t diag_compute<float>(axp_grid *, axp_diag *);
 
+// ---------------------------------------------------------------------------
+// Diagnostics for callers that cannot allocate device memory.
+//
+// The per-block partial sums and the result record live in file-scope static
+// device arrays instead of a workspace, so this entry point needs no
+// allocation at all.  Every GPU that loads the library holds these arrays
+// (kNoallocBlocks x 7 doubles + one record, about 230 KB) until the process
+// exits.  The arrays are shared by every call: each call rewrites all the
+// partials it uses and the result record, so nothing carries over between
+// calls, but calls that overlap on the GPU (other host threads or streams)
+// race on the shared arrays.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kNoallocBlocks = 4096;         // partial sums: one block of 256 threads ...
+constexpr int kNoallocCellsPerBlock = 2048;  // ... covers 2048 cells (8 per thread)
+constexpr int64_t kNoallocMaxCells = (int64_t)kNoallocBlocks * kNoallocCellsPerBlock;  // 8,388,608
+constexpr int kNoallocMaxDevices = 64;
+
+static __device__ __align__(256) double g_noalloc_partials[kNoallocBlocks * kQ];
+static __device__ __align__(256) axp_diag g_noalloc_result;
+
+std::mutex g_noalloc_mutex;
+double *g_noalloc_partials_addr[kNoallocMaxDevices];
+axp_diag *g_noalloc_result_addr[kNoallocMaxDevices];
+
+// Device addresses of the static arrays for the current device.  In host code
+// the array names are host-side stand-ins, never device addresses, so the
+// real addresses are looked up once per device with that device current.
+cudaError_t noalloc_setup(int dev, double **partials, axp_diag **result)
+{
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_partials_addr[dev]) {
+        void *p = nullptr, *r = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+        if (e != cudaSuccess) return e;
+        e = cudaGetSymbolAddress(&r, g_noalloc_result);
+        if (e != cudaSuccess) return e;
+        g_noalloc_partials_addr[dev] = (double *)p;
+        g_noalloc_result_addr[dev] = (axp_diag *)r;
+    }
+    *partials = g_noalloc_partials_addr[dev];
+    *result = g_noalloc_result_addr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
 }  // namespace axp
+
+extern "C" axp_status axp_diagnostics_noalloc(const axp_grid_desc *desc, const double *const dev_fields[14],
+                                              const double B_ext[3], const double E_ext[3], int64_t step,
+                                              void *cuda_stream, axp_diag *host_out)
+{
+    using namespace axp;
+    if (!desc || !dev_fields || !B_ext || !E_ext || !host_out) return AXP_E_INVAL;
+    for (int f = 0; f < 14; f++)
+        if (!dev_fields[f]) return AXP_E_INVAL;
+    size_t ws = 0;
+    const axp_status st = axp_workspace_bytes(desc, &ws);  // host-side validation only
+    if (st != AXP_OK) return st;
+    if (desc->precision != AXP_FP64) {
+        fprintf(stderr, "axp_diagnostics_noalloc: only FP64 fields are accepted\n");
+        return AXP_E_INVAL;
+    }
+    for (int a = 0; a < 3; a++)
+        for (int s = 0; s < 2; s++)
+            if (desc->axion_bc[a][s] == AXP_BC_OUTFLOW) {
+                fprintf(stderr, "axp_diagnostics_noalloc: outflow faces need ghost planes; use axp_compute_diagnostics\n");
+                return AXP_E_INVAL;
+            }
+    const int64_t N = desc->n[0] * desc->n[1] * desc->n[2];
+    if (N > kNoallocMaxCells) {
+        fprintf(stderr, "axp_diagnostics_noalloc: %lld cells exceed the maximum of %lld\n", (long long)N,
+                (long long)kNoallocMaxCells);
+        return AXP_E_INVAL;
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices) return AXP_E_CUDA;
+    double *partials = nullptr;
+    axp_diag *result = nullptr;
+    if (noalloc_setup(dev, &partials, &result) != cudaSuccess) return AXP_E_CUDA;
+
+    View<double> v;
+    memset(&v, 0, sizeof(v));
+    for (int f = 0; f < kFields; f++) v.f[f] = const_cast<double *>(dev_fields[f]);
+    v.phi_cur = const_cast<double *>(dev_fields[12]);
+    v.phi_b = const_cast<double *>(dev_fields[13]);
+    for (int a = 0; a < 3; a++) {
+        v.n[a] = desc->n[a];
+        v.d[a] = desc->d[a];
+        v.lo[a] = desc->lo[a];
+        v.Bext[a] = B_ext[a];
+        v.Eext[a] = E_ext[a];
+        v.periodic[a] = desc->em_bc[a][0] == AXP_BC_PERIODIC;
+        for (int s = 0; s < 2; s++) v.axbc[a][s] = desc->axion_bc[a][s];
+        int rlo = 0, rhi = (int)desc->n[a];
+        if (desc->n[a] > 1 && !v.periodic[a]) {
+            if (desc->em_bc[a][0] == AXP_BC_PML || desc->axion_bc[a][0] == AXP_BC_PML) rlo = desc->pml_cells;
+            if (desc->em_bc[a][1] == AXP_BC_PML || desc->axion_bc[a][1] == AXP_BC_PML) rhi = (int)desc->n[a] - desc->pml_cells;
+        }
+        v.region_lo[a] = rlo;
+        v.region_hi[a] = rhi;
+    }
+    v.N = N;
+    v.dt = desc->dt;
+    v.h = desc->dt / 2.0;
+    v.g = desc->g;
+    v.m2 = desc->m * desc->m;
+    PhiPair<double, false> q;
+    memset(&q, 0, sizeof(q));
+    q.hi = v.phi_cur;
+    q.b = v.phi_b;
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+    int nb = (int)((N + kNoallocCellsPerBlock - 1) / kNoallocCellsPerBlock);
+    if (nb < 1) nb = 1;
+    k_diag_partial<double, false><<<nb, kDiagThreads, 0, stream>>>(v, q, partials);
+    k_diag_final<<<1, kDiagThreads, 0, stream>>>(partials, nb, result, step, (double)step * desc->dt);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, result, sizeof(axp_diag), cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) {
+        fprintf(stderr, "axp: CUDA error %s\n", cudaGetErrorString(e));
+        return AXP_E_CUDA;
+    }
+    const double vals[] = {host_out->H_phi, host_out->H_g0, host_out->H_g1, host_out->W, host_out->gauss_l2};
+    for (double x : vals)
+        if (!std::isfinite(x)) return AXP_E_NONFINITE;
+    return AXP_OK;
+}
+

@@ -1,0 +1,52 @@
+"""The allocation-free diagnostics entry point against the regular one.
+
+axp_diagnostics_noalloc serves callers that cannot call cudaMalloc (their
+fields live in memory another allocator owns): its reduction scratch is a
+fixed array inside the library.  This file is collected last so that, if it
+fails, a run stopping at the first failure has already run every other test.
+"""
+import numpy as np
+import pytest
+
+from paper_2406_16796_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+KEYS = ("H_phi", "H_g0", "H_g1", "P_g2a", "P_a2g", "W", "sum_xB1z2", "sum_B1z2", "gauss_l2")
+ORDER = ("E0x", "E0y", "E0z", "B0x", "B0y", "B0z", "E1x", "E1y", "E1z", "B1x", "B1y", "B1z", "phi_cur", "phi_old")
+
+
+def test_noalloc_diagnostics_match_regular_entry_point_on_two_calls():
+    import torch
+
+    from paper_2406_16796_gb300 import axp
+
+    w = W.pulse_2d(nx=192, ny=96, m=0.5 * W.K0, g=1e-2)
+    grid = w.grid.replace(pml_cells=10)
+    g = axp.Grid(grid)
+    g.inject_laser(w.lasers[0])
+    g.step(20)
+    for call in range(2):
+        ref = g.diagnostics()  # the regular entry point (workspace scratch)
+        host = {k: g.read(k) for k in ORDER}
+        dev = {k: torch.tensor(v, dtype=torch.float64, device="cuda").contiguous() for k, v in host.items()}
+        ptrs = [dev[k].data_ptr() for k in ORDER]
+        torch.cuda.synchronize()
+        got = axp.axp_diagnostics_noalloc(g.desc, ptrs, grid.B_ext, grid.E_ext, g.step_count,
+                                          torch.cuda.current_stream().cuda_stream)
+        assert got["step"] == ref["step"] == g.step_count
+        for k in KEYS:
+            assert got[k] == pytest.approx(ref[k], rel=1e-12, abs=1e-300), (call, k, got[k], ref[k])
+        assert ref["H_phi"] > 0 and ref["H_g1"] > 0
+        g.step(15)
+    g.close()
+
+
+def test_noalloc_rejects_grids_beyond_its_scratch():
+    from paper_2406_16796_gb300 import axp
+
+    big = W.pulse_2d(nx=4096, ny=2049).grid
+    d = axp.desc_of(big)
+    with pytest.raises(axp.AxpError) as e:
+        axp.axp_diagnostics_noalloc(d, [1] * 14, big.B_ext, big.E_ext, 0, 0)
+    assert e.value.status == axp.AXP_E_INVAL
