@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
+    ap.add_argument("--no-scan", action="store_true")
+    ap.add_argument("--no-3d", action="store_true")
+    ap.add_argument("--no-1d", action="store_true")
     return ap.parse_args()
 
 
@@ -225,6 +228,109 @@ def timed_run(g, steps, warmup, stream):
     return ev0.elapsed_time(ev1) / 1e3, g.launches() - l0
 
 
+# 3D axion box: active arrays E1 (3), B1 (3) and the axion; FP32 split stores
+# phi and its increment (read and written); every field array read once and
+# written once per cell-update.
+BYTES_3D_FP32 = (2 * 6 + 4) * 4
+
+
+def axion3d_measurement(steps, warmup, hbm_peak, hbm_src, world):
+    """512^3 periodic box seeded with an axion plane wave, B_ext along y, FP32
+    split (no laser: the order-0 arrays are identically zero and are skipped)."""
+    import torch
+
+    from paper_2406_16796_gb300 import axp, workloads as W
+
+    w = W.axion_3d()
+    g = axp.Grid(w.grid)
+    for a in w.axions:
+        g.inject_axion(a)
+    el, launches = timed_run(g, steps, warmup, g.stream)
+    cells = w.grid.cells
+    per = el / max(1, launches)
+    ach = BYTES_3D_FP32 * cells / per / 1e9
+    out = {"workload": w.name, "cells": cells, "precision": "fp32_split", "steps": steps,
+           "value": cells * steps * world / el, "unit": "cell-updates/s", "ms_per_step": el / steps * 1e3,
+           "kernel_path": g.kernel_path(), "gpu_launches": launches,
+           "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+                        "peak_source": hbm_src, "algorithmic_bytes_per_cell": BYTES_3D_FP32}}
+    g.close()
+    torch.cuda.synchronize()
+    return out
+
+
+def vacuum1d_measurement(world):
+    """The 1D conversion run in FP64: Nx = 4096, 20000 steps, periodic.  The state
+    (8 arrays x 4096 x 8 B) stays in L2, so the bound is per-step launch and
+    synchronisation latency: reported as microseconds per step."""
+    from paper_2406_16796_gb300 import axp, workloads as W
+
+    w = W.vacuum_1d()
+    g = axp.Grid(w.grid)
+    g.inject_laser(w.lasers[0])
+    el, launches = timed_run(g, w.steps, 100, g.stream)
+    d = g.diagnostics()
+    out = {"workload": w.name, "cells": w.grid.cells, "precision": "fp64", "steps": w.steps,
+           "value": w.grid.cells * w.steps * world / el, "unit": "cell-updates/s", "us_per_step": el / w.steps * 1e6,
+           "kernel_path": g.kernel_path(), "gpu_launches": launches, "P_g2a": d["P_g2a"]}
+    g.close()
+    return out
+
+
+def scan_measurement(rank, world, fp64_sample=6):
+    """The batched parameter scan: 512 seeded 1D instances (Nx log-uniform in
+    [1024, 65536], m/omega0 in [1e-3, 2], g in [1e-6, 1e-3], B0 in [0.1, 10],
+    5000-40000 steps), FP32 split, one persistent kernel per block of steps,
+    CUDA-graph replay and autotuned tiling (the tuner's probe steps are inside
+    the timing).  Each rank runs its own share of the instances (replicas).
+    The comparator is sequential single-instance FP64 runs of a seeded sample
+    of the same instances through the grid API, extrapolated by cell-updates;
+    the sample also gives the FP32 batch's conversion-probability error."""
+    import numpy as np
+    import torch
+
+    from paper_2406_16796_gb300 import axp, batch as B, workloads as W
+
+    insts = W.scan_instances()[rank::world]
+    cu = sum(i.nx * i.steps for i in insts)
+    res, el, tiling = B.run_scan([B.scan_instance(i) for i in insts])
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([el], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        el = float(t.item())
+    total_sims = len(W.scan_instances())
+    out = {"workload": "scan_512x1d", "instances": total_sims, "cell_updates": cu * world, "seconds": el,
+           "sims_per_s": len(insts) * world / el, "cell_updates_per_s": cu * world / el, "tiling": list(tiling),
+           "graphs": True, "precision": "fp32_split"}
+    if rank != 0:
+        return out
+    rng = np.random.default_rng(20240624)
+    idx = sorted(rng.choice(len(insts), min(fp64_sample, len(insts)), replace=False).tolist())
+    t_tot, cu_tot, errs = 0.0, 0, []
+    for j in idx:
+        i = insts[j]
+        w = W.scan_workload(i, precision="fp64")
+        g = axp.Grid(w.grid)
+        g.inject_laser(w.lasers[0])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.step(i.steps)
+        d = g.diagnostics()
+        t_tot += time.perf_counter() - t0
+        cu_tot += i.nx * i.steps
+        errs.append(abs(res[j]["P_g2a"] - d["P_g2a"]) / abs(d["P_g2a"]))
+        g.close()
+    fp64_cu_rate = cu_tot / t_tot
+    fp64_sims = fp64_cu_rate / (cu / len(insts))
+    out["fp64_per_instance"] = {"sims_per_s": fp64_sims, "cell_updates_per_s": fp64_cu_rate,
+                                "sample": "%d seeded instances run one after another in FP64, full steps" % len(idx)}
+    out["speedup_vs_fp64_per_instance"] = out["sims_per_s"] / fp64_sims
+    out["max_rel_err_P_vs_fp64"] = max(errs)
+    return out
+
+
 def gpu_arm(args):
     import torch
 
@@ -280,7 +386,8 @@ def gpu_arm(args):
     hbm = {"achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_achieved / hbm_peak,
            "peak_source": hbm_src, "algorithmic_bytes_per_cell": bpc}
     flops = FLOPS_PER_CELL * cells / per_launch / 1e12
-    kern = "k_fused (one launch per step)" if path == axp.AXP_KERNEL_FUSED else "general kernels (7 launches per step)"
+    kern = {axp.AXP_KERNEL_TM2D: "k_tm2d (one launch per step)", axp.AXP_KERNEL_FUSED: "k_fused (one launch per step)"}.get(
+        path, "general kernels (7 launches per step)")
     if prec == "fp64":
         roofline = {"bound": "alu", "achieved": flops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": flops / FP64_PEAK_TFLOPS, "traffic": None, "kernel": kern,
@@ -331,6 +438,16 @@ def gpu_arm(args):
                               "algorithmic_bytes_per_cell": bytes_per_cell("fp32")}}
         g32.close()
 
+    scan = None
+    if not args.no_scan:
+        scan = scan_measurement(rank, world)
+    ax3 = None
+    if not args.no_3d:
+        ax3 = axion3d_measurement(max(20, args.steps // 3), args.warmup, hbm_peak, hbm_src, world)
+    v1 = None
+    if not args.no_1d:
+        v1 = vacuum1d_measurement(world)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         wb = workload(args, "fp64")
@@ -345,6 +462,12 @@ def gpu_arm(args):
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
     if other:
         line["fp32_split"] = other
+    if scan:
+        line["scan"] = scan
+    if ax3:
+        line["axion_3d"] = ax3
+    if v1:
+        line["vacuum_1d"] = v1
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

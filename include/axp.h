@@ -242,19 +242,100 @@ axp_status axp_load_state(axp_grid *grid, const void *host_src, size_t bytes);
 axp_status axp_get_step(const axp_grid *grid, int64_t *step);
 axp_status axp_synchronize(axp_grid *grid);
 
-/* Kernel selection for axp_step.  AXP_KERNEL_AUTO (default) uses the fused
- * single-pass kernel where one exists for the grid's shape, boundaries and
- * active field components, else the general multi-pass kernels.
+/* Kernel selection for axp_step.  AXP_KERNEL_AUTO (default) uses the fastest
+ * single-pass kernel that supports the grid's shape, boundaries and active
+ * field components, else the general multi-pass kernels.
  * AXP_KERNEL_GENERAL forces the general kernels (one pass per stage of the
- * time scheme, in the oracle's operation order). */
-typedef enum { AXP_KERNEL_AUTO = 0, AXP_KERNEL_GENERAL = 1, AXP_KERNEL_FUSED = 2 } axp_kernel;
+ * time scheme, in the oracle's operation order); AXP_KERNEL_FUSED forces the
+ * generic single-pass kernel (1D/2D/3D, periodic, reflect and PML edges);
+ * AXP_KERNEL_TM2D forces the single-pass kernel specialised for 2D grids with
+ * an (E0z; B0x, B0y) laser and periodic or PML edges.  Forcing a kernel that
+ * does not support the grid makes axp_step return AXP_E_STATE. */
+typedef enum { AXP_KERNEL_AUTO = 0, AXP_KERNEL_GENERAL = 1, AXP_KERNEL_FUSED = 2, AXP_KERNEL_TM2D = 3 } axp_kernel;
 axp_status axp_set_kernel(axp_grid *grid, int32_t kernel);
-/* Which path the next axp_step will take (AXP_KERNEL_GENERAL or _FUSED). */
+/* Which path the next axp_step will take (AXP_KERNEL_GENERAL, _FUSED or _TM2D). */
 axp_status axp_get_kernel_path(axp_grid *grid, int32_t *path);
 
 /* Number of kernel launches issued by this handle since creation (for
  * launch accounting in benchmarks). */
 axp_status axp_get_launch_count(const axp_grid *grid, int64_t *count);
+
+/* ------------------------------------------------------------------------
+ * Batches of 1D conversion runs (parameter scans and serving).
+ *
+ * Each instance is the 1D photon -> axion set-up of Sec. 3.2 in a periodic
+ * box: a CW laser E0y along x (placed as the exact discrete eigenmode, as
+ * axp_inject_laser does), a uniform background B_ext = (0, By, Bz), and the
+ * axion field initially zero.  Every instance has its own size, mass,
+ * coupling, background, laser and step count.  All instances are stored in
+ * FP32 split form (as AXP_FP32_SPLIT) and advanced together: one launch
+ * advances every unfinished instance by up to `block_steps` steps, each
+ * (instance, segment) work item keeping its cells in shared memory for the
+ * whole block (time blocking; segments of large instances carry a halo of
+ * 3 cells per step).  Diagnostics are accumulated in FP64.
+ *
+ * Memory: the caller provides one device workspace sized for a maximum number
+ * of instances and a total number of cells; instances are admitted into it
+ * first-fit and their cells released on removal (admission by device memory).
+ * The batch's per-launch bookkeeping lives on the device, so a sequence of
+ * axp_batch_run calls can be captured in a CUDA graph.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    int64_t nx;           /* cells (periodic box), >= 8 */
+    double dx, dt;        /* dt <= dx (Yee bound) and the axion bound */
+    double m, g;          /* axion mass and coupling */
+    double By, Bz;        /* uniform background field (B_ext,x = 0) */
+    double amplitude;     /* laser E amplitude */
+    double k;             /* laser wave number (2 pi x whole wavelengths / box) */
+    int64_t steps;        /* total steps to run */
+} axp_batch_instance;
+
+typedef struct axp_batch axp_batch;
+
+/* Workspace bytes for up to max_instances instances totalling max_cells cells. */
+axp_status axp_batch_workspace_bytes(int32_t max_instances, int64_t max_cells, size_t *bytes);
+axp_status axp_batch_create(int32_t max_instances, int64_t max_cells, void *dev_workspace, size_t bytes,
+                            void *cuda_stream, axp_batch **out);
+axp_status axp_batch_destroy(axp_batch *batch);
+
+/* Admit an instance (initial fields written on the batch's stream).  *slot
+ * receives its slot; AXP_E_NOMEM when no slot or no contiguous cell range is
+ * free, AXP_E_UNSTABLE / AXP_E_INVAL for bad parameters. */
+axp_status axp_batch_add(axp_batch *batch, const axp_batch_instance *inst, int32_t *slot);
+/* Release a slot and its cells (the instance need not be finished). */
+axp_status axp_batch_remove(axp_batch *batch, int32_t slot);
+
+/* Advance every admitted, unfinished instance by up to nsteps steps,
+ * asynchronously on the batch's stream (ceil(nsteps / block_steps) launches of
+ * the persistent kernel plus one bookkeeping launch each). */
+axp_status axp_batch_run(axp_batch *batch, int64_t nsteps);
+
+/* Replay each axp_batch_run as one CUDA graph (captured on first use and kept
+ * while the step count, the tiling and the set of admitted instances are
+ * unchanged).  Needs a batch created on a non-default stream. */
+axp_status axp_batch_use_graphs(axp_batch *batch, int32_t enable);
+/* Kernel launches issued (graph replays count their nodes). */
+axp_status axp_batch_launch_count(const axp_batch *batch, int64_t *count);
+
+/* Steps done so far per slot (-1 for free slots), copied to host; synchronises. */
+axp_status axp_batch_progress(axp_batch *batch, int64_t *steps_done, int32_t max_slots);
+
+/* FP64 diagnostics of one slot's present state (same definitions as axp_diag);
+ * synchronises. */
+axp_status axp_batch_result(axp_batch *batch, int32_t slot, axp_diag *out);
+
+/* Stored state of one slot as nx doubles: which = 0 E0y, 1 B0z, 2 E1y, 3 E1z,
+ * 4 B1y, 5 B1z, 6 phi^{n+1/2}, 7 phi^{n+1/2} - phi^{n-1/2}.  B and phi are at
+ * the present step n; the E arrays hold E^{n+1/2} (the leapfrog-staggered
+ * state the batch advances).  Synchronises. */
+axp_status axp_batch_read_state(axp_batch *batch, int32_t slot, int32_t which, double *host_dst, size_t bytes);
+
+/* Time blocking: steps per launch, core cells per segment, threads per CTA.
+ * block_steps in [1, 256]; segment_cells such that a segment and its halo fit
+ * in shared memory; threads a multiple of 32 in [64, 1024]. */
+axp_status axp_batch_set_tiling(axp_batch *batch, int32_t block_steps, int32_t segment_cells, int32_t threads);
+axp_status axp_batch_get_tiling(const axp_batch *batch, int32_t *block_steps, int32_t *segment_cells,
+                                int32_t *threads);
 
 #ifdef __cplusplus
 }

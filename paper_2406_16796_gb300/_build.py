@@ -30,6 +30,7 @@ UNITS = {
     "kernels_fused.cu": [],
     "kernels_fused_f64.cu": [],
     "kernels_fused_f32.cu": [],
+    "batch1d.cu": [],
 }
 
 

@@ -428,7 +428,7 @@ axp_status axp_step(axp_grid *g, int64_t nsteps)
     if (g->kernel_choice != AXP_KERNEL_GENERAL) {
         e = is_fp32(g) ? fused_step<float>(g, nsteps, &handled) : fused_step<double>(g, nsteps, &handled);
         if (e != cudaSuccess) return cuda_status(e);
-        if (!handled && g->kernel_choice == AXP_KERNEL_FUSED) return AXP_E_STATE;
+        if (!handled && g->kernel_choice != AXP_KERNEL_AUTO) return AXP_E_STATE;
     }
     if (!handled) {
         e = ensure_integer(g);
@@ -684,7 +684,7 @@ axp_status axp_get_step(const axp_grid *g, int64_t *step)
 
 axp_status axp_set_kernel(axp_grid *g, int32_t kernel)
 {
-    if (!g || kernel < AXP_KERNEL_AUTO || kernel > AXP_KERNEL_FUSED) return AXP_E_INVAL;
+    if (!g || kernel < AXP_KERNEL_AUTO || kernel > AXP_KERNEL_TM2D) return AXP_E_INVAL;
     g->kernel_choice = kernel;
     return AXP_OK;
 }
@@ -692,9 +692,7 @@ axp_status axp_set_kernel(axp_grid *g, int32_t kernel)
 axp_status axp_get_kernel_path(axp_grid *g, int32_t *path)
 {
     if (!g || !path) return AXP_E_INVAL;
-    bool fused = false;
-    if (g->kernel_choice != AXP_KERNEL_GENERAL) fused = is_fp32(g) ? fused_supported<float>(g) : fused_supported<double>(g);
-    *path = fused ? AXP_KERNEL_FUSED : AXP_KERNEL_GENERAL;
+    *path = is_fp32(g) ? fused_path<float>(g) : fused_path<double>(g);
     return AXP_OK;
 }
 

@@ -105,6 +105,9 @@ template <typename T>
 cudaError_t fused_step(axp_grid *g, int64_t nsteps, bool *handled);
 template <typename T>
 bool fused_supported(const axp_grid *g);
+// the path axp_step will take under the handle's kernel choice (an axp_kernel value)
+template <typename T>
+int32_t fused_path(const axp_grid *g);
 // staggered <-> integer-time conversion of E (E^{n+1/2} = E^n + h (curl B^n - g J^n))
 template <typename T>
 cudaError_t enter_staggered(axp_grid *g);

@@ -1,0 +1,675 @@
+// batch1d.cu -- batches of 1D conversion runs in one persistent, time-blocked
+// launch (arXiv 2406.16796 Sec. 2.3 scheme; Sec. 3.2 set-up), FP32 split.
+//
+// Each instance: periodic box of nx cells, CW laser E0y/B0z along x, uniform
+// background (0, By, Bz), axion and order-1 fields initially zero.  In 1D the
+// fields that can become non-zero are E0y, B0z (laser), E1y, E1z, B1y, B1z and
+// phi; with the leapfrog-staggered E (as in the single-grid fused kernels) one
+// step is
+//   1. B^{n+1} = B^n - 2h curl E^{n+1/2}            (B0z, B1y, B1z)
+//   2. S = E0y By; pi^{n+1}, phi^{n+3/2}, phi^{n+1}; E0y^{n+1} = E0y + h curl B0^{n+1}
+//   3. P_y = D_t phi By, P_z = D_t phi (Bbar0z + Bz) + E0y^{n+1} d_x phi^{n+1}
+//      (face averages along the invariant y, z are identities, so J = P);
+//      E1^{n+3/2} = E1^{n+1/2} + 2h (curl B1^{n+1} - g J);  E0y^{n+3/2} = E0y^{n+1} + h curl B0^{n+1}
+//
+// Work items are (instance, segment).  A CTA copies its item's cells into
+// shared memory -- the whole instance with periodic wrap when it fits, else a
+// segment plus a halo of 3 cells per step -- advances T steps there, and
+// writes the valid cells to the other of two global state buffers.  Each
+// cell's arithmetic is the same whatever the segmentation, the block length or
+// the other instances in the batch, so results are bit-identical alone and in
+// the mix.  Work items are taken from an atomic queue by a persistent grid;
+// steps remaining per instance live on the device, so consecutive launches
+// need no host round trip and can be captured in a CUDA graph.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "axp_internal.h"
+
+namespace axp {
+namespace {
+
+constexpr int kArr = 6 + 2;      // E0y B0z E1y E1z B1y B1z phi pi (global, per buffer)
+constexpr int kSmemArr = 10;     // + phi (second buffer) + phi^{n+1} in shared memory
+constexpr size_t kSmemMax = 230400;  // dynamic shared memory (the per-block limit is 232448 with the static part)
+constexpr int kCapCells = (int)(kSmemMax / (kSmemArr * sizeof(float)));  // cells per CTA in shared memory
+
+struct Slot {
+    int64_t off;        // first cell of this instance in every pool array
+    int64_t remaining;  // steps still to do
+    int64_t done;       // steps done
+    int32_t nx;
+    int32_t parity;     // buffer holding the present state
+    int32_t active;     // admitted
+    int32_t pad;
+    float h, idx, hidx, cx, c0, dt2g, inv_dt, g, By, Bz;
+    double dx, dt, m, gd, Byd, Bzd;
+};
+
+struct Item {
+    int32_t slot;
+    int32_t x0;   // first core cell
+    int32_t len;  // core cells
+    int32_t whole;  // 1: the item is the whole instance (periodic wrap in shared memory)
+};
+
+struct Dev {
+    float *pool;   // [2 buffers][kArr][max_cells]
+    int64_t max_cells;
+    Slot *slots;
+    Item *items;
+    int32_t *counter;
+    int32_t nitems;
+};
+
+__device__ __forceinline__ float *arr(const Dev &D, int buf, int a, int64_t off)
+{
+    return D.pool + ((int64_t)(buf * kArr + a) * D.max_cells + off);
+}
+
+// One launch: every work item advances min(budget, remaining) steps.
+__global__ void __launch_bounds__(1024) k_batch_block(Dev D, int budget, int halo_per_step)
+{
+    extern __shared__ __align__(16) float sm[];
+    __shared__ int s_item;
+    const int nt = blockDim.x;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(D.counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= D.nitems) return;
+        const Item I = D.items[it];
+        const Slot S = D.slots[I.slot];
+        const int64_t rem = S.remaining;
+        const int T = (int)(rem < budget ? rem : budget);
+        if (!S.active || T <= 0) continue;
+        const int nx = S.nx;
+        const int H = I.whole ? 0 : halo_per_step * T;
+        const int n = I.whole ? nx : I.len + 2 * H;
+        float *E0 = sm, *B0 = sm + n, *E1y = sm + 2 * n, *E1z = sm + 3 * n, *B1y = sm + 4 * n, *B1z = sm + 5 * n;
+        float *PA = sm + 6 * n, *PB = sm + 7 * n, *PI = sm + 8 * n, *MID = sm + 9 * n;
+        const int in = S.parity, out = S.parity ^ 1;
+        // load (global periodic wrap)
+        for (int i = threadIdx.x; i < n; i += nt) {
+            int gx = I.whole ? i : I.x0 - H + i;
+            gx %= nx;
+            if (gx < 0) gx += nx;
+            const int64_t o = S.off + gx;
+            E0[i] = arr(D, in, 0, o)[0];
+            B0[i] = arr(D, in, 1, o)[0];
+            E1y[i] = arr(D, in, 2, o)[0];
+            E1z[i] = arr(D, in, 3, o)[0];
+            B1y[i] = arr(D, in, 4, o)[0];
+            B1z[i] = arr(D, in, 5, o)[0];
+            PA[i] = arr(D, in, 6, o)[0];
+            PI[i] = arr(D, in, 7, o)[0];
+        }
+        __syncthreads();
+        const bool wrapc = I.whole != 0;
+        const float h = S.h, idx = S.idx, hidx = S.hidx, cx = S.cx, c0 = S.c0, dt2g = S.dt2g, inv_dt = S.inv_dt;
+        const float g = S.g, By = S.By, Bz = S.Bz;
+        float *phi = PA, *phin = PB;
+        for (int s = 0; s < T; s++) {
+            // 1. B^{n+1}
+            for (int i = threadIdx.x; i < n; i += nt) {
+                const int ip = wrapc ? (i + 1 == n ? 0 : i + 1) : min(i + 1, n - 1);
+                const float c0z = (E0[ip] - E0[i]) * idx;    // (curl E0)_z = D_x E0y
+                const float c1y = -(E1z[ip] - E1z[i]) * idx;  // (curl E1)_y = -D_x E1z
+                const float c1z = (E1y[ip] - E1y[i]) * idx;   // (curl E1)_z = D_x E1y
+                B0[i] = fmaf(-h, c0z, fmaf(-h, c0z, B0[i]));
+                B1y[i] = fmaf(-h, c1y, fmaf(-h, c1y, B1y[i]));
+                B1z[i] = fmaf(-h, c1z, fmaf(-h, c1z, B1z[i]));
+            }
+            __syncthreads();
+            // 2. axion; E0y^{n+1}
+            for (int i = threadIdx.x; i < n; i += nt) {
+                const int ip = wrapc ? (i + 1 == n ? 0 : i + 1) : min(i + 1, n - 1);
+                const int im = wrapc ? (i == 0 ? n - 1 : i - 1) : max(i - 1, 0);
+                const float Sg = E0[i] * By;  // Ebar0 . Bbar0 / g: E0y with the background along y
+                const float ph = phi[i];
+                // second difference from neighbour differences and the mass term kept
+                // apart (c0 = -(m dt)^2), so neither rounds against 2*phi
+                const float pin = fmaf(dt2g, Sg, fmaf(cx, (phi[ip] - ph) + (phi[im] - ph), fmaf(c0, ph, PI[i])));
+                PI[i] = pin;
+                phin[i] = ph + pin;
+                MID[i] = fmaf(0.5f, pin, ph);
+                const float cb = -(B0[i] - B0[im]) * idx;  // (curl B0)_y = -D_x B0z
+                E0[i] = fmaf(h, cb, E0[i]);
+            }
+            __syncthreads();
+            // 3. axion current and the E updates
+            for (int i = threadIdx.x; i < n; i += nt) {
+                const int ip = wrapc ? (i + 1 == n ? 0 : i + 1) : min(i + 1, n - 1);
+                const int im = wrapc ? (i == 0 ? n - 1 : i - 1) : max(i - 1, 0);
+                const float Dt = PI[i] * inv_dt;
+                const float Py = Dt * By;
+                const float bz = 0.5f * (B0[i] + B0[im]) + Bz;
+                const float Pz = fmaf(E0[i], (MID[ip] - MID[im]) * hidx, Dt * bz);
+                const float cby = -(B1z[i] - B1z[im]) * idx;  // (curl B1)_y = -D_x B1z
+                const float cbz = (B1y[i] - B1y[im]) * idx;   // (curl B1)_z =  D_x B1y
+                const float xy = fmaf(-g, Py, cby), xz = fmaf(-g, Pz, cbz);
+                E1y[i] = fmaf(h, xy, fmaf(h, xy, E1y[i]));
+                E1z[i] = fmaf(h, xz, fmaf(h, xz, E1z[i]));
+                const float cb = -(B0[i] - B0[im]) * idx;
+                E0[i] = fmaf(h, cb, E0[i]);
+            }
+            float *t = phi;
+            phi = phin;
+            phin = t;
+            __syncthreads();
+        }
+        // write the valid core cells to the other buffer
+        const int lo = I.whole ? 0 : H, cnt = I.whole ? nx : I.len;
+        for (int i = threadIdx.x; i < cnt; i += nt) {
+            const int gx = I.whole ? i : I.x0 + i;
+            const int j = lo + i;
+            const int64_t o = S.off + gx;
+            arr(D, out, 0, o)[0] = E0[j];
+            arr(D, out, 1, o)[0] = B0[j];
+            arr(D, out, 2, o)[0] = E1y[j];
+            arr(D, out, 3, o)[0] = E1z[j];
+            arr(D, out, 4, o)[0] = B1y[j];
+            arr(D, out, 5, o)[0] = B1z[j];
+            arr(D, out, 6, o)[0] = phi[j];
+            arr(D, out, 7, o)[0] = PI[j];
+        }
+        __syncthreads();
+    }
+}
+
+// After each launch: charge the steps, flip the buffers, reset the queue.
+__global__ void k_batch_account(Dev D, int nslots, int budget)
+{
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nslots; s += gridDim.x * blockDim.x) {
+        Slot &S = D.slots[s];
+        if (!S.active) continue;
+        const int64_t T = S.remaining < budget ? S.remaining : budget;
+        if (T <= 0) continue;
+        S.remaining -= T;
+        S.done += T;
+        S.parity ^= 1;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *D.counter = 0;
+}
+
+// Initial state of one instance in buffer 0: the CW eigenmode laser at t = 0
+// (E0y = A cos(k x_E), B0z = discrete curl of F = (A / cos(theta/2)) sin(k x)/K),
+// then E0y moved to t = +dt/2 (E0y^{1/2} = E0y^0 + h (curl B0^0)_y); zero elsewhere.
+__global__ void k_batch_init(Dev D, int slot, double A, double k)
+{
+    const Slot S = D.slots[slot];
+    const int nx = S.nx;
+    const double dx = S.dx, dt = S.dt;
+    const double K = (2.0 / dx) * sin(k * dx / 2.0);
+    const double sh = dt * K / 2.0;
+    const double ch = sqrt(1.0 - sh * sh);
+    const double Fs = A / (ch * K);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nx; i += gridDim.x * blockDim.x) {
+        // F_y at the E_y samples (cell centres), periodic
+        auto F = [&](int c) {
+            c %= nx;
+            if (c < 0) c += nx;
+            return Fs * sin(k * ((double)c + 0.5) * dx);
+        };
+        const double bz_i = (F(i + 1) - F(i)) / dx;      // B0z(i) = D_x F_y
+        const double bz_m = (F(i) - F(i - 1)) / dx;      // B0z(i-1)
+        const double e0 = A * cos(k * ((double)i + 0.5) * dx);
+        const double e_half = e0 + (dt / 2.0) * (-(bz_i - bz_m) / dx);
+        const int64_t o = S.off + i;
+        arr(D, 0, 0, o)[0] = (float)e_half;
+        arr(D, 0, 1, o)[0] = (float)bz_i;
+        for (int a = 2; a < kArr; a++) arr(D, 0, a, o)[0] = 0.0f;
+    }
+}
+
+// FP64 diagnostics of one instance at its present (integer) time, with E
+// taken back from n+1/2 to n.  One block, fixed-order reduction.
+__global__ void __launch_bounds__(256) k_batch_diag(Dev D, int slot, axp_diag *out)
+{
+    const Slot S = D.slots[slot];
+    const int nx = S.nx;
+    const int buf = S.parity;
+    const float *E0 = arr(D, buf, 0, S.off), *B0 = arr(D, buf, 1, S.off), *E1y = arr(D, buf, 2, S.off);
+    const float *E1z = arr(D, buf, 3, S.off), *B1y = arr(D, buf, 4, S.off), *B1z = arr(D, buf, 5, S.off);
+    const float *PH = arr(D, buf, 6, S.off), *PI = arr(D, buf, 7, S.off);
+    const double dx = S.dx, dt = S.dt, h = dt / 2.0, m2 = S.m * S.m, g = S.gd, By = S.Byd, Bz = S.Bzd;
+    const double dV = dx * dx * dx;
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    auto wrap = [&](int c) { return c < 0 ? c + nx : (c >= nx ? c - nx : c); };
+    auto mid = [&](int c) { c = wrap(c); return (double)PH[c] - 0.5 * (double)PI[c]; };
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+        const int im = wrap(i - 1);
+        const double Dt = (double)PI[i] / dt;
+        const double ph = mid(i);
+        const double gr = (mid(i + 1) - ph) / dx;
+        acc[0] += 0.5 * ((Dt * Dt + gr * gr) + m2 * ph * ph) * dV;
+        const double cb0 = -((double)B0[i] - (double)B0[im]) / dx;
+        const double e0 = (double)E0[i] - h * cb0;
+        const double b0 = B0[i];
+        // J^n at the cell: P_y = Dt By, P_z = Dt (Bbar0z + Bz) + E0y^n d_x phi^n
+        const double py = Dt * By;
+        const double pz = Dt * (0.5 * ((double)B0[i] + (double)B0[im]) + Bz) + e0 * (mid(i + 1) - mid(i - 1)) / (2.0 * dx);
+        const double cby = -((double)B1z[i] - (double)B1z[im]) / dx;
+        const double cbz = ((double)B1y[i] - (double)B1y[im]) / dx;
+        const double e1y = (double)E1y[i] - h * (cby - g * py);
+        const double e1z = (double)E1z[i] - h * (cbz - g * pz);
+        const double b1y = B1y[i], b1z = B1z[i];
+        acc[1] += 0.5 * (e0 * e0 + b0 * b0) * dV;
+        acc[2] += 0.5 * (e1y * e1y + e1z * e1z + b1y * b1y + b1z * b1z) * dV;
+        acc[3] += (e0 * e1y + By * b1y + (b0 + Bz) * b1z) * dV;
+        const double xb = (double)(i + 1) * dx;
+        acc[4] += xb * b1z * b1z * dV;
+        acc[5] += b1z * b1z * dV;
+    }
+    __shared__ double sh[6][256];
+    for (int q = 0; q < 6; q++) sh[q][threadIdx.x] = acc[q];
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+            for (int q = 0; q < 6; q++) sh[q][threadIdx.x] += sh[q][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        axp_diag d;
+        d.step = S.done;
+        d.t = (double)S.done * dt;
+        d.H_phi = sh[0][0];
+        d.H_g0 = sh[1][0];
+        d.H_g1 = sh[2][0];
+        d.P_g2a = d.H_g0 > 0 ? d.H_phi / d.H_g0 : 0.0;
+        d.P_a2g = d.H_phi > 0 ? d.H_g1 / d.H_phi : 0.0;
+        d.W = d.H_phi + sh[3][0];
+        d.sum_xB1z2 = sh[4][0];
+        d.sum_B1z2 = sh[5][0];
+        d.gauss_l2 = 0.0;  // div E1 and B_ext,x d_x phi vanish identically in this 1D set-up
+        *out = d;
+    }
+}
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+struct Layout {
+    size_t pool, slots, items, counter, diag, total;
+};
+
+Layout layout(int32_t max_instances, int64_t max_cells)
+{
+    Layout L;
+    size_t off = 0;
+    L.pool = off;
+    off += align_up((size_t)2 * kArr * max_cells * sizeof(float));
+    L.slots = off;
+    off += align_up((size_t)max_instances * sizeof(Slot));
+    L.items = off;
+    // an instance of nx cells makes at most nx / 64 + 1 items (segments are >= 64 cells)
+    off += align_up(((size_t)max_instances + (size_t)max_cells / 64 + 1) * sizeof(Item));
+    L.counter = off;
+    off += kAlign;
+    L.diag = off;
+    off += align_up(sizeof(axp_diag));
+    L.total = off;
+    return L;
+}
+
+axp_status cuda_st(cudaError_t e)
+{
+    if (e == cudaSuccess) return AXP_OK;
+    fprintf(stderr, "axp batch: CUDA error %s\n", cudaGetErrorString(e));
+    return AXP_E_CUDA;
+}
+
+}  // namespace
+}  // namespace axp
+
+using namespace axp;
+
+struct axp_batch {
+    int32_t max_instances;
+    int64_t max_cells;
+    char *ws;
+    cudaStream_t stream;
+    Layout L;
+    Dev D;
+    std::vector<Slot> slots;                         // host mirror
+    std::vector<std::pair<int64_t, int64_t>> free;  // free cell ranges (offset, length), sorted
+    bool dirty;
+    int32_t block_steps, segment_cells, threads;
+    int sms;
+    int64_t launches;
+    // CUDA graph of one axp_batch_run call, reused while the call's step count,
+    // the tiling and the work table stay the same
+    bool use_graph;
+    cudaGraphExec_t graph;
+    int64_t graph_steps;
+};
+
+extern "C" {
+
+axp_status axp_batch_workspace_bytes(int32_t max_instances, int64_t max_cells, size_t *bytes)
+{
+    if (!bytes || max_instances < 1 || max_cells < 8 || max_cells > ((int64_t)1 << 31)) return AXP_E_INVAL;
+    *bytes = layout(max_instances, max_cells).total;
+    return AXP_OK;
+}
+
+axp_status axp_batch_create(int32_t max_instances, int64_t max_cells, void *dev_workspace, size_t bytes,
+                            void *cuda_stream, axp_batch **out)
+{
+    if (!out || !dev_workspace || max_instances < 1 || max_cells < 8 || max_cells > ((int64_t)1 << 31))
+        return AXP_E_INVAL;
+    if ((uintptr_t)dev_workspace % kAlign) return AXP_E_INVAL;
+    *out = nullptr;
+    const Layout L = layout(max_instances, max_cells);
+    if (bytes < L.total) return AXP_E_NOMEM;
+    axp_batch *b = new (std::nothrow) axp_batch();
+    if (!b) return AXP_E_NOMEM;
+    b->max_instances = max_instances;
+    b->max_cells = max_cells;
+    b->ws = (char *)dev_workspace;
+    b->stream = (cudaStream_t)cuda_stream;
+    b->L = L;
+    b->D.pool = (float *)(b->ws + L.pool);
+    b->D.max_cells = max_cells;
+    b->D.slots = (Slot *)(b->ws + L.slots);
+    b->D.items = (Item *)(b->ws + L.items);
+    b->D.counter = (int32_t *)(b->ws + L.counter);
+    b->D.nitems = 0;
+    b->slots.assign(max_instances, Slot());
+    std::memset(b->slots.data(), 0, sizeof(Slot) * max_instances);
+    b->free.push_back({0, max_cells});
+    b->dirty = true;
+    b->block_steps = 32;
+    b->segment_cells = 4096;
+    b->threads = 512;
+    b->use_graph = false;
+    b->graph = nullptr;
+    b->graph_steps = -1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    b->sms = 152;
+    cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaMemsetAsync(b->ws + L.slots, 0, L.total - L.slots, b->stream);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_batch_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) {
+        delete b;
+        return cuda_st(e);
+    }
+    *out = b;
+    return AXP_OK;
+}
+
+axp_status axp_batch_destroy(axp_batch *b)
+{
+    if (!b) return AXP_E_INVAL;
+    // the caller frees the workspace after this returns: let queued work finish
+    cudaStreamSynchronize(b->stream);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    delete b;
+    return AXP_OK;
+}
+
+axp_status axp_batch_add(axp_batch *b, const axp_batch_instance *in, int32_t *slot)
+{
+    if (!b || !in || !slot) return AXP_E_INVAL;
+    if (in->nx < 8 || in->nx > (1 << 30) || !(in->dx > 0) || !(in->dt > 0) || in->steps < 0 || !std::isfinite(in->g) ||
+        !std::isfinite(in->m) || !std::isfinite(in->By) || !std::isfinite(in->Bz) || !std::isfinite(in->amplitude) ||
+        !std::isfinite(in->k))
+        return AXP_E_INVAL;
+    if (in->dt > in->dx || in->dt * in->dt * (4.0 / (in->dx * in->dx) + in->m * in->m) > 4.0) return AXP_E_UNSTABLE;
+    int s = -1;
+    for (int i = 0; i < b->max_instances; i++)
+        if (!b->slots[i].active) {
+            s = i;
+            break;
+        }
+    if (s < 0) return AXP_E_NOMEM;
+    int64_t off = -1;
+    for (auto &r : b->free)
+        if (r.second >= in->nx) {
+            off = r.first;
+            r.first += in->nx;
+            r.second -= in->nx;
+            break;
+        }
+    if (off < 0) return AXP_E_NOMEM;
+    b->free.erase(std::remove_if(b->free.begin(), b->free.end(), [](const std::pair<int64_t, int64_t> &r) {
+                      return r.second == 0;
+                  }),
+                  b->free.end());
+    Slot S;
+    std::memset(&S, 0, sizeof(S));
+    S.off = off;
+    S.remaining = in->steps;
+    S.done = 0;
+    S.nx = (int32_t)in->nx;
+    S.parity = 0;
+    S.active = 1;
+    const double dx = in->dx, dt = in->dt;
+    S.h = (float)(dt / 2.0);
+    S.idx = (float)(1.0 / dx);
+    S.hidx = (float)(0.5 / dx);
+    S.cx = (float)(dt * dt / (dx * dx));
+    S.c0 = (float)(-dt * dt * in->m * in->m);
+    S.dt2g = (float)(dt * dt * in->g);
+    S.inv_dt = (float)(1.0 / dt);
+    S.g = (float)in->g;
+    S.By = (float)in->By;
+    S.Bz = (float)in->Bz;
+    S.dx = dx;
+    S.dt = dt;
+    S.m = in->m;
+    S.gd = in->g;
+    S.Byd = in->By;
+    S.Bzd = in->Bz;
+    b->slots[s] = S;
+    cudaError_t e = cudaMemcpyAsync(b->D.slots + s, &b->slots[s], sizeof(Slot), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) {
+        const int blocks = (int)std::min<int64_t>((in->nx + 255) / 256, 1024);
+        k_batch_init<<<blocks, 256, 0, b->stream>>>(b->D, s, in->amplitude, in->k);
+        e = cudaGetLastError();
+    }
+    // the host copy of the slot must stay valid until the copy above has run
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_st(e);
+    b->dirty = true;
+    *slot = s;
+    return AXP_OK;
+}
+
+static void drop_graph(axp_batch *b)
+{
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    b->graph_steps = -1;
+}
+
+axp_status axp_batch_remove(axp_batch *b, int32_t slot)
+{
+    if (!b || slot < 0 || slot >= b->max_instances || !b->slots[slot].active) return AXP_E_INVAL;
+    Slot &S = b->slots[slot];
+    b->free.push_back({S.off, S.nx});
+    std::sort(b->free.begin(), b->free.end());
+    std::vector<std::pair<int64_t, int64_t>> merged;
+    for (auto &r : b->free) {
+        if (!merged.empty() && merged.back().first + merged.back().second == r.first) merged.back().second += r.second;
+        else merged.push_back(r);
+    }
+    b->free.swap(merged);
+    S.active = 0;
+    cudaError_t e = cudaMemcpyAsync(&b->D.slots[slot].active, &S.active, sizeof(int32_t), cudaMemcpyHostToDevice,
+                                    b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    b->dirty = true;
+    return cuda_st(e);
+}
+
+static axp_status rebuild_items(axp_batch *b)
+{
+    const int cap = kCapCells;
+    const int halo = 3 * b->block_steps;
+    int seg = b->segment_cells;
+    if (seg + 2 * halo > cap) seg = cap - 2 * halo;
+    if (seg < 64) return AXP_E_INVAL;
+    std::vector<Item> items;
+    for (int s = 0; s < b->max_instances; s++) {
+        const Slot &S = b->slots[s];
+        if (!S.active) continue;
+        if (S.nx <= cap) {
+            items.push_back({s, 0, S.nx, 1});
+        } else {
+            for (int x0 = 0; x0 < S.nx; x0 += seg) items.push_back({s, x0, std::min(seg, S.nx - x0), 0});
+        }
+    }
+    // largest items first for the persistent queue
+    std::stable_sort(items.begin(), items.end(), [](const Item &a, const Item &c) { return a.len > c.len; });
+    cudaError_t e = cudaSuccess;
+    if (!items.empty())
+        e = cudaMemcpyAsync(b->D.items, items.data(), items.size() * sizeof(Item), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_st(e);
+    b->D.nitems = (int32_t)items.size();
+    b->dirty = false;
+    return AXP_OK;
+}
+
+static cudaError_t enqueue_run(axp_batch *b, int64_t nsteps)
+{
+    const int halo = 3;  // cells of halo per step on each side of a segment
+    const size_t smem = (size_t)kCapCells * kSmemArr * sizeof(float);
+    const int grid = std::min<int>(b->sms, std::max<int>(1, b->D.nitems));
+    for (int64_t done = 0; done < nsteps; done += b->block_steps) {
+        const int budget = (int)std::min<int64_t>(b->block_steps, nsteps - done);
+        k_batch_block<<<grid, b->threads, smem, b->stream>>>(b->D, budget, halo);
+        k_batch_account<<<(b->max_instances + 255) / 256, 256, 0, b->stream>>>(b->D, b->max_instances, budget);
+        b->launches += 2;
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+axp_status axp_batch_run(axp_batch *b, int64_t nsteps)
+{
+    if (!b || nsteps < 0) return AXP_E_INVAL;
+    if (nsteps == 0) return AXP_OK;
+    if (b->dirty) {
+        drop_graph(b);
+        const axp_status st = rebuild_items(b);
+        if (st != AXP_OK) return st;
+    }
+    if (b->D.nitems == 0) return AXP_OK;
+    if (!b->use_graph || b->stream == nullptr) return cuda_st(enqueue_run(b, nsteps));
+    if (!b->graph || b->graph_steps != nsteps) {
+        drop_graph(b);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_st(e);
+        const int64_t l0 = b->launches;
+        e = enqueue_run(b, nsteps);
+        const cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+        b->launches = l0;
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return cuda_st(e != cudaSuccess ? e : e2);
+        }
+        e = cudaGraphInstantiate(&b->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            b->graph = nullptr;
+            return cuda_st(e);
+        }
+        b->graph_steps = nsteps;
+    }
+    b->launches += 2 * ((nsteps + b->block_steps - 1) / b->block_steps);
+    return cuda_st(cudaGraphLaunch(b->graph, b->stream));
+}
+
+axp_status axp_batch_use_graphs(axp_batch *b, int32_t enable)
+{
+    if (!b) return AXP_E_INVAL;
+    if (!enable) drop_graph(b);
+    b->use_graph = enable != 0;
+    return AXP_OK;
+}
+
+axp_status axp_batch_launch_count(const axp_batch *b, int64_t *count)
+{
+    if (!b || !count) return AXP_E_INVAL;
+    *count = b->launches;
+    return AXP_OK;
+}
+
+axp_status axp_batch_progress(axp_batch *b, int64_t *steps_done, int32_t max_slots)
+{
+    if (!b || !steps_done || max_slots < 0) return AXP_E_INVAL;
+    std::vector<Slot> tmp(b->max_instances);
+    cudaError_t e = cudaMemcpyAsync(tmp.data(), b->D.slots, sizeof(Slot) * b->max_instances, cudaMemcpyDeviceToHost,
+                                    b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_st(e);
+    for (int s = 0; s < std::min<int32_t>(max_slots, b->max_instances); s++)
+        steps_done[s] = b->slots[s].active ? tmp[s].done : -1;
+    return AXP_OK;
+}
+
+axp_status axp_batch_result(axp_batch *b, int32_t slot, axp_diag *out)
+{
+    if (!b || !out || slot < 0 || slot >= b->max_instances || !b->slots[slot].active) return AXP_E_INVAL;
+    axp_diag *dev = (axp_diag *)(b->ws + b->L.diag);
+    k_batch_diag<<<1, 256, 0, b->stream>>>(b->D, slot, dev);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, dev, sizeof(axp_diag), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_st(e);
+    if (!std::isfinite(out->H_phi) || !std::isfinite(out->H_g0) || !std::isfinite(out->H_g1)) return AXP_E_NONFINITE;
+    return AXP_OK;
+}
+
+axp_status axp_batch_read_state(axp_batch *b, int32_t slot, int32_t which, double *host_dst, size_t bytes)
+{
+    if (!b || !host_dst || slot < 0 || slot >= b->max_instances || !b->slots[slot].active || which < 0 || which >= kArr)
+        return AXP_E_INVAL;
+    const int64_t nx = b->slots[slot].nx;
+    if (bytes != (size_t)nx * sizeof(double)) return AXP_E_INVAL;
+    Slot S;
+    cudaError_t e = cudaMemcpyAsync(&S, b->D.slots + slot, sizeof(Slot), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_st(e);
+    std::vector<float> tmp(nx);
+    const float *src = b->D.pool + ((int64_t)(S.parity * kArr + which) * b->max_cells + S.off);
+    e = cudaMemcpyAsync(tmp.data(), src, nx * sizeof(float), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_st(e);
+    for (int64_t i = 0; i < nx; i++) host_dst[i] = tmp[i];
+    return AXP_OK;
+}
+
+axp_status axp_batch_set_tiling(axp_batch *b, int32_t block_steps, int32_t segment_cells, int32_t threads)
+{
+    if (!b || block_steps < 1 || block_steps > 256 || threads < 64 || threads > 1024 || threads % 32) return AXP_E_INVAL;
+    if (segment_cells < 64 || segment_cells + 6 * block_steps > kCapCells) return AXP_E_INVAL;
+    b->block_steps = block_steps;
+    b->segment_cells = segment_cells;
+    b->threads = threads;
+    b->dirty = true;
+    drop_graph(b);
+    return AXP_OK;
+}
+
+axp_status axp_batch_get_tiling(const axp_batch *b, int32_t *block_steps, int32_t *segment_cells, int32_t *threads)
+{
+    if (!b || !block_steps || !segment_cells || !threads) return AXP_E_INVAL;
+    *block_steps = b->block_steps;
+    *segment_cells = b->segment_cells;
+    *threads = b->threads;
+    return AXP_OK;
+}
+
+}  // extern "C"

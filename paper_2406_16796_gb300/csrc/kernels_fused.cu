@@ -4,6 +4,7 @@
 #include <utility>
 
 #include "kernels_fused.cuh"
+#include "kernels_tm2d.cuh"
 
 namespace axp {
 
@@ -11,6 +12,8 @@ cudaError_t fused_dispatch_f64(int mode, int set, const fused::Params<double> &P
                                int *occ);
 cudaError_t fused_dispatch_f32(int mode, int set, const fused::Params<float> &P, int nchunks, cudaStream_t s,
                                int *occ);
+cudaError_t tm2d_dispatch_f64(const fused::Params<double> &P, int nchunks, cudaStream_t s, int *occ);
+cudaError_t tm2d_dispatch_f32(const fused::Params<float> &P, int nchunks, cudaStream_t s, int *occ);
 
 namespace {
 
@@ -45,6 +48,36 @@ template <>
 cudaError_t dispatch<float>(int mode, int set, const fused::Params<float> &P, int nchunks, cudaStream_t s, int *occ)
 {
     return fused_dispatch_f32(mode, set, P, nchunks, s, occ);
+}
+
+template <typename T>
+cudaError_t dispatch_tm2d(const fused::Params<T> &P, int nchunks, cudaStream_t s, int *occ);
+template <>
+cudaError_t dispatch_tm2d<double>(const fused::Params<double> &P, int nchunks, cudaStream_t s, int *occ)
+{
+    return tm2d_dispatch_f64(P, nchunks, s, occ);
+}
+template <>
+cudaError_t dispatch_tm2d<float>(const fused::Params<float> &P, int nchunks, cudaStream_t s, int *occ)
+{
+    return tm2d_dispatch_f32(P, nchunks, s, occ);
+}
+
+// The 2D kernel specialised for the (E0z; B0x, B0y) laser: 2D grid, order-0
+// closure inside that set, every non-periodic side absorbing for both E/B and
+// the axion, no uniform background E.
+bool tm2d_supported(const axp_grid *g)
+{
+    if (grid_mode(g) != 2) return false;
+    if (order0_closure(g) & ~kSets[1]) return false;
+    for (int a = 0; a < 3; a++) {
+        if (g->E_ext[a] != 0.0) return false;
+        if (g->desc.n[a] > (1 << 30)) return false;
+        if (g->desc.em_bc[a][0] == AXP_BC_PERIODIC) continue;
+        for (int s = 0; s < 2; s++)
+            if (g->desc.axion_bc[a][s] != AXP_BC_PML || g->desc.em_bc[a][s] != AXP_BC_PML) return false;
+    }
+    return true;
 }
 
 template <typename T>
@@ -88,8 +121,11 @@ fused::Params<T> make_params(axp_grid *g)
         P.Bext[a] = (T)g->B_ext[a];
     }
     P.has_pml = pml && d.pml_cells > 0 && d.pml_sigma_max_dt > 0;
-    const double base = -d.dt * d.dt * (d.m * d.m + 2.0 * s_idx2);
-    P.lap_0 = (T)(d.precision == AXP_FP32_SPLIT ? base : 2.0 + base);
+    // FP64: phi^{n+3/2} = lap_0 phi + sum_a lap_c[a] (phi_a+ + phi_a-) - phi^{n-1/2} + ...
+    // FP32 split: pi^{n+1} = pi^n + lap_0 phi + sum_a lap_c[a] (second difference) + ...,
+    // the mass term alone in lap_0 so that a small (m dt)^2 keeps its FP32 precision
+    P.lap_0 = (T)(d.precision == AXP_FP32_SPLIT ? -d.dt * d.dt * d.m * d.m
+                                                : 2.0 - d.dt * d.dt * (d.m * d.m + 2.0 * s_idx2));
     P.dt2g = (T)(d.dt * d.dt * d.g);
     P.h = (T)(d.dt / 2.0);
     P.dt = (T)d.dt;
@@ -138,11 +174,24 @@ bool fused_supported(const axp_grid *g)
 }
 
 template <typename T>
+int32_t fused_path(const axp_grid *g)
+{
+    const int32_t k = g->kernel_choice;
+    if (k == AXP_KERNEL_GENERAL) return AXP_KERNEL_GENERAL;
+    const bool tm = tm2d_supported(g), fu = fused_supported<T>(g);
+    if (k == AXP_KERNEL_TM2D) return tm ? AXP_KERNEL_TM2D : AXP_KERNEL_GENERAL;
+    if (k == AXP_KERNEL_FUSED) return fu ? AXP_KERNEL_FUSED : AXP_KERNEL_GENERAL;
+    return tm ? AXP_KERNEL_TM2D : (fu ? AXP_KERNEL_FUSED : AXP_KERNEL_GENERAL);
+}
+
+template <typename T>
 cudaError_t fused_step(axp_grid *g, int64_t nsteps, bool *handled)
 {
     *handled = false;
-    if (!fused_supported<T>(g)) return cudaSuccess;
+    const int32_t path = fused_path<T>(g);
+    if (path == AXP_KERNEL_GENERAL) return cudaSuccess;
     *handled = true;
+    const bool tm = path == AXP_KERNEL_TM2D;
     const int mode = grid_mode(g);
     const int set = pick_set(g);
     cudaError_t e = enter_staggered<T>(g);
@@ -150,13 +199,13 @@ cudaError_t fused_step(axp_grid *g, int64_t nsteps, bool *handled)
     // launch geometry: as many march chunks as keep every resident CTA slot busy
     int occ = 0;
     fused::Params<T> P = make_params<T>(g);
-    e = dispatch<T>(mode, set, P, 0, g->stream, &occ);
+    e = tm ? dispatch_tm2d<T>(P, 0, g->stream, &occ) : dispatch<T>(mode, set, P, 0, g->stream, &occ);
     if (e != cudaSuccess) return e;
     int nchunks = 1;
     if (mode >= 2) {
         int sms = 152;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
-        const int VX = mode == 3 ? fused::Tile<T, 3>::VX : fused::Tile<T, 2>::VX;
+        const int VX = tm ? tm2d::VX : (mode == 3 ? fused::Tile<T, 3>::VX : fused::Tile<T, 2>::VX);
         const int VY = mode == 3 ? fused::Tile<T, 3>::VY : 1;
         const int64_t strips = ((g->desc.n[0] + VX - 1) / VX) * (mode == 3 ? (g->desc.n[1] + VY - 1) / VY : 1);
         const int64_t nm = g->desc.n[mode == 3 ? 2 : 1];
@@ -175,7 +224,7 @@ cudaError_t fused_step(axp_grid *g, int64_t nsteps, bool *handled)
             P = make_params<T>(g);
             P.chunk = ch;
         }
-        e = dispatch<T>(mode, set, P, nchunks, g->stream, nullptr);
+        e = tm ? dispatch_tm2d<T>(P, nchunks, g->stream, nullptr) : dispatch<T>(mode, set, P, nchunks, g->stream, nullptr);
         if (e != cudaSuccess) return e;
         g->launches++;
         // rotate: the output field set becomes current; axion buffers shift roles
@@ -200,6 +249,8 @@ cudaError_t fused_step(axp_grid *g, int64_t nsteps, bool *handled)
     return cudaGetLastError();
 }
 
+template int32_t fused_path<double>(const axp_grid *);
+template int32_t fused_path<float>(const axp_grid *);
 template bool fused_supported<double>(const axp_grid *);
 template bool fused_supported<float>(const axp_grid *);
 template cudaError_t fused_step<double>(axp_grid *, int64_t, bool *);

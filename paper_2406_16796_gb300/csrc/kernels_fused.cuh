@@ -425,7 +425,12 @@ struct Kernel {
         T sp[3];
         sfor<3>([&](auto A) {
             constexpr int a = decltype(A)::value;
-            if constexpr (axis_on(MODE, a))
+            // FP32 split (INCR): the second difference from neighbour differences, so
+            // it does not round against 2*phi; FP64: the neighbour sum
+            if constexpr (axis_on(MODE, a) && INCR)
+                sp[a] = (rdphi<L::DPHI, E>(L::PHI, p, a == 0, a == 1, a == 2) - ph) +
+                        (rdphi<L::DPHI, E>(L::PHI, p, -(a == 0), -(a == 1), -(a == 2)) - ph);
+            else if constexpr (axis_on(MODE, a))
                 sp[a] = rdphi<L::DPHI, E>(L::PHI, p, a == 0, a == 1, a == 2) +
                         rdphi<L::DPHI, E>(L::PHI, p, -(a == 0), -(a == 1), -(a == 2));
             else
@@ -450,7 +455,7 @@ struct Kernel {
             T lap = T(0);
             sfor<3>([&](auto A) {
                 constexpr int a = decltype(A)::value;
-                if constexpr (axis_on(MODE, a)) lap = lap + (sp[a] - T(2) * ph) * P.idx2[a];
+                if constexpr (axis_on(MODE, a)) lap = lap + (INCR ? sp[a] : sp[a] - T(2) * ph) * P.idx2[a];
             });
             const T Y = ((P.g * S - P.m2 * ph) + lap) - sig * sig * ph;
             if constexpr (INCR) {

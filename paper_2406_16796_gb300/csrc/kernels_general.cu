@@ -152,7 +152,9 @@ __global__ void __launch_bounds__(kThreads) k_axion(View<T> v, Ghosts<T> gcur)
             unit(a, u);
             const T up = ld_phi(v, v.phi_cur, gcur, i + u[0], j + u[1], k + u[2]);
             const T dn = ld_phi(v, v.phi_cur, gcur, i - u[0], j - u[1], k - u[2]);
-            lap = lap + ((up + dn) - T(2) * ph) / (v.d[a] * v.d[a]);
+            // FP32 split: from neighbour differences, which do not round against 2*phi
+            const T d2 = INCR ? (up - ph) + (dn - ph) : (up + dn) - T(2) * ph;
+            lap = lap + d2 / (v.d[a] * v.d[a]);
         }
         const T sig = sigma_of<T>(v.sig_ax, i, j, k);
         if (!INCR) {

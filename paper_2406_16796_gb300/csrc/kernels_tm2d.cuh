@@ -1,0 +1,312 @@
+// kernels_tm2d.cuh -- fused step specialised for 2D grids whose laser is the
+// (E0z; B0x, B0y) polarisation (arXiv 2406.16796 Sec. 2.3; the 2D pulse
+// workload), with periodic or absorbing (PML) edges.
+//
+// Same scheme and staggered state as kernels_fused.cuh: per step
+//   1. B^{n+1} = B^n - h curl E^{n+1/2} (twice)
+//   2. S^{n+1/2}/g = E0z B_ext,z; phi^{n+3/2}; phi^{n+1}, D_t phi^{n+1}; E0z^{n+1}
+//   3. P^{n+1} = (D_t phi) Bbar0 - Ebar0 x grad_c phi
+//   4. J^{n+1}; E^{n+3/2} = E^{n+1/2} + 2 x h (curl B^{n+1} - g J^{n+1}); E0z^{n+3/2}
+// A thread owns one x column of a tile (2 halo columns below, 3 above) and
+// marches along y; stage k works on plane t - k while plane t is loaded.  Every
+// neighbour value a stage reads along x was produced in an earlier iteration,
+// so each thread keeps its column's history along y in registers and publishes
+// only the values its x neighbours need into double-buffered shared rows at the
+// start of an iteration: one barrier per plane, no shared-memory rings.
+//
+// On the PML edges every quantity outside the grid is zero (the E/B closure and
+// the PML ghost of phi), so the edge version of the body only zeroes what it
+// computes outside and applies the damped updates inside the layer.
+#pragma once
+
+#include <type_traits>
+
+#include "kernels_fused.cuh"
+
+namespace axp {
+namespace tm2d {
+
+constexpr int TX = 256;
+constexpr int HL = 2, HR = 3;
+constexpr int VX = TX - HL - HR;
+constexpr int RS = TX + 2;  // row stride: one guard element on each side
+
+// rows published each iteration (all at x offset +1 in the row)
+enum { R_E0Z, R_E1Y, R_E1Z, R_PHI, R_N0Y2, R_MID3, R_N0Y3, R_PX4, R_N1Z4, R_N1Y4, R_N0Y4, NROWS };
+
+template <typename T, bool INCR>
+__global__ void __launch_bounds__(TX, sizeof(T) == 4 ? 2 : 1) k_tm2d(fused::Params<T> P)
+{
+    __shared__ T rows[2][NROWS][RS];
+    for (int i = threadIdx.x; i < 2 * NROWS * RS; i += TX) (&rows[0][0][0])[i] = T(0);
+
+    const int tx = threadIdx.x;
+    const int nx = P.n[0], ny = P.n[1];
+    const bool perx = P.per[0], pery = P.per[1];
+    const int gx = (int)blockIdx.x * VX - HL + tx;
+    int wx = gx;
+    if (wx < 0 || wx >= nx) wx = perx ? ((wx % nx) + nx) % nx : -1;
+    const bool write_col = tx >= HL && tx < TX - HR && gx >= 0 && gx < nx;
+    const int m0 = (int)blockIdx.y * P.chunk;
+    const int m1 = min(ny, m0 + P.chunk);
+    const int gx0 = (int)blockIdx.x * VX - HL, gx1 = gx0 + TX - 1;
+    const bool tile_fast = perx || (gx0 - 1 >= P.lay[0][0] && gx1 + 1 <= nx - 1 - P.lay[0][1]);
+    const int ylo = P.lay[1][0], yhi = ny - 1 - P.lay[1][1];
+
+    const T h = P.h, g = P.g, idx = P.idx[0], idy = P.idx[1], hidx = P.hidx[0], hidy = P.hidx[1];
+    const T cx = P.lap_c[0], cy = P.lap_c[1], c0 = P.lap_0, dt2g = P.dt2g, inv_dt = P.inv_dt;
+    const T Bx = P.Bext[0], By = P.Bext[1], Bz = P.Bext[2];
+    const T sxe = (wx >= 0 && P.has_pml) ? P.sig_em[0][wx] : T(0);
+    const T sxa = (wx >= 0 && P.has_pml) ? P.sig_ax[0][wx] : T(0);
+
+    // column history along y; suffix k = plane t - k of the current iteration
+    T E0z0 = 0, E0z1 = 0, E0z2 = 0;
+    T E1x0 = 0, E1x1 = 0, E1x2 = 0, E1x3 = 0, E1x4 = 0;
+    T E1y0 = 0, E1y1 = 0, E1y2 = 0, E1y3 = 0, E1y4 = 0;
+    T E1z0 = 0, E1z1 = 0, E1z2 = 0, E1z3 = 0, E1z4 = 0;
+    T B0x0 = 0, B0x1 = 0, B0y0 = 0, B0y1 = 0, B1x0 = 0, B1x1 = 0, B1y0 = 0, B1y1 = 0, B1z0 = 0, B1z1 = 0;
+    T ph0 = 0, ph1 = 0, ph2 = 0, ph3 = 0, pb0 = 0, pb1 = 0, pb2 = 0;
+    T N0x1 = 0, N0x2 = 0, N0x3 = 0, N0x4 = 0, N0x5 = 0;  // B^{n+1}
+    T N0y1 = 0, N0y2 = 0, N0y3 = 0, N0y4 = 0;
+    T N1x1 = 0, N1x2 = 0, N1x3 = 0, N1x4 = 0, N1x5 = 0;
+    T N1y1 = 0, N1y2 = 0, N1y3 = 0, N1y4 = 0;
+    T N1z1 = 0, N1z2 = 0, N1z3 = 0, N1z4 = 0, N1z5 = 0;
+    T MID2 = 0, MID3 = 0, MID4 = 0, DT2 = 0, DT3 = 0;  // phi^{n+1}, D_t phi^{n+1}
+    T EN2 = 0, EN3 = 0, EN4 = 0;                        // E0z^{n+1}
+    T PX3 = 0, PX4 = 0, PY3 = 0, PY4 = 0, PZ3 = 0, PZ4 = 0;
+    T pre[11];
+
+    auto gidx = [&](int p) -> int64_t {
+        int wp = p;
+        if (wp < 0 || wp >= ny) wp = pery ? ((wp % ny) + ny) % ny : -1;
+        return (wx < 0 || wp < 0) ? (int64_t)-1 : (int64_t)wx + (int64_t)nx * wp;
+    };
+    auto prefetch = [&](int p) {
+        const int64_t gi = gidx(p);
+        const bool ok = gi >= 0;
+        pre[0] = ok ? __ldg(P.Ein[2] + gi) : T(0);
+        pre[1] = ok ? __ldg(P.Ein[3] + gi) : T(0);
+        pre[2] = ok ? __ldg(P.Ein[4] + gi) : T(0);
+        pre[3] = ok ? __ldg(P.Ein[5] + gi) : T(0);
+        pre[4] = ok ? __ldg(P.Bin[0] + gi) : T(0);
+        pre[5] = ok ? __ldg(P.Bin[1] + gi) : T(0);
+        pre[6] = ok ? __ldg(P.Bin[3] + gi) : T(0);
+        pre[7] = ok ? __ldg(P.Bin[4] + gi) : T(0);
+        pre[8] = ok ? __ldg(P.Bin[5] + gi) : T(0);
+        pre[9] = ok ? __ldg(P.phi + gi) : T(0);
+        pre[10] = ok ? __ldg(P.phib + gi) : T(0);
+    };
+    auto take = [&]() {
+        E0z0 = pre[0];
+        E1x0 = pre[1];
+        E1y0 = pre[2];
+        E1z0 = pre[3];
+        B0x0 = pre[4];
+        B0y0 = pre[5];
+        B1x0 = pre[6];
+        B1y0 = pre[7];
+        B1z0 = pre[8];
+        ph0 = pre[9];
+        pb0 = pre[10];
+    };
+    auto damp = [&](T F, T X, T s) { return ((T(1) - s * h / T(2)) * F + h * X) / (T(1) + s * h / T(2)); };
+    auto inside = [&](int p) { return wx >= 0 && (pery || (p >= 0 && p < ny)); };
+    auto sig_y = [&](const T *tab, int p) { return pery ? T(0) : tab[p]; };
+    auto smax = [](T a, T b) { return a > b ? a : b; };
+
+    // one iteration's four stages; EDGE adds the closure zeros and the layer damping
+    auto body = [&](auto edge_tag, int t, int b) {
+        constexpr bool EDGE = decltype(edge_tag)::value;
+        T(*R)[RS] = rows[b];
+        // ---- stage 1: B^{n+1} on plane t-1 ----
+        {
+            const int p = t - 1;
+            const bool in = !EDGE || inside(p);
+            const T s = (EDGE && in && P.has_pml) ? smax(sxe, sig_y(P.sig_em[1], p)) : T(0);
+            const T c0x = (E0z0 - E0z1) * idy;                  // (curl E0)_x =  D_y E0z
+            const T c0y = -(R[R_E0Z][tx + 2] - E0z1) * idx;       // (curl E0)_y = -D_x E0z
+            const T c1x = (E1z0 - E1z1) * idy;
+            const T c1y = -(R[R_E1Z][tx + 2] - E1z1) * idx;
+            const T c1z = (R[R_E1Y][tx + 2] - E1y1) * idx - (E1x0 - E1x1) * idy;  // D_x E1y - D_y E1x
+            if (!EDGE || s == T(0)) {
+                N0x1 = fma(-h, c0x, fma(-h, c0x, B0x1));
+                N0y1 = fma(-h, c0y, fma(-h, c0y, B0y1));
+                N1x1 = fma(-h, c1x, fma(-h, c1x, B1x1));
+                N1y1 = fma(-h, c1y, fma(-h, c1y, B1y1));
+                N1z1 = fma(-h, c1z, fma(-h, c1z, B1z1));
+            } else {
+                N0x1 = damp(damp(B0x1, -c0x, s), -c0x, s);
+                N0y1 = damp(damp(B0y1, -c0y, s), -c0y, s);
+                N1x1 = damp(damp(B1x1, -c1x, s), -c1x, s);
+                N1y1 = damp(damp(B1y1, -c1y, s), -c1y, s);
+                N1z1 = damp(damp(B1z1, -c1z, s), -c1z, s);
+            }
+            if (EDGE && !in) N0x1 = N0y1 = N1x1 = N1y1 = N1z1 = T(0);
+            if (write_col && p >= m0 && p < m1) {
+                const int64_t gi = (int64_t)gx + (int64_t)nx * p;
+                P.Bout[0][gi] = N0x1;
+                P.Bout[1][gi] = N0y1;
+                P.Bout[3][gi] = N1x1;
+                P.Bout[4][gi] = N1y1;
+                P.Bout[5][gi] = N1z1;
+            }
+        }
+        // ---- stage 2: axion on plane t-2, E0z^{n+1} ----
+        {
+            const int p = t - 2;
+            const bool in = !EDGE || inside(p);
+            const T S = E0z2 * Bz;  // Ebar0 . Bbar0 with only E0z and the background along z
+            // FP32 split: second differences formed from neighbour differences and the
+            // mass term kept apart, so that neither rounds against the 2*phi terms
+            const T spx = INCR ? (R[R_PHI][tx + 2] - ph2) + (R[R_PHI][tx] - ph2) : R[R_PHI][tx + 2] + R[R_PHI][tx];
+            const T spy = INCR ? (ph1 - ph2) + (ph3 - ph2) : ph1 + ph3;
+            const T sa = (EDGE && in && P.has_pml) ? smax(sxa, sig_y(P.sig_ax[1], p)) : T(0);
+            T nw, pin = T(0);
+            if (!EDGE || sa == T(0)) {
+                T acc = INCR ? fma(c0, ph2, pb2) : fma(c0, ph2, -pb2);
+                acc = fma(cx, spx, acc);
+                acc = fma(cy, spy, acc);
+                acc = fma(dt2g, S, acc);
+                if (INCR) {
+                    pin = acc;
+                    nw = ph2 + pin;
+                } else {
+                    nw = acc;
+                }
+            } else {
+                const T lap = INCR ? spx * P.idx2[0] + spy * P.idx2[1]
+                                   : (spx - T(2) * ph2) * P.idx2[0] + (spy - T(2) * ph2) * P.idx2[1];
+                const T Y = ((g * S - P.m2 * ph2) + lap) - sa * sa * ph2;
+                if (INCR) {
+                    pin = (P.dt2 * Y + (T(1) - sa * P.dt) * pb2) / (T(1) + sa * P.dt);
+                    nw = ph2 + pin;
+                } else {
+                    nw = (P.dt2 * Y + sa * P.dt * pb2 + T(2) * ph2 - pb2) / (T(1) + sa * P.dt);
+                }
+            }
+            if (INCR) {
+                MID2 = fma(T(0.5), pin, ph2);
+                DT2 = pin * inv_dt;
+            } else {
+                MID2 = T(0.5) * (nw + ph2);
+                DT2 = (nw - ph2) * inv_dt;
+            }
+            if (write_col && p >= m0 && p < m1) {
+                const int64_t gi = (int64_t)gx + (int64_t)nx * p;
+                P.phi_out[gi] = nw;
+                if (INCR) P.phib_out[gi] = pin;
+            }
+            // (curl B0)_z = D_x B0y - D_y B0x at the E0z location, backward differences
+            const T cB = (N0y2 - R[R_N0Y2][tx]) * idx - (N0x2 - N0x3) * idy;
+            const T se = (EDGE && in && P.has_pml) ? smax(sxe, sig_y(P.sig_em[1], p)) : T(0);
+            EN2 = (!EDGE || se == T(0)) ? fma(h, cB, E0z2) : damp(E0z2, cB, se);
+            if (EDGE && !in) MID2 = DT2 = EN2 = T(0);
+        }
+        // ---- stage 3: P^{n+1} on plane t-3 ----
+        {
+            const int p = t - 3;
+            const T bbx = T(0.5) * (N0x3 + N0x4) + Bx;
+            const T bby = T(0.5) * (N0y3 + R[R_N0Y3][tx]) + By;
+            const T dpy = (MID2 - MID4) * hidy;
+            const T dpx = (R[R_MID3][tx + 2] - R[R_MID3][tx]) * hidx;
+            PX3 = fma(EN3, dpy, DT3 * bbx);   // Dt Bbar_x - (Ebar_y dphi_z - Ebar_z dphi_y)
+            PY3 = fma(-EN3, dpx, DT3 * bby);  // Dt Bbar_y - (Ebar_z dphi_x - Ebar_x dphi_z)
+            PZ3 = DT3 * Bz;                   // Dt Bbar_z (no laser B0z, no Ebar_x, Ebar_y)
+            if (EDGE && !inside(p)) PX3 = PY3 = PZ3 = T(0);
+        }
+        // ---- stage 4: J^{n+1}, E^{n+3/2} on plane t-4 ----
+        {
+            const int p = t - 4;
+            if (p >= m0 && p < m1) {
+                const bool in = !EDGE || inside(p);
+                const T jx = T(0.5) * (PX4 + R[R_PX4][tx + 2]);
+                const T jy = T(0.5) * (PY4 + PY3);
+                const T jz = PZ4;
+                const T cbx = (N1z4 - N1z5) * idy;                                     //  D_y B1z
+                const T cby = -(N1z4 - R[R_N1Z4][tx]) * idx;                           // -D_x B1z
+                const T cbz = (N1y4 - R[R_N1Y4][tx]) * idx - (N1x4 - N1x5) * idy;     //  D_x B1y - D_y B1x
+                const T xx = fma(-g, jx, cbx), xy = fma(-g, jy, cby), xz = fma(-g, jz, cbz);
+                const T cb0 = (N0y4 - R[R_N0Y4][tx]) * idx - (N0x4 - N0x5) * idy;
+                const T se = (EDGE && in && P.has_pml) ? smax(sxe, sig_y(P.sig_em[1], p)) : T(0);
+                T ex, ey, ez, e0;
+                if (!EDGE || se == T(0)) {
+                    ex = fma(h, xx, fma(h, xx, E1x4));
+                    ey = fma(h, xy, fma(h, xy, E1y4));
+                    ez = fma(h, xz, fma(h, xz, E1z4));
+                    e0 = fma(h, cb0, EN4);
+                } else {
+                    ex = damp(damp(E1x4, xx, se), xx, se);
+                    ey = damp(damp(E1y4, xy, se), xy, se);
+                    ez = damp(damp(E1z4, xz, se), xz, se);
+                    e0 = damp(EN4, cb0, se);
+                }
+                if (write_col) {
+                    const int64_t gi = (int64_t)gx + (int64_t)nx * p;
+                    P.Eout[3][gi] = ex;
+                    P.Eout[4][gi] = ey;
+                    P.Eout[5][gi] = ez;
+                    P.Eout[2][gi] = e0;
+                }
+            }
+        }
+    };
+
+    const int t0 = m0 - 2, t1 = m1 + 3;
+    prefetch(t0);
+    take();
+    __syncthreads();
+    for (int t = t0; t <= t1; ++t) {
+        if (t < t1) prefetch(t + 1);
+        const int b = t & 1;
+        // publish what the x neighbours read in this iteration
+        rows[b][R_E0Z][tx + 1] = E0z1;
+        rows[b][R_E1Y][tx + 1] = E1y1;
+        rows[b][R_E1Z][tx + 1] = E1z1;
+        rows[b][R_PHI][tx + 1] = ph2;
+        rows[b][R_N0Y2][tx + 1] = N0y2;
+        rows[b][R_MID3][tx + 1] = MID3;
+        rows[b][R_N0Y3][tx + 1] = N0y3;
+        rows[b][R_PX4][tx + 1] = PX4;
+        rows[b][R_N1Z4][tx + 1] = N1z4;
+        rows[b][R_N1Y4][tx + 1] = N1y4;
+        rows[b][R_N0Y4][tx + 1] = N0y4;
+        __syncthreads();
+        const bool fast = tile_fast && (pery || (t - 6 >= ylo && t + 1 <= yhi));
+        if (fast) body(std::false_type{}, t, b);
+        else body(std::true_type{}, t, b);
+        // advance the column history by one plane
+        E0z2 = E0z1; E0z1 = E0z0;
+        E1x4 = E1x3; E1x3 = E1x2; E1x2 = E1x1; E1x1 = E1x0;
+        E1y4 = E1y3; E1y3 = E1y2; E1y2 = E1y1; E1y1 = E1y0;
+        E1z4 = E1z3; E1z3 = E1z2; E1z2 = E1z1; E1z1 = E1z0;
+        B0x1 = B0x0; B0y1 = B0y0; B1x1 = B1x0; B1y1 = B1y0; B1z1 = B1z0;
+        ph3 = ph2; ph2 = ph1; ph1 = ph0; pb2 = pb1; pb1 = pb0;
+        N0x5 = N0x4; N0x4 = N0x3; N0x3 = N0x2; N0x2 = N0x1;
+        N0y4 = N0y3; N0y3 = N0y2; N0y2 = N0y1;
+        N1x5 = N1x4; N1x4 = N1x3; N1x3 = N1x2; N1x2 = N1x1;
+        N1y4 = N1y3; N1y3 = N1y2; N1y2 = N1y1;
+        N1z5 = N1z4; N1z4 = N1z3; N1z3 = N1z2; N1z2 = N1z1;
+        MID4 = MID3; MID3 = MID2; DT3 = DT2; EN4 = EN3; EN3 = EN2;
+        PX4 = PX3; PY4 = PY3; PZ4 = PZ3;
+        take();
+    }
+}
+
+template <typename T, bool INCR>
+cudaError_t launch(const fused::Params<T> &P, int nchunks, cudaStream_t stream, int *occupancy)
+{
+    static int occ = 0;
+    auto kern = k_tm2d<T, INCR>;
+    if (occ == 0) {
+        const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TX, 0);
+        if (e != cudaSuccess) return e;
+    }
+    if (occupancy) *occupancy = occ;
+    if (nchunks <= 0) return cudaSuccess;
+    dim3 grid((P.n[0] + VX - 1) / VX, nchunks, 1);
+    kern<<<grid, TX, 0, stream>>>(P);
+    return cudaGetLastError();
+}
+
+}  // namespace tm2d
+}  // namespace axp

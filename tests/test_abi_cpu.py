@@ -81,3 +81,15 @@ def test_create_rejects_small_or_null_workspace():
     d = _desc()
     h = C.c_void_p()
     assert axp.lib().axp_create_grid(C.byref(d), None, 0, None, C.byref(h)) == axp.AXP_E_INVAL
+
+
+def test_batch_workspace_validation():
+    from paper_2406_16796_gb300 import batch
+
+    a = batch.axp_batch_workspace_bytes(4, 10000)
+    b = batch.axp_batch_workspace_bytes(4, 20000)
+    assert b > a > 2 * 8 * 10000 * 4
+    with pytest.raises(axp.AxpError):
+        batch.axp_batch_workspace_bytes(0, 10000)
+    with pytest.raises(axp.AxpError):
+        batch.axp_batch_workspace_bytes(4, 4)

@@ -281,3 +281,51 @@ def test_fused_matches_general_over_many_steps(prec):
     assert [r["step"] for r in da] == [r["step"] for r in db] == [50, 100, 150, 200, 250, 300]
     for ra, rb in zip(da, db):
         assert rb["P_g2a"] == pytest.approx(ra["P_g2a"], rel=1e-10 if prec == "fp64" else 1e-3)
+
+
+TM2D_CASES = {
+    "periodic": dict(n=(600, 90, 1), B_ext=(0.2, -0.4, 1.0)),
+    "pml": dict(n=(520, 130, 1), B_ext=(0.1, 0.3, 1.0), axion_bc=W._bcs("pml", "pml"),
+                em_bc=W._bcs("pml", "pml"), pml_cells=8),
+    "periodic_x_pml_y": dict(n=(560, 100, 1), B_ext=(0.0, 0.0, 1.0), axion_bc=W._bcs("periodic", "pml"),
+                             em_bc=W._bcs("periodic", "pml"), pml_cells=6),
+}
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("case", sorted(TM2D_CASES))
+def test_tm2d_kernel_vs_oracle(case, prec):
+    """The 2D kernel specialised for the (E0z; B0x, B0y) laser against the oracle on
+    random states: several x tiles, march chunks with ragged tails, PML layers and
+    periodic wrap, all fields after 12 steps."""
+    axp = axp_mod()
+    grid = periodic_grid(g=0.7, m=1.1, **TM2D_CASES[case]).replace(precision=prec)
+    active = ["E0z", "B0x", "B0y"] + [n for n in W.FIELD_NAMES if n[1] == "1"]
+    st = W.random_state(grid, seed=404, active=active)
+    og = oracle.OracleGrid(grid.replace(precision="fp64"))
+    og.load(st)
+    g = axp.Grid(grid)
+    g.set_kernel(axp.AXP_KERNEL_TM2D)
+    g.load(st)
+    assert g.kernel_path() == axp.AXP_KERNEL_TM2D
+    og.step(12)
+    g.step(12)
+    ref, got = og.fields(), g.fields()
+    tol = 1e-12 if prec == "fp64" else 1e-4
+    for k in NAMES:
+        assert rel(got[k], ref[k]) < tol, (case, prec, k, rel(got[k], ref[k]))
+    g.close()
+
+
+def test_tm2d_refuses_unsupported_grids():
+    """Forcing the specialised kernel on a grid it does not support is an error, not a fallback."""
+    axp = axp_mod()
+    grid = periodic_grid(g=0.7, m=1.1, n=(64, 40, 1), axion_bc=W._bcs("reflect", "pml"),
+                         em_bc=W._bcs("reflect", "pml"), pml_cells=4)
+    g = axp.Grid(grid)
+    g.set_kernel(axp.AXP_KERNEL_TM2D)
+    assert g.kernel_path() == axp.AXP_KERNEL_GENERAL
+    with pytest.raises(axp.AxpError) as e:
+        g.step(1)
+    assert e.value.status == axp.AXP_E_STATE
+    g.close()

@@ -36,7 +36,12 @@ def test_noalloc_diagnostics_match_regular_entry_point_on_two_calls():
                                           torch.cuda.current_stream().cuda_stream)
         assert got["step"] == ref["step"] == g.step_count
         for k in KEYS:
-            assert got[k] == pytest.approx(ref[k], rel=1e-12, abs=1e-300), (call, k, got[k], ref[k])
+            # the two entry points partition the sums over blocks differently; W
+            # (H_phi plus the cross energy sum(E0.E1 + B0.B1) dV) nearly cancels,
+            # so its rounding is measured against the size of its terms, which
+            # Cauchy-Schwarz bounds by H_phi + 2 sqrt(H_g0 H_g1)
+            scale = ref["H_phi"] + 2.0 * np.sqrt(ref["H_g0"] * ref["H_g1"]) if k == "W" else abs(ref[k])
+            assert abs(got[k] - ref[k]) <= 1e-12 * scale + 1e-300, (call, k, got[k], ref[k])
         assert ref["H_phi"] > 0 and ref["H_g1"] > 0
         g.step(15)
     g.close()
