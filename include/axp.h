@@ -337,6 +337,51 @@ axp_status axp_batch_set_tiling(axp_batch *batch, int32_t block_steps, int32_t s
 axp_status axp_batch_get_tiling(const axp_batch *batch, int32_t *block_steps, int32_t *segment_cells,
                                 int32_t *threads);
 
+/* ------------------------------------------------------------------------
+ * Groups of 2D grids stepped together (continuous batching of 2D runs).
+ *
+ * A group advances many independent 2D grids -- each created with
+ * axp_create_grid in FP32 split precision, with the (E0z; B0x, B0y) laser
+ * polarisation of the 2D pulse set-up (Sec. 3.2) or none, periodic or
+ * absorbing (PML on E/B and phi together) sides, no uniform background E,
+ * and diag_every = 0 -- by one persistent launch per time step.  Each launch
+ * moves every unfinished member on by exactly one step of the same scheme
+ * axp_step runs; members differ in size, mass, coupling, fields and step
+ * count.  Results equal those of axp_step on the grid alone (the same
+ * arithmetic per cell).
+ *
+ * While a grid is a member, every axp_* call on the grid itself returns
+ * AXP_E_STATE; axp_group_remove hands it back with its step count advanced
+ * by the steps the group ran on it, after which diagnostics, reads and
+ * further axp_step calls work as usual.  Memory: the group's workspace holds
+ * only per-member parameters and the tile table (the grids keep their own
+ * workspaces); admission is bounded by max_grids and max_tiles, where a grid
+ * of nx x ny cells takes ceil(nx / 251) x ceil(ny / chunk) tiles.
+ * ------------------------------------------------------------------------ */
+typedef struct axp_group axp_group;
+
+axp_status axp_group_workspace_bytes(int32_t max_grids, int32_t max_tiles, size_t *bytes);
+axp_status axp_group_create(int32_t max_grids, int32_t max_tiles, void *dev_workspace, size_t bytes,
+                            void *cuda_stream, axp_group **out);
+/* AXP_E_STATE while members remain. */
+axp_status axp_group_destroy(axp_group *group);
+/* Join a grid that will run `steps` more steps; *member receives its index.
+ * Synchronises the grid's stream.  AXP_E_INVAL for grids the group cannot
+ * step, AXP_E_NOMEM when no member index or too few tiles are free. */
+axp_status axp_group_add(axp_group *group, axp_grid *grid, int64_t steps, int32_t *member);
+/* Hand a member's grid back (finished or not); synchronises the group's stream. */
+axp_status axp_group_remove(axp_group *group, int32_t member);
+/* nsteps launches on the group's stream, asynchronous. */
+axp_status axp_group_run(axp_group *group, int64_t nsteps);
+/* Steps done per member index (-1 for free indices); synchronises. */
+axp_status axp_group_progress(axp_group *group, int64_t *steps_done, int32_t max_members);
+/* y planes per tile (default 64, >= 8); only while the group is empty. */
+axp_status axp_group_set_chunk(axp_group *group, int32_t rows);
+/* Replay each axp_group_run as one CUDA graph, kept while the step count and
+ * the membership are unchanged.  Needs a non-default stream. */
+axp_status axp_group_use_graphs(axp_group *group, int32_t enable);
+axp_status axp_group_launch_count(const axp_group *group, int64_t *count);
+
 #ifdef __cplusplus
 }
 #endif

@@ -31,6 +31,7 @@ UNITS = {
     "kernels_fused_f64.cu": [],
     "kernels_fused_f32.cu": [],
     "batch1d.cu": [],
+    "group2d.cu": [],
 }
 
 

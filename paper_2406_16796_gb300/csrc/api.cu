@@ -364,6 +364,7 @@ axp_status axp_create_grid(const axp_grid_desc *desc, void *dev_workspace, size_
 axp_status axp_destroy_grid(axp_grid *grid)
 {
     if (!grid) return AXP_E_INVAL;
+    if (grid->group) return AXP_E_STATE;
     delete grid;
     return AXP_OK;
 }
@@ -371,6 +372,7 @@ axp_status axp_destroy_grid(axp_grid *grid)
 axp_status axp_set_background_field(axp_grid *g, const double B_ext[3], const double E_ext[3])
 {
     if (!g) return AXP_E_INVAL;
+    if (g->group) return AXP_E_STATE;
     for (int a = 0; a < 3; a++) {
         if (B_ext && !std::isfinite(B_ext[a])) return AXP_E_INVAL;
         if (E_ext && !std::isfinite(E_ext[a])) return AXP_E_INVAL;
@@ -388,6 +390,7 @@ axp_status axp_set_background_field(axp_grid *g, const double B_ext[3], const do
 axp_status axp_inject_laser(axp_grid *g, const axp_laser_desc *L)
 {
     if (!g || !L) return AXP_E_INVAL;
+    if (g->group) return AXP_E_STATE;
     double kk = 0;
     for (int a = 0; a < 3; a++) {
         if (!std::isfinite(L->k[a]) || !std::isfinite(L->pol[a]) || !std::isfinite(L->centre[a])) return AXP_E_INVAL;
@@ -409,6 +412,7 @@ axp_status axp_inject_laser(axp_grid *g, const axp_laser_desc *L)
 axp_status axp_inject_axion(axp_grid *g, const axp_axion_desc *A)
 {
     if (!g || !A) return AXP_E_INVAL;
+    if (g->group) return AXP_E_STATE;
     for (int a = 0; a < 3; a++)
         if (!std::isfinite(A->k[a]) || !std::isfinite(A->centre[a])) return AXP_E_INVAL;
     if (!std::isfinite(A->amplitude) || A->waist < 0 || A->length < 0) return AXP_E_INVAL;
@@ -422,6 +426,7 @@ axp_status axp_inject_axion(axp_grid *g, const axp_axion_desc *A)
 axp_status axp_step(axp_grid *g, int64_t nsteps)
 {
     if (!g || nsteps < 0) return AXP_E_INVAL;
+    if (g->group) return AXP_E_STATE;
     if (nsteps == 0) return AXP_OK;
     cudaError_t e;
     bool handled = false;
@@ -448,6 +453,7 @@ axp_status axp_synchronize(axp_grid *g)
 axp_status axp_read_diagnostics(axp_grid *g, axp_diag *out, int64_t max, int64_t *n)
 {
     if (!g || !n || max < 0 || (max > 0 && !out)) return AXP_E_INVAL;
+    if (g->group) return AXP_E_STATE;
     *n = 0;
     cudaError_t e = cudaStreamSynchronize(g->stream);
     if (e != cudaSuccess) return cuda_status(e);
@@ -470,6 +476,7 @@ axp_status axp_read_diagnostics(axp_grid *g, axp_diag *out, int64_t max, int64_t
 axp_status axp_compute_diagnostics(axp_grid *g, axp_diag *out)
 {
     if (!g || !out) return AXP_E_INVAL;
+    if (g->group) return AXP_E_STATE;
     axp_diag *dst = scratch_slot(g);
     cudaError_t e = is_fp32(g) ? diag_compute<float>(g, dst) : diag_compute<double>(g, dst);
     if (e == cudaSuccess) e = cudaMemcpyAsync(out, dst, sizeof(axp_diag), cudaMemcpyDeviceToHost, g->stream);
@@ -488,6 +495,7 @@ static void *field_ptr(axp_grid *g, int which)
 axp_status axp_read_field(axp_grid *g, int32_t which, double *dst, size_t bytes)
 {
     if (!g || !dst || which < 0 || which > AXP_PHI_OLD) return AXP_E_INVAL;
+    if (g->group) return AXP_E_STATE;
     const int64_t N = cells(g->desc);
     if (bytes != (size_t)N * 8) return AXP_E_INVAL;
     cudaError_t e = ensure_integer(g);
@@ -509,6 +517,7 @@ axp_status axp_read_field(axp_grid *g, int32_t which, double *dst, size_t bytes)
 axp_status axp_write_field(axp_grid *g, int32_t which, const double *src, size_t bytes)
 {
     if (!g || !src || which < 0 || which > AXP_PHI_OLD) return AXP_E_INVAL;
+    if (g->group) return AXP_E_STATE;
     const int64_t N = cells(g->desc);
     if (bytes != (size_t)N * 8) return AXP_E_INVAL;
     cudaError_t e = ensure_integer(g);
@@ -575,12 +584,14 @@ static axp_status ghost_io(axp_grid *g, int32_t axis, int32_t side, int32_t leve
 axp_status axp_read_ghost(axp_grid *g, int32_t axis, int32_t side, int32_t level, double *dst, size_t bytes)
 {
     if (!dst) return AXP_E_INVAL;
+    if (g && g->group) return AXP_E_STATE;
     return ghost_io(g, axis, side, level, dst, nullptr, bytes);
 }
 
 axp_status axp_write_ghost(axp_grid *g, int32_t axis, int32_t side, int32_t level, const double *src, size_t bytes)
 {
     if (!src) return AXP_E_INVAL;
+    if (g && g->group) return AXP_E_STATE;
     return ghost_io(g, axis, side, level, nullptr, src, bytes);
 }
 
@@ -617,6 +628,7 @@ axp_status axp_save_state(axp_grid *g, void *dst, size_t bytes)
 {
     size_t need;
     if (!g || !dst || axp_state_bytes(g, &need) != AXP_OK || bytes != need) return AXP_E_INVAL;
+    if (g->group) return AXP_E_STATE;
     cudaError_t e = ensure_integer(g);
     if (e != cudaSuccess) return cuda_status(e);
     StateHeader h;
@@ -648,6 +660,7 @@ axp_status axp_load_state(axp_grid *g, const void *src, size_t bytes)
 {
     size_t need;
     if (!g || !src || axp_state_bytes(g, &need) != AXP_OK || bytes != need) return AXP_E_INVAL;
+    if (g->group) return AXP_E_STATE;
     StateHeader h;
     std::memcpy(&h, src, sizeof(h));
     if (h.magic != kStateMagic || h.bytes != need || std::memcmp(&h.desc, &g->desc, sizeof(axp_grid_desc)) != 0)
@@ -685,6 +698,7 @@ axp_status axp_get_step(const axp_grid *g, int64_t *step)
 axp_status axp_set_kernel(axp_grid *g, int32_t kernel)
 {
     if (!g || kernel < AXP_KERNEL_AUTO || kernel > AXP_KERNEL_TM2D) return AXP_E_INVAL;
+    if (g->group) return AXP_E_STATE;
     g->kernel_choice = kernel;
     return AXP_OK;
 }

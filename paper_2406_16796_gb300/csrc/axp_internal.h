@@ -77,6 +77,7 @@ struct axp_grid {
     int64_t launches;
     uint32_t active;       // bit per field array that may be non-zero
     bool phi_active;
+    void *group;           // the axp_group stepping this grid, or null
 };
 
 namespace axp {
@@ -116,6 +117,8 @@ cudaError_t exit_staggered(axp_grid *g, bool in_place);
 // mask of E0/B0 components that can become non-zero (bits 0-2 E0xyz, 3-5 B0xyz)
 uint32_t order0_closure(const axp_grid *g);
 cudaError_t ensure_integer(axp_grid *g);
+// buffer roles after one more fused step (field sets and axion slots alternate)
+void rotate_roles(axp_grid *g);
 
 axp_diag *ring_slot(axp_grid *g, int64_t index);
 

@@ -227,17 +227,7 @@ cudaError_t fused_step(axp_grid *g, int64_t nsteps, bool *handled)
         e = tm ? dispatch_tm2d<T>(P, nchunks, g->stream, nullptr) : dispatch<T>(mode, set, P, nchunks, g->stream, nullptr);
         if (e != cudaSuccess) return e;
         g->launches++;
-        // rotate: the output field set becomes current; axion buffers shift roles
-        g->fset = 1 - g->fset;
-        if (g->desc.precision == AXP_FP32_SPLIT) {
-            std::swap(g->phi_cur_slot, g->phi_next_slot);
-            std::swap(g->phi_b_slot, g->phi_next_b_slot);
-        } else {
-            const int old = g->phi_b_slot;
-            g->phi_b_slot = g->phi_cur_slot;
-            g->phi_cur_slot = g->phi_next_slot;
-            g->phi_next_slot = old;
-        }
+        rotate_roles(g);
         g->step++;
         if (g->desc.diag_every > 0 && g->step % g->desc.diag_every == 0) {
             axp_diag *dst = ring_slot(g, g->ring_written);
@@ -249,6 +239,32 @@ cudaError_t fused_step(axp_grid *g, int64_t nsteps, bool *handled)
     return cudaGetLastError();
 }
 
+void rotate_roles(axp_grid *g)
+{
+    // the output field set becomes current; the axion buffers shift roles
+    g->fset = 1 - g->fset;
+    if (g->desc.precision == AXP_FP32_SPLIT) {
+        std::swap(g->phi_cur_slot, g->phi_next_slot);
+        std::swap(g->phi_b_slot, g->phi_next_b_slot);
+    } else {
+        const int old = g->phi_b_slot;
+        g->phi_b_slot = g->phi_cur_slot;
+        g->phi_cur_slot = g->phi_next_slot;
+        g->phi_next_slot = old;
+    }
+}
+
+bool tm2d_eligible(const axp_grid *g) { return tm2d_supported(g); }
+
+template <typename T>
+fused::Params<T> tm2d_params(axp_grid *g, int chunk)
+{
+    fused::Params<T> P = make_params<T>(g);
+    P.chunk = chunk;
+    return P;
+}
+
+template fused::Params<float> tm2d_params<float>(axp_grid *, int);
 template int32_t fused_path<double>(const axp_grid *);
 template int32_t fused_path<float>(const axp_grid *);
 template bool fused_supported<double>(const axp_grid *);

@@ -113,7 +113,7 @@ struct Params {
     int lay[3][2];  // cells of absorbing layer at each side (0 where none)
     T idx[3], hidx[3], idx2[3];  // 1/d, 1/(2d), 1/d^2
     T lap_c[3];                  // dt^2/d^2
-    T lap_0;                     // two levels: 2 - dt^2 (m^2 + 2 sum 1/d^2); increment: -dt^2 (m^2 + 2 sum 1/d^2)
+    T lap_0;                     // two levels: 2 - dt^2 (m^2 + 2 sum 1/d^2); increment: -dt^2 m^2
     T dt2g;                      // dt^2 g
     T h, dt, dt2, inv_dt, g, m2;
     T Bext[3];

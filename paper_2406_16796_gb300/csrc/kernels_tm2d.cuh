@@ -34,22 +34,24 @@ constexpr int RS = TX + 2;  // row stride: one guard element on each side
 // rows published each iteration (all at x offset +1 in the row)
 enum { R_E0Z, R_E1Y, R_E1Z, R_PHI, R_N0Y2, R_MID3, R_N0Y3, R_PX4, R_N1Z4, R_N1Y4, R_N0Y4, NROWS };
 
+// One tile: x strip bx (VX written columns) and march chunk by (P.chunk planes)
+// of the grid P describes.  `rows` is the block's shared staging; the caller
+// separates consecutive tiles of one block with a barrier.
 template <typename T, bool INCR>
-__global__ void __launch_bounds__(TX, sizeof(T) == 4 ? 2 : 1) k_tm2d(fused::Params<T> P)
+__device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, const int by, T (&rows)[2][NROWS][RS])
 {
-    __shared__ T rows[2][NROWS][RS];
     for (int i = threadIdx.x; i < 2 * NROWS * RS; i += TX) (&rows[0][0][0])[i] = T(0);
 
     const int tx = threadIdx.x;
     const int nx = P.n[0], ny = P.n[1];
     const bool perx = P.per[0], pery = P.per[1];
-    const int gx = (int)blockIdx.x * VX - HL + tx;
+    const int gx = bx * VX - HL + tx;
     int wx = gx;
     if (wx < 0 || wx >= nx) wx = perx ? ((wx % nx) + nx) % nx : -1;
     const bool write_col = tx >= HL && tx < TX - HR && gx >= 0 && gx < nx;
-    const int m0 = (int)blockIdx.y * P.chunk;
+    const int m0 = by * P.chunk;
     const int m1 = min(ny, m0 + P.chunk);
-    const int gx0 = (int)blockIdx.x * VX - HL, gx1 = gx0 + TX - 1;
+    const int gx0 = bx * VX - HL, gx1 = gx0 + TX - 1;
     const bool tile_fast = perx || (gx0 - 1 >= P.lay[0][0] && gx1 + 1 <= nx - 1 - P.lay[0][1]);
     const int ylo = P.lay[1][0], yhi = ny - 1 - P.lay[1][1];
 
@@ -290,6 +292,13 @@ __global__ void __launch_bounds__(TX, sizeof(T) == 4 ? 2 : 1) k_tm2d(fused::Para
         PX4 = PX3; PY4 = PY3; PZ4 = PZ3;
         take();
     }
+}
+
+template <typename T, bool INCR>
+__global__ void __launch_bounds__(TX, sizeof(T) == 4 ? 2 : 1) k_tm2d(fused::Params<T> P)
+{
+    __shared__ T rows[2][NROWS][RS];
+    tile<T, INCR>(P, (int)blockIdx.x, (int)blockIdx.y, rows);
 }
 
 template <typename T, bool INCR>

@@ -218,6 +218,28 @@ def serve_requests(count=10000, rate_per_s=100.0, seed=SEED_BASE + 4, frac_1d=0.
     return out
 
 
+def beam_2d(nx, ny, steps=0, m=0.0, g=1e-4, B0=1.0, amplitude=1e-3, precision="fp32", pml_cells=20) -> Workload:
+    """2D conversion request: a box periodic along x and absorbing along y
+    (PML on E/B and phi), a CW E_z beam along x (waist Ly/8, a whole number of
+    wavelengths in the box), B_ext along z."""
+    dx = 1.0 / 32.0
+    dt = 0.95 * dx / math.sqrt(2.0)
+    Lx, Ly = nx * dx, ny * dx
+    grid = GridSpec(n=(nx, ny, 1), d=(dx, dx, dx), dt=dt, lo=(0.0, -Ly / 2.0, 0.0), m=m, g=g,
+                    B_ext=(0.0, 0.0, B0), axion_bc=_bcs("periodic", "pml"), em_bc=_bcs("periodic", "pml"),
+                    pml_cells=pml_cells, precision=precision)
+    waves = max(1, round(Lx))
+    laser = LaserSpec(amplitude=amplitude, k=(2.0 * math.pi * waves / Lx, 0.0, 0.0), pol=(0.0, 0.0, 1.0),
+                      centre=(0.0, 0.0, 0.0), waist=Ly / 8.0)
+    return Workload("2d_beam_%dx%d" % (nx, ny), grid, lasers=(laser,), steps=steps)
+
+
+def request_workload(r: Request, precision="fp32") -> Workload:
+    if r.ndim == 1:
+        return vacuum_1d(nx=r.n[0], steps=r.steps, g=r.g, B0=r.B0, m=r.m, precision=precision)
+    return beam_2d(r.n[0], r.n[1], steps=r.steps, m=r.m, g=r.g, B0=r.B0, precision=precision)
+
+
 # ---------------------------------------------------------------------------
 # Random states for element-wise parity tests
 # ---------------------------------------------------------------------------
