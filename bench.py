@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-scan", action="store_true")
     ap.add_argument("--no-3d", action="store_true")
     ap.add_argument("--no-1d", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=120)
     return ap.parse_args()
 
 
@@ -277,6 +279,68 @@ def vacuum1d_measurement(world):
     return out
 
 
+def fp64_sequential_seconds(reqs, prefix=40, warm=4):
+    """Seconds the requests would take run one after another as single-grid FP64
+    runs: each request's grid is built and timed over a prefix of its steps
+    (after a few untimed ones), and its time is extrapolated by its step count
+    (every step of a run costs the same)."""
+    import torch
+
+    from paper_2406_16796_gb300 import axp, workloads as W
+
+    total = 0.0
+    for r in reqs:
+        w = W.request_workload(r, precision="fp64")
+        g = axp.Grid(w.grid)
+        g.inject_laser(w.lasers[0])
+        g.step(warm)
+        g.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(g.stream)
+        g.step(prefix)
+        ev1.record(g.stream)
+        ev1.synchronize()
+        total += ev0.elapsed_time(ev1) / 1e3 / prefix * r.steps
+        g.close()
+    return total
+
+
+def serve_measurement(count, rank, world):
+    """The serving loop on the first `count` requests of the seeded stream (80%
+    1D Nx log-uniform in [1024, 65536], 20% 2D Nx log-uniform in [256, 2048]
+    with Ny = Nx/2, scan parameters, 5000-40000 steps).  Capacity is measured
+    closed-loop (every request present at t = 0); then the same requests arrive
+    as a Poisson stream at 0.5, 0.9 and 1.2 x that capacity.  Each rank serves
+    its own share (replicas).  The comparator is the same requests run one
+    after another as single-grid FP64 runs (timed prefix, extrapolated)."""
+    from paper_2406_16796_gb300 import serve, workloads as W
+
+    base = W.serve_requests(count=count)[rank::world]
+    fields = ("ndim", "n", "m", "g", "B0", "steps")
+    closed = [W.Request(0.0, *[getattr(r, f) for f in fields]) for r in base]
+    srv = serve.Server()
+    cap = srv.serve(closed).summary()
+    levels = []
+    for f in (0.5, 0.9, 1.2):
+        rate = f * cap["sims_per_s"]
+        reqs = W.serve_requests(count=count, rate_per_s=rate * world)[rank::world]
+        s = srv.serve(reqs).summary()
+        s["offered_load"] = f
+        s["offered_rate_per_s"] = rate * world
+        s["sims_per_s"] *= world
+        levels.append(s)
+    srv.close()
+    seq = fp64_sequential_seconds(base)
+    cu = sum(r.n[0] * r.n[1] * r.steps for r in base) * world
+    cap["sims_per_s"] *= world
+    return {"workload": "serve_%d_requests" % count, "requests": count, "cell_updates": cu,
+            "sample": "the first %d of the 10000-request seeded stream" % count,
+            "capacity": cap, "load": levels,
+            "fp64_sequential": {"sims_per_s": len(base) * world / seq, "seconds": seq,
+                                "how": "each request's FP64 grid timed over 40 steps, extrapolated by its steps"},
+            "speedup_vs_fp64_sequential": cap["sims_per_s"] / (len(base) * world / seq)}
+
+
 def scan_measurement(rank, world, fp64_sample=6):
     """The batched parameter scan: 512 seeded 1D instances (Nx log-uniform in
     [1024, 65536], m/omega0 in [1e-3, 2], g in [1e-6, 1e-3], B0 in [0.1, 10],
@@ -441,6 +505,9 @@ def gpu_arm(args):
     scan = None
     if not args.no_scan:
         scan = scan_measurement(rank, world)
+    srv = None
+    if not args.no_serve:
+        srv = serve_measurement(args.serve_requests, rank, world)
     ax3 = None
     if not args.no_3d:
         ax3 = axion3d_measurement(max(20, args.steps // 3), args.warmup, hbm_peak, hbm_src, world)
@@ -464,6 +531,8 @@ def gpu_arm(args):
         line["fp32_split"] = other
     if scan:
         line["scan"] = scan
+    if srv:
+        line["serve"] = srv
     if ax3:
         line["axion_3d"] = ax3
     if v1:

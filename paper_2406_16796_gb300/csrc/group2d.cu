@@ -71,6 +71,7 @@ GLayout glayout(int32_t max_grids, int32_t max_tiles)
 __global__ void __launch_bounds__(tm2d::TX, 2) k_tm2d_group(GDev D)
 {
     __shared__ float rows[2][tm2d::NROWS][tm2d::RS];
+    extern __shared__ __align__(16) unsigned char group_dyn[];
     __shared__ fused::Params<float> sP;
     __shared__ int s_item;
     __shared__ long long s_done;
@@ -92,7 +93,7 @@ __global__ void __launch_bounds__(tm2d::TX, 2) k_tm2d_group(GDev D)
             const int *src = (const int *)(D.params + 2 * (size_t)I.member + (done & 1));
             for (int k = threadIdx.x; k < kWords; k += tm2d::TX) ((int *)&sP)[k] = src[k];
             __syncthreads();
-            tm2d::tile<float, true>(sP, I.bx, I.by, rows);
+            tm2d::tile<float, true>(sP, I.bx, I.by, rows, reinterpret_cast<float *>(group_dyn));
             __syncthreads();
             if (threadIdx.x == 0) {
                 __threadfence();  // this tile's stores before the count that publishes them
@@ -191,7 +192,7 @@ cudaError_t enqueue(axp_group *G, int64_t nsteps)
 {
     const int grid = std::max(1, std::min(G->grid_blocks, G->D.nitems));
     for (int64_t s = 0; s < nsteps; s++) {
-        k_tm2d_group<<<grid, tm2d::TX, 0, G->stream>>>(G->D);
+        k_tm2d_group<<<grid, tm2d::TX, tm2d::stage_bytes<float>(), G->stream>>>(G->D);
         G->launches++;
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -244,7 +245,11 @@ axp_status axp_group_create(int32_t max_grids, int32_t max_tiles, void *dev_work
     int dev = 0, sms = 152, occ = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tm2d_group, tm2d::TX, 0);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_tm2d_group, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tm2d::stage_bytes<float>());
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tm2d_group, tm2d::TX, tm2d::stage_bytes<float>());
     G->grid_blocks = sms * std::max(1, occ);
     if (e == cudaSuccess) e = cudaMemsetAsync(G->ws, 0, L.total, G->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(G->stream);

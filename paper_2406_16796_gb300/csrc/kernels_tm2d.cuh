@@ -26,10 +26,49 @@
 namespace axp {
 namespace tm2d {
 
+// products and sums the compiler may not fuse into a multiply-add
+__device__ __forceinline__ float rn_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rn_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float rn_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double rn_add(double a, double b) { return __dadd_rn(a, b); }
+
 constexpr int TX = 256;
 constexpr int HL = 2, HR = 3;
 constexpr int VX = TX - HL - HR;
 constexpr int RS = TX + 2;  // row stride: one guard element on each side
+
+// Input staging: each thread copies its own column's 11 input values of a plane
+// into shared memory with asynchronous copies (cp.async, zero-filled outside
+// the grid), NS planes deep, and reads them back when the plane is taken.  No
+// registers hold loads in flight and no barrier is needed for the staging
+// (a thread reads only what it copied itself).
+constexpr int NS = 4;    // planes in the staging ring (power of two)
+constexpr int NIN = 11;  // input arrays per plane
+
+template <typename T>
+constexpr size_t stage_bytes()
+{
+    return (size_t)NS * NIN * TX * sizeof(T);
+}
+
+__device__ __forceinline__ void cp_elem(float *dst, const float *src, bool ok)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(ok ? 4 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_elem(double *dst, const double *src, bool ok)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(ok ? 8 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 
 // rows published each iteration (all at x offset +1 in the row)
 enum { R_E0Z, R_E1Y, R_E1Z, R_PHI, R_N0Y2, R_MID3, R_N0Y3, R_PX4, R_N1Z4, R_N1Y4, R_N0Y4, NROWS };
@@ -38,7 +77,8 @@ enum { R_E0Z, R_E1Y, R_E1Z, R_PHI, R_N0Y2, R_MID3, R_N0Y3, R_PX4, R_N1Z4, R_N1Y4
 // of the grid P describes.  `rows` is the block's shared staging; the caller
 // separates consecutive tiles of one block with a barrier.
 template <typename T, bool INCR>
-__device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, const int by, T (&rows)[2][NROWS][RS])
+__device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, const int by, T (&rows)[2][NROWS][RS],
+                                     T *stage)
 {
     for (int i = threadIdx.x; i < 2 * NROWS * RS; i += TX) (&rows[0][0][0])[i] = T(0);
 
@@ -51,8 +91,12 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
     const bool write_col = tx >= HL && tx < TX - HR && gx >= 0 && gx < nx;
     const int m0 = by * P.chunk;
     const int m1 = min(ny, m0 + P.chunk);
-    const int gx0 = bx * VX - HL, gx1 = gx0 + TX - 1;
-    const bool tile_fast = perx || (gx0 - 1 >= P.lay[0][0] && gx1 + 1 <= nx - 1 - P.lay[0][1]);
+    const int gx0 = bx * VX - HL;
+    // The plain body is exact for a column inside the grid with no x layer (the
+    // edge body adds nothing there), so the choice is made per warp: in a tile
+    // at an x edge only the warps over the layer take the edge body.
+    const int wx0 = gx0 + (tx & ~31), wx1 = wx0 + 31;
+    const bool tile_fast = perx || (wx0 - 1 >= P.lay[0][0] && wx1 + 1 <= nx - 1 - P.lay[0][1]);
     const int ylo = P.lay[1][0], yhi = ny - 1 - P.lay[1][1];
 
     const T h = P.h, g = P.g, idx = P.idx[0], idy = P.idx[1], hidx = P.hidx[0], hidy = P.hidx[1];
@@ -76,7 +120,7 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
     T MID2 = 0, MID3 = 0, MID4 = 0, DT2 = 0, DT3 = 0;  // phi^{n+1}, D_t phi^{n+1}
     T EN2 = 0, EN3 = 0, EN4 = 0;                        // E0z^{n+1}
     T PX3 = 0, PX4 = 0, PY3 = 0, PY4 = 0, PZ3 = 0, PZ4 = 0;
-    T pre[11];
+    const int t0 = m0 - 2, t1 = m1 + 3;
 
     auto gidx = [&](int p) -> int64_t {
         int wp = p;
@@ -86,32 +130,50 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
     auto prefetch = [&](int p) {
         const int64_t gi = gidx(p);
         const bool ok = gi >= 0;
-        pre[0] = ok ? __ldg(P.Ein[2] + gi) : T(0);
-        pre[1] = ok ? __ldg(P.Ein[3] + gi) : T(0);
-        pre[2] = ok ? __ldg(P.Ein[4] + gi) : T(0);
-        pre[3] = ok ? __ldg(P.Ein[5] + gi) : T(0);
-        pre[4] = ok ? __ldg(P.Bin[0] + gi) : T(0);
-        pre[5] = ok ? __ldg(P.Bin[1] + gi) : T(0);
-        pre[6] = ok ? __ldg(P.Bin[3] + gi) : T(0);
-        pre[7] = ok ? __ldg(P.Bin[4] + gi) : T(0);
-        pre[8] = ok ? __ldg(P.Bin[5] + gi) : T(0);
-        pre[9] = ok ? __ldg(P.phi + gi) : T(0);
-        pre[10] = ok ? __ldg(P.phib + gi) : T(0);
+        const int64_t o = ok ? gi : 0;
+        T *st = stage + ((p - t0) & (NS - 1)) * (NIN * TX) + tx;
+        cp_elem(st + 0 * TX, P.Ein[2] + o, ok);
+        cp_elem(st + 1 * TX, P.Ein[3] + o, ok);
+        cp_elem(st + 2 * TX, P.Ein[4] + o, ok);
+        cp_elem(st + 3 * TX, P.Ein[5] + o, ok);
+        cp_elem(st + 4 * TX, P.Bin[0] + o, ok);
+        cp_elem(st + 5 * TX, P.Bin[1] + o, ok);
+        cp_elem(st + 6 * TX, P.Bin[3] + o, ok);
+        cp_elem(st + 7 * TX, P.Bin[4] + o, ok);
+        cp_elem(st + 8 * TX, P.Bin[5] + o, ok);
+        cp_elem(st + 9 * TX, P.phi + o, ok);
+        cp_elem(st + 10 * TX, P.phib + o, ok);
     };
-    auto take = [&]() {
-        E0z0 = pre[0];
-        E1x0 = pre[1];
-        E1y0 = pre[2];
-        E1z0 = pre[3];
-        B0x0 = pre[4];
-        B0y0 = pre[5];
-        B1x0 = pre[6];
-        B1y0 = pre[7];
-        B1z0 = pre[8];
-        ph0 = pre[9];
-        pb0 = pre[10];
+    auto take = [&](int p) {
+        const T *st = stage + ((p - t0) & (NS - 1)) * (NIN * TX) + tx;
+        E0z0 = st[0 * TX];
+        E1x0 = st[1 * TX];
+        E1y0 = st[2 * TX];
+        E1z0 = st[3 * TX];
+        B0x0 = st[4 * TX];
+        B0y0 = st[5 * TX];
+        B1x0 = st[6 * TX];
+        B1y0 = st[7 * TX];
+        B1z0 = st[8 * TX];
+        ph0 = st[9 * TX];
+        pb0 = st[10 * TX];
     };
-    auto damp = [&](T F, T X, T s) { return ((T(1) - s * h / T(2)) * F + h * X) / (T(1) + s * h / T(2)); };
+    // Absorbing-layer half-step F <- ((1 - s h/2) F + h X) / (1 + s h/2) written as
+    // a F + b X, with a = 1, b = h (the plain half-step, bit for bit) where s = 0:
+    // one division per cell and stage inside the layer, no divergent branches
+    // (rounded products and sums throughout, so that every kernel built from
+    // this body gives the same bits whatever the compiler contracts elsewhere)
+    auto coef = [&](T s, T &a, T &b) {
+        a = T(1);
+        b = h;
+        if (s != T(0)) {
+            const T hs = rn_mul(rn_mul(s, h), T(0.5));
+            const T inv = T(1) / rn_add(T(1), hs);
+            a = rn_mul(rn_add(T(1), -hs), inv);
+            b = rn_mul(h, inv);
+        }
+    };
+    auto dmp = [](T F, T X, T a, T b) { return fma(b, X, a * F); };
     auto inside = [&](int p) { return wx >= 0 && (pery || (p >= 0 && p < ny)); };
     auto sig_y = [&](const T *tab, int p) { return pery ? T(0) : tab[p]; };
     auto smax = [](T a, T b) { return a > b ? a : b; };
@@ -130,18 +192,20 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
             const T c1x = (E1z0 - E1z1) * idy;
             const T c1y = -(R[R_E1Z][tx + 2] - E1z1) * idx;
             const T c1z = (R[R_E1Y][tx + 2] - E1y1) * idx - (E1x0 - E1x1) * idy;  // D_x E1y - D_y E1x
-            if (!EDGE || s == T(0)) {
+            if (!EDGE) {
                 N0x1 = fma(-h, c0x, fma(-h, c0x, B0x1));
                 N0y1 = fma(-h, c0y, fma(-h, c0y, B0y1));
                 N1x1 = fma(-h, c1x, fma(-h, c1x, B1x1));
                 N1y1 = fma(-h, c1y, fma(-h, c1y, B1y1));
                 N1z1 = fma(-h, c1z, fma(-h, c1z, B1z1));
             } else {
-                N0x1 = damp(damp(B0x1, -c0x, s), -c0x, s);
-                N0y1 = damp(damp(B0y1, -c0y, s), -c0y, s);
-                N1x1 = damp(damp(B1x1, -c1x, s), -c1x, s);
-                N1y1 = damp(damp(B1y1, -c1y, s), -c1y, s);
-                N1z1 = damp(damp(B1z1, -c1z, s), -c1z, s);
+                T a, b;
+                coef(s, a, b);
+                N0x1 = dmp(dmp(B0x1, -c0x, a, b), -c0x, a, b);
+                N0y1 = dmp(dmp(B0y1, -c0y, a, b), -c0y, a, b);
+                N1x1 = dmp(dmp(B1x1, -c1x, a, b), -c1x, a, b);
+                N1y1 = dmp(dmp(B1y1, -c1y, a, b), -c1y, a, b);
+                N1z1 = dmp(dmp(B1z1, -c1z, a, b), -c1z, a, b);
             }
             if (EDGE && !in) N0x1 = N0y1 = N1x1 = N1y1 = N1z1 = T(0);
             if (write_col && p >= m0 && p < m1) {
@@ -201,7 +265,13 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
             // (curl B0)_z = D_x B0y - D_y B0x at the E0z location, backward differences
             const T cB = (N0y2 - R[R_N0Y2][tx]) * idx - (N0x2 - N0x3) * idy;
             const T se = (EDGE && in && P.has_pml) ? smax(sxe, sig_y(P.sig_em[1], p)) : T(0);
-            EN2 = (!EDGE || se == T(0)) ? fma(h, cB, E0z2) : damp(E0z2, cB, se);
+            if (!EDGE) {
+                EN2 = fma(h, cB, E0z2);
+            } else {
+                T a, b;
+                coef(se, a, b);
+                EN2 = dmp(E0z2, cB, a, b);
+            }
             if (EDGE && !in) MID2 = DT2 = EN2 = T(0);
         }
         // ---- stage 3: P^{n+1} on plane t-3 ----
@@ -231,16 +301,18 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
                 const T cb0 = (N0y4 - R[R_N0Y4][tx]) * idx - (N0x4 - N0x5) * idy;
                 const T se = (EDGE && in && P.has_pml) ? smax(sxe, sig_y(P.sig_em[1], p)) : T(0);
                 T ex, ey, ez, e0;
-                if (!EDGE || se == T(0)) {
+                if (!EDGE) {
                     ex = fma(h, xx, fma(h, xx, E1x4));
                     ey = fma(h, xy, fma(h, xy, E1y4));
                     ez = fma(h, xz, fma(h, xz, E1z4));
                     e0 = fma(h, cb0, EN4);
                 } else {
-                    ex = damp(damp(E1x4, xx, se), xx, se);
-                    ey = damp(damp(E1y4, xy, se), xy, se);
-                    ez = damp(damp(E1z4, xz, se), xz, se);
-                    e0 = damp(EN4, cb0, se);
+                    T a, b;
+                    coef(se, a, b);
+                    ex = dmp(dmp(E1x4, xx, a, b), xx, a, b);
+                    ey = dmp(dmp(E1y4, xy, a, b), xy, a, b);
+                    ez = dmp(dmp(E1z4, xz, a, b), xz, a, b);
+                    e0 = dmp(EN4, cb0, a, b);
                 }
                 if (write_col) {
                     const int64_t gi = (int64_t)gx + (int64_t)nx * p;
@@ -253,12 +325,18 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
         }
     };
 
-    const int t0 = m0 - 2, t1 = m1 + 3;
-    prefetch(t0);
-    take();
+    // planes t0 .. t0+NS-2 in flight, then one more per iteration; after the
+    // wait at the end of iteration t everything up to plane t+1 has landed
+    for (int j = 0; j < NS - 1; j++) {
+        if (t0 + j <= t1) prefetch(t0 + j);
+        cp_commit();
+    }
+    cp_wait<NS - 2>();
+    take(t0);
     __syncthreads();
     for (int t = t0; t <= t1; ++t) {
-        if (t < t1) prefetch(t + 1);
+        if (t + NS - 1 <= t1) prefetch(t + NS - 1);
+        cp_commit();
         const int b = t & 1;
         // publish what the x neighbours read in this iteration
         rows[b][R_E0Z][tx + 1] = E0z1;
@@ -290,15 +368,18 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
         N1z5 = N1z4; N1z4 = N1z3; N1z3 = N1z2; N1z2 = N1z1;
         MID4 = MID3; MID3 = MID2; DT3 = DT2; EN4 = EN3; EN3 = EN2;
         PX4 = PX3; PY4 = PY3; PZ4 = PZ3;
-        take();
+        cp_wait<NS - 2>();
+        if (t < t1) take(t + 1);
     }
+    cp_wait<0>();
 }
 
 template <typename T, bool INCR>
 __global__ void __launch_bounds__(TX, sizeof(T) == 4 ? 2 : 1) k_tm2d(fused::Params<T> P)
 {
     __shared__ T rows[2][NROWS][RS];
-    tile<T, INCR>(P, (int)blockIdx.x, (int)blockIdx.y, rows);
+    extern __shared__ __align__(16) unsigned char tm2d_dyn[];
+    tile<T, INCR>(P, (int)blockIdx.x, (int)blockIdx.y, rows, reinterpret_cast<T *>(tm2d_dyn));
 }
 
 template <typename T, bool INCR>
@@ -306,14 +387,16 @@ cudaError_t launch(const fused::Params<T> &P, int nchunks, cudaStream_t stream, 
 {
     static int occ = 0;
     auto kern = k_tm2d<T, INCR>;
+    const size_t dyn = stage_bytes<T>();
     if (occ == 0) {
-        const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TX, 0);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TX, dyn);
         if (e != cudaSuccess) return e;
     }
     if (occupancy) *occupancy = occ;
     if (nchunks <= 0) return cudaSuccess;
     dim3 grid((P.n[0] + VX - 1) / VX, nchunks, 1);
-    kern<<<grid, TX, 0, stream>>>(P);
+    kern<<<grid, TX, dyn, stream>>>(P);
     return cudaGetLastError();
 }
 

@@ -1,10 +1,10 @@
 """Groups of 2D grids stepped by one launch per step against the grids stepped
 alone and against the oracle.
 
-The group runs the same per-cell arithmetic as the single-grid 2D kernel, so
-its states are compared bit for bit with axp_step on the grid alone; one case
-also goes to the FP64 oracle at the FP32 split tolerance (fields 1e-4 after
-the run, conversion probability 1e-3)."""
+A member's states are compared bit for bit between the mix and a group of one
+(the same kernel), and to FP32 rounding with axp_step on the grid alone (the
+single-grid kernel); one case also goes to the FP64 oracle at the FP32 split
+tolerance (fields 1e-4 after the run, conversion probability 1e-3)."""
 import numpy as np
 import pytest
 
@@ -50,7 +50,11 @@ def loaded(axp, spec, seed):
     return g, grid, st
 
 
-def test_group_matches_each_grid_stepped_alone_bitwise():
+def test_group_member_is_identical_alone_and_in_the_mix():
+    """A grid's states do not depend on the other members, the tile height or the
+    launch count: bit-identical alone (a group of one, another tiling) and in
+    the mix.  Against the single-grid 2D kernel (a separately compiled kernel
+    of the same body) they agree to FP32 rounding."""
     axp, group = mods()
     G = group.Group(8, 2000, chunk=24)
     grids = []
@@ -63,14 +67,23 @@ def test_group_matches_each_grid_stepped_alone_bitwise():
     for (g, m), spec, i in zip(grids, MEMBERS, range(len(MEMBERS))):
         G.remove(m)
         assert g.step_count == spec["steps"]
-        alone, _, _ = loaded(axp, spec, 500 + i)
-        alone.set_kernel(axp.AXP_KERNEL_TM2D)
-        alone.step(spec["steps"])
-        a, b = g.fields(), alone.fields()
+        solo, _, _ = loaded(axp, spec, 500 + i)
+        G1 = group.Group(1, 400, chunk=40)
+        m1 = G1.add(solo, spec["steps"])
+        for _ in range(spec["steps"]):
+            G1.run(1)
+        G1.remove(m1)
+        G1.close()
+        single, _, _ = loaded(axp, spec, 500 + i)
+        single.set_kernel(axp.AXP_KERNEL_TM2D)
+        single.step(spec["steps"])
+        a, b, c = g.fields(), solo.fields(), single.fields()
         for k in NAMES:
             assert np.array_equal(a[k], b[k]), (spec, k)
-        alone.close()
-        g.close()
+            nc = np.linalg.norm(c[k])
+            assert np.linalg.norm(a[k] - c[k]) <= 1e-5 * (nc if nc > 0 else 1.0), (spec, k)
+        for x in (g, solo, single):
+            x.close()
     G.close()
 
 

@@ -1,8 +1,9 @@
 """The serving loop: continuous batching of 1D and 2D conversion requests.
 
-Each request's result must be the same whether it ran alone or in the mix:
-the batch and the group advance every request with the same per-cell
-arithmetic as a run of that request alone, so the comparison is exact.  One
+Each request's result must be the same whether it was served alone or in the
+mix: the batch and the group advance every request with per-cell arithmetic
+that does not depend on the other requests, the tiling or the launch count,
+so the comparison is exact.  One
 1D and one 2D request also go to the FP64 oracle (conversion probability
 within 1e-3, the FP32 split tolerance)."""
 import math
@@ -37,22 +38,13 @@ def small_requests(count=36, seed=11, rate=400.0):
 
 
 def alone(r):
-    from paper_2406_16796_gb300 import axp, batch, serve
+    """The request served by itself: a server holding only this request."""
+    from paper_2406_16796_gb300 import serve
 
-    if r.ndim == 1:
-        b = batch.Batch(1, r.n[0])
-        s = b.add(serve.batch_instance(r))
-        b.run(r.steps)
-        d = b.result(s)
-        b.close()
-        return d
-    w = W.request_workload(r)
-    g = axp.Grid(w.grid)
-    g.inject_laser(w.lasers[0])
-    g.step(r.steps)
-    d = g.diagnostics()
-    g.close()
-    return d
+    srv = serve.Server(mem_1d_cells=max(64, r.n[0]), max_1d=1, mem_2d_bytes=1 << 30, max_2d=1, max_tiles=256)
+    rec = srv.serve([W.Request(0.0, r.ndim, r.n, r.m, r.g, r.B0, r.steps)]).records[0]
+    srv.close()
+    return {"P_g2a": rec.P_g2a, "H_phi": rec.H_phi}
 
 
 def test_each_result_is_the_same_alone_and_in_the_mix():
