@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-1d", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=120)
+    ap.add_argument("--n3d", type=int, default=512, help="edge of the 3D axion box")
     return ap.parse_args()
 
 
@@ -59,6 +60,18 @@ def workload(args, precision):
 
     w = W.pulse_2d(nx=args.nx, ny=args.ny, precision=precision)
     return w
+
+
+def max_over_ranks(x, world, device="cuda"):
+    """The largest of the ranks' values of x (the job's time is its slowest rank's)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def dist_env():
@@ -190,17 +203,34 @@ def reference_arm(args):
 #  * HBM bytes: every active array read once and written once: 9 field arrays
 #    plus the axion (FP64: phi^{n+1/2}, phi^{n-1/2} read, phi^{n+3/2} written;
 #    FP32 split: phi and its increment read and written).
-#  * FLOPs (FMA = 2): 110 per cell-update, counted from the operations of the
-#    fused scheme for this component set (B update 33, axion + E0 22, axion
-#    current 17, E update 38).
+#  * FP64 operations: 77 adds, multiplies and fused multiply-adds per
+#    cell-update, 33 of them FMAs, so 110 FLOPs (FMA = 2), counted from the
+#    operations of the fused scheme for this component set (B update 22 ops /
+#    33 FLOPs, axion + E0 16 / 22, axion current 13 / 17, E update 26 / 38).
+#    Every one of them occupies the FP64 pipe for the same issue slot, so the
+#    FP64 roofline is in pipe operations.
 ACTIVE_ARRAYS = 9
 FLOPS_PER_CELL = 110
+FP64_OPS_PER_CELL = 77
 
 
 def bytes_per_cell(prec):
     e = 8 if prec == "fp64" else 4
     phi_words = 3 if prec == "fp64" else 4
     return (2 * ACTIVE_ARRAYS + phi_words) * e
+
+
+# DRAM bytes (read + write) per launch of the timed kernel at the bench's full
+# size, from ncu captures of a smaller case scaled by cells (the traffic of a
+# one-pass stencil grows with the cells); None until a capture of the kernel as
+# it stands exists.  Sources are summarised under profiles/.
+TRAFFIC = {
+    # k_tm2d, 2048 x 2048 captures: FP64 682.2 MB, FP32 split 345.3 MB per launch
+    ("k_tm2d (one launch per step)", "fp64"): 682.2e6 * (4096 * 2048) / (2048 * 2048),
+    ("k_tm2d (one launch per step)", "fp32"): 345.3e6 * (4096 * 2048) / (2048 * 2048),
+}
+# k_fused 3D (no order-0 fields), 256^3 capture: 1106.2 MB per launch
+TRAFFIC_3D_PER_CELL = 1106.2e6 / 256 ** 3
 
 
 def load_peaks():
@@ -210,9 +240,11 @@ def load_peaks():
         return {}
 
 
-# FP64 ALU peak of GB300: 2 FP64 FMA per clock per SM (1.25 TFLOP/s nominal,
-# 152 SMs at 2.07 GHz): 2 x 2 x 152 x 2.07e9.
-FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12
+# FP64 pipe of GB300: 2 FP64 operations (add, multiply or FMA) per clock per SM,
+# 152 SMs at 2.07 GHz: 629 Gop/s, i.e. 1.259 TFLOP/s when every operation is an
+# FMA (the nominal FP64 peak).
+FP64_PEAK_GOPS = 2 * 152 * 2.07e9 / 1e9
+FP64_PEAK_TFLOPS = 2 * FP64_PEAK_GOPS / 1e3
 
 
 def timed_run(g, steps, warmup, stream):
@@ -236,14 +268,15 @@ def timed_run(g, steps, warmup, stream):
 BYTES_3D_FP32 = (2 * 6 + 4) * 4
 
 
-def axion3d_measurement(steps, warmup, hbm_peak, hbm_src, world):
-    """512^3 periodic box seeded with an axion plane wave, B_ext along y, FP32
-    split (no laser: the order-0 arrays are identically zero and are skipped)."""
+def axion3d_measurement(steps, warmup, hbm_peak, hbm_src, world, n=512):
+    """n^3 (512^3) periodic box seeded with an axion plane wave, B_ext along y,
+    FP32 split (no laser: the order-0 arrays are identically zero and are
+    skipped)."""
     import torch
 
     from paper_2406_16796_gb300 import axp, workloads as W
 
-    w = W.axion_3d()
+    w = W.axion_3d(n=n)
     g = axp.Grid(w.grid)
     for a in w.axions:
         g.inject_axion(a)
@@ -255,7 +288,8 @@ def axion3d_measurement(steps, warmup, hbm_peak, hbm_src, world):
            "value": cells * steps * world / el, "unit": "cell-updates/s", "ms_per_step": el / steps * 1e3,
            "kernel_path": g.kernel_path(), "gpu_launches": launches,
            "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
-                        "peak_source": hbm_src, "algorithmic_bytes_per_cell": BYTES_3D_FP32}}
+                        "peak_source": hbm_src, "algorithmic_bytes_per_cell": BYTES_3D_FP32,
+                        "traffic": TRAFFIC_3D_PER_CELL * cells if g.kernel_path() == axp.AXP_KERNEL_FUSED else None}}
     g.close()
     torch.cuda.synchronize()
     return out
@@ -315,30 +349,34 @@ def serve_measurement(count, rank, world):
     after another as single-grid FP64 runs (timed prefix, extrapolated)."""
     from paper_2406_16796_gb300 import serve, workloads as W
 
-    base = W.serve_requests(count=count)[rank::world]
+    base = W.shard(W.serve_requests(count=count), rank, world)
     fields = ("ndim", "n", "m", "g", "B0", "steps")
     closed = [W.Request(0.0, *[getattr(r, f) for f in fields]) for r in base]
+    def job_rate(summary, n_local):
+        # all ranks' requests over the slowest rank's span (latencies are rank 0's)
+        return count / max_over_ranks(n_local / summary["sims_per_s"], world)
+
     srv = serve.Server()
     cap = srv.serve(closed).summary()
+    cap["sims_per_s"] = job_rate(cap, len(base))
     levels = []
     for f in (0.5, 0.9, 1.2):
         rate = f * cap["sims_per_s"]
-        reqs = W.serve_requests(count=count, rate_per_s=rate * world)[rank::world]
+        reqs = W.shard(W.serve_requests(count=count, rate_per_s=rate), rank, world)
         s = srv.serve(reqs).summary()
+        s["sims_per_s"] = job_rate(s, len(reqs))
         s["offered_load"] = f
-        s["offered_rate_per_s"] = rate * world
-        s["sims_per_s"] *= world
+        s["offered_rate_per_s"] = rate
         levels.append(s)
     srv.close()
-    seq = fp64_sequential_seconds(base)
-    cu = sum(r.n[0] * r.n[1] * r.steps for r in base) * world
-    cap["sims_per_s"] *= world
+    seq = max_over_ranks(fp64_sequential_seconds(base), world)
+    cu = sum(r.n[0] * r.n[1] * r.steps for r in W.serve_requests(count=count))
     return {"workload": "serve_%d_requests" % count, "requests": count, "cell_updates": cu,
             "sample": "the first %d of the 10000-request seeded stream" % count,
             "capacity": cap, "load": levels,
-            "fp64_sequential": {"sims_per_s": len(base) * world / seq, "seconds": seq,
+            "fp64_sequential": {"sims_per_s": count / seq, "seconds": seq,
                                 "how": "each request's FP64 grid timed over 40 steps, extrapolated by its steps"},
-            "speedup_vs_fp64_sequential": cap["sims_per_s"] / (len(base) * world / seq)}
+            "speedup_vs_fp64_sequential": cap["sims_per_s"] / (count / seq)}
 
 
 def scan_measurement(rank, world, fp64_sample=6):
@@ -355,18 +393,14 @@ def scan_measurement(rank, world, fp64_sample=6):
 
     from paper_2406_16796_gb300 import axp, batch as B, workloads as W
 
-    insts = W.scan_instances()[rank::world]
+    insts = W.shard(W.scan_instances(), rank, world)
     cu = sum(i.nx * i.steps for i in insts)
     res, el, tiling = B.run_scan([B.scan_instance(i) for i in insts])
-    if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([el], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        el = float(t.item())
-    total_sims = len(W.scan_instances())
-    out = {"workload": "scan_512x1d", "instances": total_sims, "cell_updates": cu * world, "seconds": el,
-           "sims_per_s": len(insts) * world / el, "cell_updates_per_s": cu * world / el, "tiling": list(tiling),
+    el = max_over_ranks(el, world)
+    every = W.scan_instances()
+    cu_all = sum(i.nx * i.steps for i in every)
+    out = {"workload": "scan_512x1d", "instances": len(every), "cell_updates": cu_all, "seconds": el,
+           "sims_per_s": len(every) / el, "cell_updates_per_s": cu_all / el, "tiling": list(tiling),
            "graphs": True, "precision": "fp32_split"}
     if rank != 0:
         return out
@@ -432,12 +466,7 @@ def gpu_arm(args):
     barrier()
     torch.cuda.synchronize()
     clk = clocks.stop()
-    if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([el], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        el = float(t.item())
+    el = max_over_ranks(el, world)
     value = cells * args.steps * world / el
     ms = el / args.steps * 1e3
     per_launch = el / max(1, launches)  # the fused path launches one kernel per step
@@ -450,17 +479,22 @@ def gpu_arm(args):
     hbm = {"achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_achieved / hbm_peak,
            "peak_source": hbm_src, "algorithmic_bytes_per_cell": bpc}
     flops = FLOPS_PER_CELL * cells / per_launch / 1e12
+    ops = FP64_OPS_PER_CELL * cells / per_launch / 1e9
     kern = {axp.AXP_KERNEL_TM2D: "k_tm2d (one launch per step)", axp.AXP_KERNEL_FUSED: "k_fused (one launch per step)"}.get(
         path, "general kernels (7 launches per step)")
     if prec == "fp64":
-        roofline = {"bound": "alu", "achieved": flops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": flops / FP64_PEAK_TFLOPS, "traffic": None, "kernel": kern,
-                    "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2.07 GHz",
-                    "algorithmic_flops_per_cell": FLOPS_PER_CELL, "hbm": hbm}
+        roofline = {"bound": "alu", "achieved": ops, "peak": FP64_PEAK_GOPS, "unit": "Gop/s (FP64 pipe)",
+                    "frac": ops / FP64_PEAK_GOPS, "traffic": TRAFFIC.get((kern, prec)) if cells == NX * NY else None, "kernel": kern,
+                    "peak_source": "derived: 2 FP64 ops/clk/SM x 152 SMs x 2.07 GHz",
+                    "algorithmic_fp64_ops_per_cell": FP64_OPS_PER_CELL,
+                    "flops": {"achieved": flops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                              "frac": flops / FP64_PEAK_TFLOPS, "algorithmic_flops_per_cell": FLOPS_PER_CELL},
+                    "hbm": hbm}
     else:
         roofline = {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
-                    "frac": hbm_achieved / hbm_peak, "traffic": None, "kernel": kern, "peak_source": hbm_src,
-                    "algorithmic_bytes_per_cell": bpc}
+                    "frac": hbm_achieved / hbm_peak, "traffic": TRAFFIC.get((kern, prec)) if cells == NX * NY else None,
+                    "kernel": kern,
+                    "peak_source": hbm_src, "algorithmic_bytes_per_cell": bpc}
 
     # e2e through the C ABI with pinned host buffers: upload the state, run the
     # steps reading the diagnostics record back after each, download the state
@@ -499,6 +533,7 @@ def gpu_arm(args):
                  "steps": k32, "ms_per_step": el32 / k32 * 1e3,
                  "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
                               "frac": ach / hbm_peak, "peak_source": hbm_src,
+                              "traffic": TRAFFIC.get((kern, "fp32")) if args.nx * args.ny == NX * NY else None,
                               "algorithmic_bytes_per_cell": bytes_per_cell("fp32")}}
         g32.close()
 
@@ -510,7 +545,7 @@ def gpu_arm(args):
         srv = serve_measurement(args.serve_requests, rank, world)
     ax3 = None
     if not args.no_3d:
-        ax3 = axion3d_measurement(max(20, args.steps // 3), args.warmup, hbm_peak, hbm_src, world)
+        ax3 = axion3d_measurement(max(20, args.steps // 3), args.warmup, hbm_peak, hbm_src, world, n=args.n3d)
     v1 = None
     if not args.no_1d:
         v1 = vacuum1d_measurement(world)

@@ -186,6 +186,14 @@ def scan_workload(inst: ScanInstance, precision="fp32", amplitude=1e-3) -> Workl
     return w
 
 
+def shard(items, rank, world):
+    """The share of a list of independent problems that rank `rank` of `world`
+    runs: items rank, rank + world, rank + 2 world, ... (replicas, no exchange)."""
+    if world < 1 or not 0 <= rank < world:
+        raise ValueError("rank %d of %d" % (rank, world))
+    return list(items)[rank::world]
+
+
 @dataclass
 class Request:
     arrival: float  # seconds after the start
