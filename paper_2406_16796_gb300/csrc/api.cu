@@ -84,6 +84,51 @@ void sigma_tables(const axp_grid_desc &d, bool axion, std::vector<T> out[3])
     }
 }
 
+// The layer coefficients of off_pml_tab from the FP64 profiles (em: E/B, ax: axion).
+template <typename T>
+void layer_coefficients(const axp_grid_desc &d, const std::vector<double> em[3], const std::vector<double> ax[3],
+                        std::vector<T> out[3])
+{
+    const double h = d.dt / 2.0, dt = d.dt;
+    for (int a = 0; a < 3; a++) {
+        const int64_t n = d.n[a];
+        out[a].assign(4 * n, T(0));
+        for (int64_t c = 0; c < n; c++) {
+            const double se = em[a][c], sa = ax[a][c];
+            out[a][c] = (T)((1.0 - se * h / 2.0) / (1.0 + se * h / 2.0));
+            out[a][n + c] = (T)(h / (1.0 + se * h / 2.0));
+            out[a][2 * n + c] = (T)(dt * dt / (1.0 + sa * dt));
+            out[a][3 * n + c] = (T)((1.0 - sa * dt) / (1.0 + sa * dt));
+        }
+    }
+}
+
+template <typename T>
+cudaError_t upload_layer_tables(const axp_grid_desc &d, char *ws, const Workspace &w, cudaStream_t stream)
+{
+    std::vector<double> em64[3], ax64[3];
+    sigma_tables<double>(d, false, em64);
+    sigma_tables<double>(d, true, ax64);
+    std::vector<T> em[3], ax[3], tab[3];
+    sigma_tables<T>(d, false, em);
+    sigma_tables<T>(d, true, ax);
+    layer_coefficients<T>(d, em64, ax64, tab);
+    cudaError_t e = cudaSuccess;
+    for (int a = 0; a < 3 && e == cudaSuccess; a++) {
+        e = cudaMemcpyAsync(ws + w.off_sig_em[a], em[a].data(), em[a].size() * sizeof(T), cudaMemcpyHostToDevice,
+                            stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ws + w.off_sig_ax[a], ax[a].data(), ax[a].size() * sizeof(T), cudaMemcpyHostToDevice,
+                                stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ws + w.off_pml_tab[a], tab[a].data(), tab[a].size() * sizeof(T),
+                                cudaMemcpyHostToDevice, stream);
+    }
+    // the host vectors must outlive the copies
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    return e;
+}
+
 axp_status cuda_status(cudaError_t e)
 {
     if (e == cudaSuccess) return AXP_OK;
@@ -155,6 +200,8 @@ bool compute_layout(const axp_grid_desc &d, Workspace *w)
         off += align_up((size_t)d.n[a] * e);
         w->off_sig_ax[a] = off;
         off += align_up((size_t)d.n[a] * e);
+        w->off_pml_tab[a] = off;
+        off += align_up((size_t)4 * d.n[a] * e);
     }
     int64_t nb = (cells(d) + 255) / 256;
     if (nb > 1024) nb = 1024;
@@ -326,32 +373,9 @@ axp_status axp_create_grid(const axp_grid_desc *desc, void *dev_workspace, size_
     g->kernel_choice = AXP_KERNEL_AUTO;
     cudaError_t e = cudaMemsetAsync(g->ws, 0, w.total, g->stream);
     if (e == cudaSuccess) {
-        // absorbing-layer profiles, computed once on the host
-        if (desc->precision == AXP_FP32_SPLIT) {
-            std::vector<float> em[3], ax[3];
-            sigma_tables<float>(*desc, false, em);
-            sigma_tables<float>(*desc, true, ax);
-            for (int a = 0; a < 3 && e == cudaSuccess; a++) {
-                e = cudaMemcpyAsync(g->ws + w.off_sig_em[a], em[a].data(), em[a].size() * 4, cudaMemcpyHostToDevice,
-                                    g->stream);
-                if (e == cudaSuccess)
-                    e = cudaMemcpyAsync(g->ws + w.off_sig_ax[a], ax[a].data(), ax[a].size() * 4,
-                                        cudaMemcpyHostToDevice, g->stream);
-            }
-            if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
-        } else {
-            std::vector<double> em[3], ax[3];
-            sigma_tables<double>(*desc, false, em);
-            sigma_tables<double>(*desc, true, ax);
-            for (int a = 0; a < 3 && e == cudaSuccess; a++) {
-                e = cudaMemcpyAsync(g->ws + w.off_sig_em[a], em[a].data(), em[a].size() * 8, cudaMemcpyHostToDevice,
-                                    g->stream);
-                if (e == cudaSuccess)
-                    e = cudaMemcpyAsync(g->ws + w.off_sig_ax[a], ax[a].data(), ax[a].size() * 8,
-                                        cudaMemcpyHostToDevice, g->stream);
-            }
-            if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
-        }
+        // absorbing-layer profiles and coefficients, computed once on the host
+        e = desc->precision == AXP_FP32_SPLIT ? upload_layer_tables<float>(*desc, g->ws, w, g->stream)
+                                              : upload_layer_tables<double>(*desc, g->ws, w, g->stream);
     }
     if (e != cudaSuccess) {
         delete g;

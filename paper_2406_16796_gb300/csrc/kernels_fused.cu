@@ -104,6 +104,7 @@ fused::Params<T> make_params(axp_grid *g)
     for (int a = 0; a < 3; a++) {
         P.sig_em[a] = (const T *)(g->ws + w.off_sig_em[a]);
         P.sig_ax[a] = (const T *)(g->ws + w.off_sig_ax[a]);
+        P.pml_tab[a] = (const T *)(g->ws + w.off_pml_tab[a]);
         P.n[a] = (int)d.n[a];
         P.per[a] = d.em_bc[a][0] == AXP_BC_PERIODIC;
         for (int s = 0; s < 2; s++) {

@@ -26,12 +26,6 @@
 namespace axp {
 namespace tm2d {
 
-// products and sums the compiler may not fuse into a multiply-add
-__device__ __forceinline__ float rn_mul(float a, float b) { return __fmul_rn(a, b); }
-__device__ __forceinline__ double rn_mul(double a, double b) { return __dmul_rn(a, b); }
-__device__ __forceinline__ float rn_add(float a, float b) { return __fadd_rn(a, b); }
-__device__ __forceinline__ double rn_add(double a, double b) { return __dadd_rn(a, b); }
-
 constexpr int TX = 256;
 constexpr int HL = 2, HR = 3;
 constexpr int VX = TX - HL - HR;
@@ -102,8 +96,15 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
     const T h = P.h, g = P.g, idx = P.idx[0], idy = P.idx[1], hidx = P.hidx[0], hidy = P.hidx[1];
     const T cx = P.lap_c[0], cy = P.lap_c[1], c0 = P.lap_0, dt2g = P.dt2g, inv_dt = P.inv_dt;
     const T Bx = P.Bext[0], By = P.Bext[1], Bz = P.Bext[2];
-    const T sxe = (wx >= 0 && P.has_pml) ? P.sig_em[0][wx] : T(0);
-    const T sxa = (wx >= 0 && P.has_pml) ? P.sig_ax[0][wx] : T(0);
+    const bool xl = wx >= 0 && P.has_pml;
+    const T sxa = xl ? P.sig_ax[0][wx] : T(0);
+    // this column's layer coefficients (the plain update's where there is no layer)
+    const T aex = xl ? P.pml_tab[0][wx] : T(1);
+    const T bex = xl ? P.pml_tab[0][nx + wx] : h;
+    const T c1x = xl ? P.pml_tab[0][2 * nx + wx] : P.dt2;
+    const T c2x = xl ? P.pml_tab[0][3 * nx + wx] : T(1);
+    auto smax = [](T a, T b) { return a > b ? a : b; };
+    auto smin = [](T a, T b) { return a < b ? a : b; };
 
     // column history along y; suffix k = plane t - k of the current iteration
     T E0z0 = 0, E0z1 = 0, E0z2 = 0;
@@ -159,24 +160,21 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
         pb0 = st[10 * TX];
     };
     // Absorbing-layer half-step F <- ((1 - s h/2) F + h X) / (1 + s h/2) written as
-    // a F + b X, with a = 1, b = h (the plain half-step, bit for bit) where s = 0:
-    // one division per cell and stage inside the layer, no divergent branches
-    // (rounded products and sums throughout, so that every kernel built from
-    // this body gives the same bits whatever the compiler contracts elsewhere)
-    auto coef = [&](T s, T &a, T &b) {
-        a = T(1);
-        b = h;
-        if (s != T(0)) {
-            const T hs = rn_mul(rn_mul(s, h), T(0.5));
-            const T inv = T(1) / rn_add(T(1), hs);
-            a = rn_mul(rn_add(T(1), -hs), inv);
-            b = rn_mul(h, inv);
+    // a F + b X with per-axis tables of a and b; at a corner s is the largest of
+    // the axes' values, and a, b decrease with s, so the corner's a, b are the
+    // smallest of the axes' table values.  Outside every layer a = 1, b = h and
+    // the update is the plain half-step bit for bit.
+    auto lay_em = [&](bool in, int p, T &a, T &b) {
+        a = aex;
+        b = bex;
+        if (in && !pery && P.has_pml) {
+            a = smin(a, P.pml_tab[1][p]);
+            b = smin(b, P.pml_tab[1][ny + p]);
         }
     };
     auto dmp = [](T F, T X, T a, T b) { return fma(b, X, a * F); };
     auto inside = [&](int p) { return wx >= 0 && (pery || (p >= 0 && p < ny)); };
     auto sig_y = [&](const T *tab, int p) { return pery ? T(0) : tab[p]; };
-    auto smax = [](T a, T b) { return a > b ? a : b; };
 
     // one iteration's four stages; EDGE adds the closure zeros and the layer damping
     auto body = [&](auto edge_tag, int t, int b) {
@@ -186,7 +184,6 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
         {
             const int p = t - 1;
             const bool in = !EDGE || inside(p);
-            const T s = (EDGE && in && P.has_pml) ? smax(sxe, sig_y(P.sig_em[1], p)) : T(0);
             const T c0x = (E0z0 - E0z1) * idy;                  // (curl E0)_x =  D_y E0z
             const T c0y = -(R[R_E0Z][tx + 2] - E0z1) * idx;       // (curl E0)_y = -D_x E0z
             const T c1x = (E1z0 - E1z1) * idy;
@@ -200,7 +197,7 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
                 N1z1 = fma(-h, c1z, fma(-h, c1z, B1z1));
             } else {
                 T a, b;
-                coef(s, a, b);
+                lay_em(in, p, a, b);
                 N0x1 = dmp(dmp(B0x1, -c0x, a, b), -c0x, a, b);
                 N0y1 = dmp(dmp(B0y1, -c0y, a, b), -c0y, a, b);
                 N1x1 = dmp(dmp(B1x1, -c1x, a, b), -c1x, a, b);
@@ -243,11 +240,18 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
                 const T lap = INCR ? spx * P.idx2[0] + spy * P.idx2[1]
                                    : (spx - T(2) * ph2) * P.idx2[0] + (spy - T(2) * ph2) * P.idx2[1];
                 const T Y = ((g * S - P.m2 * ph2) + lap) - sa * sa * ph2;
+                // damped leapfrog (1 + s dt) pi^{n+1} = dt^2 Y + (1 - s dt) pi^n as
+                // pi^{n+1} = c1 Y + c2 pi^n, with the corner's (smallest) coefficients
+                T c1 = c1x, c2 = c2x;
+                if (!pery) {
+                    c1 = smin(c1, P.pml_tab[1][2 * ny + p]);
+                    c2 = smin(c2, P.pml_tab[1][3 * ny + p]);
+                }
                 if (INCR) {
-                    pin = (P.dt2 * Y + (T(1) - sa * P.dt) * pb2) / (T(1) + sa * P.dt);
+                    pin = fma(c1, Y, c2 * pb2);
                     nw = ph2 + pin;
                 } else {
-                    nw = (P.dt2 * Y + sa * P.dt * pb2 + T(2) * ph2 - pb2) / (T(1) + sa * P.dt);
+                    nw = ph2 + fma(c1, Y, c2 * (ph2 - pb2));
                 }
             }
             if (INCR) {
@@ -264,12 +268,11 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
             }
             // (curl B0)_z = D_x B0y - D_y B0x at the E0z location, backward differences
             const T cB = (N0y2 - R[R_N0Y2][tx]) * idx - (N0x2 - N0x3) * idy;
-            const T se = (EDGE && in && P.has_pml) ? smax(sxe, sig_y(P.sig_em[1], p)) : T(0);
             if (!EDGE) {
                 EN2 = fma(h, cB, E0z2);
             } else {
                 T a, b;
-                coef(se, a, b);
+                lay_em(in, p, a, b);
                 EN2 = dmp(E0z2, cB, a, b);
             }
             if (EDGE && !in) MID2 = DT2 = EN2 = T(0);
@@ -299,7 +302,6 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
                 const T cbz = (N1y4 - R[R_N1Y4][tx]) * idx - (N1x4 - N1x5) * idy;     //  D_x B1y - D_y B1x
                 const T xx = fma(-g, jx, cbx), xy = fma(-g, jy, cby), xz = fma(-g, jz, cbz);
                 const T cb0 = (N0y4 - R[R_N0Y4][tx]) * idx - (N0x4 - N0x5) * idy;
-                const T se = (EDGE && in && P.has_pml) ? smax(sxe, sig_y(P.sig_em[1], p)) : T(0);
                 T ex, ey, ez, e0;
                 if (!EDGE) {
                     ex = fma(h, xx, fma(h, xx, E1x4));
@@ -308,7 +310,7 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
                     e0 = fma(h, cb0, EN4);
                 } else {
                     T a, b;
-                    coef(se, a, b);
+                    lay_em(in, p, a, b);
                     ex = dmp(dmp(E1x4, xx, a, b), xx, a, b);
                     ey = dmp(dmp(E1y4, xy, a, b), xy, a, b);
                     ez = dmp(dmp(E1z4, xz, a, b), xz, a, b);
