@@ -229,8 +229,8 @@ TRAFFIC = {
     ("k_tm2d (one launch per step)", "fp64"): 682.2e6 * (4096 * 2048) / (2048 * 2048),
     ("k_tm2d (one launch per step)", "fp32"): 345.3e6 * (4096 * 2048) / (2048 * 2048),
 }
-# k_fused 3D (no order-0 fields), 256^3 capture: 1106.2 MB per launch
-TRAFFIC_3D_PER_CELL = 1106.2e6 / 256 ** 3
+# k_ax3d (3D, no order-0 fields), 256^3 capture: 1088.9 MB per launch
+TRAFFIC_3D_PER_CELL = 1088.9e6 / 256 ** 3
 
 
 def load_peaks():
@@ -289,7 +289,8 @@ def axion3d_measurement(steps, warmup, hbm_peak, hbm_src, world, n=512):
            "kernel_path": g.kernel_path(), "gpu_launches": launches,
            "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
                         "peak_source": hbm_src, "algorithmic_bytes_per_cell": BYTES_3D_FP32,
-                        "traffic": TRAFFIC_3D_PER_CELL * cells if g.kernel_path() == axp.AXP_KERNEL_FUSED else None}}
+                        "traffic": TRAFFIC_3D_PER_CELL * cells if g.kernel_path() == axp.AXP_KERNEL_AX3D else None},
+           "kernel": {axp.AXP_KERNEL_AX3D: "k_ax3d", axp.AXP_KERNEL_FUSED: "k_fused"}.get(g.kernel_path(), "general")}
     g.close()
     torch.cuda.synchronize()
     return out

@@ -249,11 +249,19 @@ axp_status axp_synchronize(axp_grid *grid);
  * time scheme, in the oracle's operation order); AXP_KERNEL_FUSED forces the
  * generic single-pass kernel (1D/2D/3D, periodic, reflect and PML edges);
  * AXP_KERNEL_TM2D forces the single-pass kernel specialised for 2D grids with
- * an (E0z; B0x, B0y) laser and periodic or PML edges.  Forcing a kernel that
- * does not support the grid makes axp_step return AXP_E_STATE. */
-typedef enum { AXP_KERNEL_AUTO = 0, AXP_KERNEL_GENERAL = 1, AXP_KERNEL_FUSED = 2, AXP_KERNEL_TM2D = 3 } axp_kernel;
+ * an (E0z; B0x, B0y) laser and periodic or PML edges; AXP_KERNEL_AX3D forces
+ * the single-pass kernel specialised for periodic 3D grids with no laser
+ * fields and no uniform E (an axion wave in a uniform B).  Forcing a kernel
+ * that does not support the grid makes axp_step return AXP_E_STATE. */
+typedef enum {
+    AXP_KERNEL_AUTO = 0,
+    AXP_KERNEL_GENERAL = 1,
+    AXP_KERNEL_FUSED = 2,
+    AXP_KERNEL_TM2D = 3,
+    AXP_KERNEL_AX3D = 4
+} axp_kernel;
 axp_status axp_set_kernel(axp_grid *grid, int32_t kernel);
-/* Which path the next axp_step will take (AXP_KERNEL_GENERAL, _FUSED or _TM2D). */
+/* Which path the next axp_step will take (AXP_KERNEL_GENERAL, _FUSED, _TM2D or _AX3D). */
 axp_status axp_get_kernel_path(axp_grid *grid, int32_t *path);
 
 /* Number of kernel launches issued by this handle since creation (for

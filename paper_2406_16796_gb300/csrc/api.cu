@@ -721,7 +721,7 @@ axp_status axp_get_step(const axp_grid *g, int64_t *step)
 
 axp_status axp_set_kernel(axp_grid *g, int32_t kernel)
 {
-    if (!g || kernel < AXP_KERNEL_AUTO || kernel > AXP_KERNEL_TM2D) return AXP_E_INVAL;
+    if (!g || kernel < AXP_KERNEL_AUTO || kernel > AXP_KERNEL_AX3D) return AXP_E_INVAL;
     if (g->group) return AXP_E_STATE;
     g->kernel_choice = kernel;
     return AXP_OK;

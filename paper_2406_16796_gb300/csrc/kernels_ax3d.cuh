@@ -1,0 +1,226 @@
+// kernels_ax3d.cuh -- fused step specialised for 3D periodic grids with no
+// order-0 (laser) fields and no uniform background E: the axion box set-up
+// (arXiv 2406.16796 Sec. 2.3 update; an axion wave converting in a uniform B).
+//
+// With E0 = B0 = 0 and E_ext = 0 the scheme reduces to
+//   S = 0,  P = (D_t phi) B_ext,  J_a(c + a/2) = B_ext,a (D_t phi(c) + D_t phi(c + a)) / 2,
+// and per step, in the leapfrog-staggered state (E^{n+1/2}, B^n, phi^{n+1/2}, pi^n):
+//   1. B1^{n+1} = B1^n - h curl E1^{n+1/2} (twice)
+//   2. phi^{n+3/2}, D_t phi^{n+1} = (phi^{n+3/2} - phi^{n+1/2}) / dt
+//   3. E1^{n+3/2} = E1^{n+1/2} + 2 x h (curl B1^{n+1} - g J^{n+1})
+// the same arithmetic, operation for operation, as the generic fused kernel for
+// this component set.
+//
+// A block of TX x TY threads owns an (x, y) tile, one column per thread with a
+// halo of one column below and two above along x and y, and marches along z.
+// Stage 1 and 2 work on plane t-1 and stage 3 on plane t-2 while plane t is
+// taken in.  Each thread keeps its column's history along z in registers; the
+// values its x/y neighbours read are published into double-buffered shared
+// planes at the start of an iteration (one barrier per plane).  Inputs are
+// staged NS planes ahead with cp.async, each thread copying and later reading
+// only its own column.
+#pragma once
+
+#include "kernels_fused.cuh"
+#include "kernels_tm2d.cuh"
+
+namespace axp {
+namespace ax3d {
+
+constexpr int TX = 32, TY = 16, NT = TX * TY;
+constexpr int HL = 1, HR = 2;
+constexpr int VX = TX - HL - HR, VY = TY - HL - HR;
+constexpr int PX = TX + 2, PY = TY + 2, PLANE = PX * PY;  // published planes, one guard cell around
+constexpr int NS = 4;                                     // input staging depth (power of two)
+constexpr int NIN = 8;                                    // E1 xyz, B1 xyz, phi, second axion level
+enum { P_EX, P_EY, P_EZ, P_PHI, P_NX, P_NY, P_NZ, P_DT, NPUB };
+
+template <typename T>
+constexpr size_t smem_bytes()
+{
+    return ((size_t)2 * NPUB * PLANE + (size_t)NS * NIN * NT) * sizeof(T);
+}
+
+template <typename T, bool INCR>
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_ax3d(fused::Params<T> P)
+{
+    extern __shared__ __align__(16) unsigned char ax3d_dyn[];
+    T *pub = reinterpret_cast<T *>(ax3d_dyn);  // [2][NPUB][PY][PX]
+    T *stage = pub + 2 * NPUB * PLANE;         // [NS][NIN][NT]
+    const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
+    for (int i = tid; i < 2 * NPUB * PLANE; i += NT) pub[i] = T(0);
+
+    const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
+    const int gx = (int)blockIdx.x * VX - HL + tx, gy = (int)blockIdx.y * VY - HL + ty;
+    const int wx = ((gx % nx) + nx) % nx, wy = ((gy % ny) + ny) % ny;
+    const bool write_col = tx >= HL && tx < TX - HR && ty >= HL && ty < TY - HR && gx < nx && gy < ny;
+    const int64_t col = (int64_t)wx + (int64_t)nx * wy, plane_stride = (int64_t)nx * ny;
+    const int m0 = (int)blockIdx.z * P.chunk, m1 = min(nz, m0 + P.chunk);
+    const int t0 = m0 - 1, t1 = m1 + 1;
+
+    const T h = P.h, g = P.g, inv_dt = P.inv_dt;
+    const T idx = P.idx[0], idy = P.idx[1], idz = P.idx[2];
+    const T cx = P.lap_c[0], cy = P.lap_c[1], cz = P.lap_c[2], c0 = P.lap_0;
+    const T BEx = P.Bext[0], BEy = P.Bext[1], BEz = P.Bext[2];  // uniform background B
+
+    // column history along z; suffix k = plane t - k of the current iteration
+    T Ex0 = 0, Ex1 = 0, Ex2 = 0, Ey0 = 0, Ey1 = 0, Ey2 = 0, Ez0 = 0, Ez1 = 0, Ez2 = 0;  // E^{n+1/2}
+    T Bx0 = 0, Bx1 = 0, By0 = 0, By1 = 0, Bz0 = 0, Bz1 = 0;                             // B^n
+    T Nx1 = 0, Nx2 = 0, Nx3 = 0, Ny1 = 0, Ny2 = 0, Ny3 = 0, Nz1 = 0, Nz2 = 0;           // B^{n+1}
+    T ph0 = 0, ph1 = 0, ph2 = 0, pb0 = 0, pb1 = 0;                                       // phi^{n+1/2}, 2nd level
+    T D1 = 0, D2 = 0;                                                                     // D_t phi^{n+1}
+
+    // planes t0 - 1 .. t1 lie in [-1, nz]: at most one period off the grid
+    auto gidx = [&](int p) -> int64_t {
+        const int wp = p < 0 ? p + nz : (p >= nz ? p - nz : p);
+        return col + plane_stride * (int64_t)wp;
+    };
+    auto oidx = [&](int p) -> int64_t { return col + plane_stride * (int64_t)p; };  // p in [m0, m1)
+    auto prefetch = [&](int p) {
+        const int64_t o = gidx(p);
+        T *st = stage + ((p - t0) & (NS - 1)) * (NIN * NT) + tid;
+        tm2d::cp_elem(st + 0 * NT, P.Ein[3] + o, true);
+        tm2d::cp_elem(st + 1 * NT, P.Ein[4] + o, true);
+        tm2d::cp_elem(st + 2 * NT, P.Ein[5] + o, true);
+        tm2d::cp_elem(st + 3 * NT, P.Bin[3] + o, true);
+        tm2d::cp_elem(st + 4 * NT, P.Bin[4] + o, true);
+        tm2d::cp_elem(st + 5 * NT, P.Bin[5] + o, true);
+        tm2d::cp_elem(st + 6 * NT, P.phi + o, true);
+        tm2d::cp_elem(st + 7 * NT, P.phib + o, true);
+    };
+    auto take = [&](int p) {
+        const T *st = stage + ((p - t0) & (NS - 1)) * (NIN * NT) + tid;
+        Ex0 = st[0 * NT];
+        Ey0 = st[1 * NT];
+        Ez0 = st[2 * NT];
+        Bx0 = st[3 * NT];
+        By0 = st[4 * NT];
+        Bz0 = st[5 * NT];
+        ph0 = st[6 * NT];
+        pb0 = st[7 * NT];
+    };
+    const int me = (ty + 1) * PX + (tx + 1);  // this column's cell in a published plane
+
+    // planes t0 .. t0+NS-2 in flight, then one more per iteration
+    for (int j = 0; j < NS - 1; j++) {
+        if (t0 + j <= t1) prefetch(t0 + j);
+        tm2d::cp_commit();
+    }
+    tm2d::cp_wait<NS - 2>();
+    take(t0);
+    __syncthreads();
+    for (int t = t0; t <= t1; ++t) {
+        if (t + NS - 1 <= t1) prefetch(t + NS - 1);
+        tm2d::cp_commit();
+        T *Q = pub + (t & 1) * (NPUB * PLANE);
+        // publish what the x/y neighbours read in this iteration
+        Q[P_EX * PLANE + me] = Ex1;
+        Q[P_EY * PLANE + me] = Ey1;
+        Q[P_EZ * PLANE + me] = Ez1;
+        Q[P_PHI * PLANE + me] = ph1;
+        Q[P_NX * PLANE + me] = Nx2;
+        Q[P_NY * PLANE + me] = Ny2;
+        Q[P_NZ * PLANE + me] = Nz2;
+        Q[P_DT * PLANE + me] = D2;
+        __syncthreads();
+        const T *qEx = Q + P_EX * PLANE + me, *qEy = Q + P_EY * PLANE + me, *qEz = Q + P_EZ * PLANE + me;
+        const T *qph = Q + P_PHI * PLANE + me, *qNx = Q + P_NX * PLANE + me, *qNy = Q + P_NY * PLANE + me;
+        const T *qNz = Q + P_NZ * PLANE + me, *qDt = Q + P_DT * PLANE + me;
+
+        // ---- stage 1: B^{n+1} on plane t-1 (forward differences of E^{n+1/2}) ----
+        {
+            const int p = t - 1;
+            const T cEx = (qEz[PX] - Ez1) * idy - (Ey0 - Ey1) * idz;  // D_y E_z - D_z E_y
+            const T cEy = (Ex0 - Ex1) * idz - (qEz[1] - Ez1) * idx;   // D_z E_x - D_x E_z
+            const T cEz = (qEy[1] - Ey1) * idx - (qEx[PX] - Ex1) * idy;  // D_x E_y - D_y E_x
+            Nx1 = fma(-h, cEx, fma(-h, cEx, Bx1));
+            Ny1 = fma(-h, cEy, fma(-h, cEy, By1));
+            Nz1 = fma(-h, cEz, fma(-h, cEz, Bz1));
+            if (write_col && p >= m0 && p < m1) {
+                const int64_t gi = oidx(p);
+                P.Bout[3][gi] = Nx1;
+                P.Bout[4][gi] = Ny1;
+                P.Bout[5][gi] = Nz1;
+            }
+        }
+        // ---- stage 2: phi^{n+3/2} and D_t phi^{n+1} on plane t-1 ----
+        {
+            const int p = t - 1;
+            T nw, pin = T(0);
+            if (INCR) {
+                // second differences from neighbour differences; the mass term apart
+                const T spx = (qph[1] - ph1) + (qph[-1] - ph1);
+                const T spy = (qph[PX] - ph1) + (qph[-PX] - ph1);
+                const T spz = (ph0 - ph1) + (ph2 - ph1);
+                T acc = fma(c0, ph1, pb1);
+                acc = fma(cx, spx, acc);
+                acc = fma(cy, spy, acc);
+                acc = fma(cz, spz, acc);
+                pin = acc;
+                nw = ph1 + pin;
+                D1 = pin * inv_dt;
+            } else {
+                const T spx = qph[1] + qph[-1], spy = qph[PX] + qph[-PX], spz = ph0 + ph2;
+                T acc = fma(c0, ph1, -pb1);
+                acc = fma(cx, spx, acc);
+                acc = fma(cy, spy, acc);
+                acc = fma(cz, spz, acc);
+                nw = acc;
+                D1 = (nw - ph1) * inv_dt;
+            }
+            if (write_col && p >= m0 && p < m1) {
+                const int64_t gi = oidx(p);
+                P.phi_out[gi] = nw;
+                if (INCR) P.phib_out[gi] = pin;
+            }
+        }
+        // ---- stage 3: J^{n+1} and E^{n+3/2} on plane t-2 (backward differences of B^{n+1}) ----
+        {
+            const int p = t - 2;
+            if (write_col && p >= m0 && p < m1) {
+                // J_a = face average of P_a = D_t phi B_ext,a
+                const T jx = T(0.5) * (D2 * BEx + qDt[1] * BEx);
+                const T jy = T(0.5) * (D2 * BEy + qDt[PX] * BEy);
+                const T jz = T(0.5) * (D2 * BEz + D1 * BEz);
+                const T cBx = (Nz2 - qNz[-PX]) * idy - (Ny2 - Ny3) * idz;  // D_y B_z - D_z B_y
+                const T cBy = (Nx2 - Nx3) * idz - (Nz2 - qNz[-1]) * idx;   // D_z B_x - D_x B_z
+                const T cBz = (Ny2 - qNy[-1]) * idx - (Nx2 - qNx[-PX]) * idy;  // D_x B_y - D_y B_x
+                const T xx = fma(-g, jx, cBx), xy = fma(-g, jy, cBy), xz = fma(-g, jz, cBz);
+                const int64_t gi = oidx(p);
+                P.Eout[3][gi] = fma(h, xx, fma(h, xx, Ex2));
+                P.Eout[4][gi] = fma(h, xy, fma(h, xy, Ey2));
+                P.Eout[5][gi] = fma(h, xz, fma(h, xz, Ez2));
+            }
+        }
+        // advance the column history by one plane
+        Ex2 = Ex1; Ex1 = Ex0; Ey2 = Ey1; Ey1 = Ey0; Ez2 = Ez1; Ez1 = Ez0;
+        Bx1 = Bx0; By1 = By0; Bz1 = Bz0;
+        Nx3 = Nx2; Nx2 = Nx1; Ny3 = Ny2; Ny2 = Ny1; Nz2 = Nz1;
+        ph2 = ph1; ph1 = ph0; pb1 = pb0;
+        D2 = D1;
+        tm2d::cp_wait<NS - 2>();
+        if (t < t1) take(t + 1);
+    }
+    tm2d::cp_wait<0>();
+}
+
+template <typename T, bool INCR>
+cudaError_t launch(const fused::Params<T> &P, int nchunks, cudaStream_t stream, int *occupancy)
+{
+    static int occ = 0;
+    auto kern = k_ax3d<T, INCR>;
+    const size_t dyn = smem_bytes<T>();
+    if (occ == 0) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, dyn);
+        if (e != cudaSuccess) return e;
+    }
+    if (occupancy) *occupancy = occ;
+    if (nchunks <= 0) return cudaSuccess;
+    dim3 grid((P.n[0] + VX - 1) / VX, (P.n[1] + VY - 1) / VY, nchunks);
+    kern<<<grid, NT, dyn, stream>>>(P);
+    return cudaGetLastError();
+}
+
+}  // namespace ax3d
+}  // namespace axp

@@ -4,6 +4,7 @@
 #include <utility>
 
 #include "kernels_fused.cuh"
+#include "kernels_ax3d.cuh"
 #include "kernels_tm2d.cuh"
 
 namespace axp {
@@ -14,6 +15,8 @@ cudaError_t fused_dispatch_f32(int mode, int set, const fused::Params<float> &P,
                                int *occ);
 cudaError_t tm2d_dispatch_f64(const fused::Params<double> &P, int nchunks, cudaStream_t s, int *occ);
 cudaError_t tm2d_dispatch_f32(const fused::Params<float> &P, int nchunks, cudaStream_t s, int *occ);
+cudaError_t ax3d_dispatch_f64(const fused::Params<double> &P, int nchunks, cudaStream_t s, int *occ);
+cudaError_t ax3d_dispatch_f32(const fused::Params<float> &P, int nchunks, cudaStream_t s, int *occ);
 
 namespace {
 
@@ -61,6 +64,35 @@ template <>
 cudaError_t dispatch_tm2d<float>(const fused::Params<float> &P, int nchunks, cudaStream_t s, int *occ)
 {
     return tm2d_dispatch_f32(P, nchunks, s, occ);
+}
+
+template <typename T>
+cudaError_t dispatch_ax3d(const fused::Params<T> &P, int nchunks, cudaStream_t s, int *occ);
+template <>
+cudaError_t dispatch_ax3d<double>(const fused::Params<double> &P, int nchunks, cudaStream_t s, int *occ)
+{
+    return ax3d_dispatch_f64(P, nchunks, s, occ);
+}
+template <>
+cudaError_t dispatch_ax3d<float>(const fused::Params<float> &P, int nchunks, cudaStream_t s, int *occ)
+{
+    return ax3d_dispatch_f32(P, nchunks, s, occ);
+}
+
+// The 3D kernel specialised for an axion box: 3D grid periodic on every axis
+// (E/B and axion), no order-0 field active, no uniform background E.
+bool ax3d_supported(const axp_grid *g)
+{
+    if (grid_mode(g) != 3) return false;
+    if (order0_closure(g) != 0) return false;
+    for (int a = 0; a < 3; a++) {
+        if (g->E_ext[a] != 0.0) return false;
+        if (g->desc.n[a] > (1 << 30)) return false;
+        if (g->desc.em_bc[a][0] != AXP_BC_PERIODIC) return false;
+        for (int s = 0; s < 2; s++)
+            if (g->desc.axion_bc[a][s] != AXP_BC_PERIODIC) return false;
+    }
+    return (int64_t)g->desc.n[0] * g->desc.n[1] * g->desc.n[2] < ((int64_t)1 << 40);
 }
 
 // The 2D kernel specialised for the (E0z; B0x, B0y) laser: 2D grid, order-0
@@ -179,10 +211,11 @@ int32_t fused_path(const axp_grid *g)
 {
     const int32_t k = g->kernel_choice;
     if (k == AXP_KERNEL_GENERAL) return AXP_KERNEL_GENERAL;
-    const bool tm = tm2d_supported(g), fu = fused_supported<T>(g);
+    const bool tm = tm2d_supported(g), ax = ax3d_supported(g), fu = fused_supported<T>(g);
     if (k == AXP_KERNEL_TM2D) return tm ? AXP_KERNEL_TM2D : AXP_KERNEL_GENERAL;
+    if (k == AXP_KERNEL_AX3D) return ax ? AXP_KERNEL_AX3D : AXP_KERNEL_GENERAL;
     if (k == AXP_KERNEL_FUSED) return fu ? AXP_KERNEL_FUSED : AXP_KERNEL_GENERAL;
-    return tm ? AXP_KERNEL_TM2D : (fu ? AXP_KERNEL_FUSED : AXP_KERNEL_GENERAL);
+    return tm ? AXP_KERNEL_TM2D : (ax ? AXP_KERNEL_AX3D : (fu ? AXP_KERNEL_FUSED : AXP_KERNEL_GENERAL));
 }
 
 template <typename T>
@@ -192,18 +225,39 @@ cudaError_t fused_step(axp_grid *g, int64_t nsteps, bool *handled)
     const int32_t path = fused_path<T>(g);
     if (path == AXP_KERNEL_GENERAL) return cudaSuccess;
     *handled = true;
-    const bool tm = path == AXP_KERNEL_TM2D;
+    const bool tm = path == AXP_KERNEL_TM2D, ax = path == AXP_KERNEL_AX3D;
     const int mode = grid_mode(g);
     const int set = pick_set(g);
     cudaError_t e = enter_staggered<T>(g);
     if (e != cudaSuccess) return e;
+    auto launch = [&](const fused::Params<T> &Pl, int nch, int *occp) {
+        if (tm) return dispatch_tm2d<T>(Pl, nch, g->stream, occp);
+        if (ax) return dispatch_ax3d<T>(Pl, nch, g->stream, occp);
+        return dispatch<T>(mode, set, Pl, nch, g->stream, occp);
+    };
     // launch geometry: as many march chunks as keep every resident CTA slot busy
     int occ = 0;
     fused::Params<T> P = make_params<T>(g);
-    e = tm ? dispatch_tm2d<T>(P, 0, g->stream, &occ) : dispatch<T>(mode, set, P, 0, g->stream, &occ);
+    e = launch(P, 0, &occ);
     if (e != cudaSuccess) return e;
     int nchunks = 1;
-    if (mode >= 2) {
+    if (ax) {
+        // z chunks: fewest waves of resident blocks for the (tile + pipeline) work
+        int sms = 152;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
+        const int64_t tiles = ((g->desc.n[0] + ax3d::VX - 1) / ax3d::VX) * ((g->desc.n[1] + ax3d::VY - 1) / ax3d::VY);
+        const int64_t nz = g->desc.n[2], slots = (int64_t)sms * (occ > 0 ? occ : 1);
+        double best = 0;
+        for (int64_t nc = 1; nc <= 32 && nc <= nz; nc++) {
+            const int64_t chunk = (nz + nc - 1) / nc, waves = (tiles * nc + slots - 1) / slots;
+            const double cost = (double)waves * (double)(chunk + 3);
+            if (nc == 1 || cost < best) {
+                best = cost;
+                P.chunk = (int)chunk;
+                nchunks = (int)((nz + chunk - 1) / chunk);
+            }
+        }
+    } else if (mode >= 2) {
         int sms = 152;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
         const int VX = tm ? tm2d::VX : (mode == 3 ? fused::Tile<T, 3>::VX : fused::Tile<T, 2>::VX);
@@ -225,7 +279,7 @@ cudaError_t fused_step(axp_grid *g, int64_t nsteps, bool *handled)
             P = make_params<T>(g);
             P.chunk = ch;
         }
-        e = tm ? dispatch_tm2d<T>(P, nchunks, g->stream, nullptr) : dispatch<T>(mode, set, P, nchunks, g->stream, nullptr);
+        e = launch(P, nchunks, nullptr);
         if (e != cudaSuccess) return e;
         g->launches++;
         rotate_roles(g);

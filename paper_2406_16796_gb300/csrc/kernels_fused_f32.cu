@@ -1,6 +1,7 @@
 // FP32-split instantiations of the fused step (increment storage of phi).
 #include "kernels_fused_inst.cuh"
 #include "kernels_tm2d.cuh"
+#include "kernels_ax3d.cuh"
 
 namespace axp {
 cudaError_t fused_dispatch_f32(int mode, int set, const fused::Params<float> &P, int nchunks, cudaStream_t s,
@@ -12,5 +13,10 @@ cudaError_t fused_dispatch_f32(int mode, int set, const fused::Params<float> &P,
 cudaError_t tm2d_dispatch_f32(const fused::Params<float> &P, int nchunks, cudaStream_t s, int *occ)
 {
     return tm2d::launch<float, true>(P, nchunks, s, occ);
+}
+
+cudaError_t ax3d_dispatch_f32(const fused::Params<float> &P, int nchunks, cudaStream_t s, int *occ)
+{
+    return ax3d::launch<float, true>(P, nchunks, s, occ);
 }
 }  // namespace axp

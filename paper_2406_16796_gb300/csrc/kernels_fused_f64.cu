@@ -1,6 +1,7 @@
 // FP64 instantiations of the fused step.
 #include "kernels_fused_inst.cuh"
 #include "kernels_tm2d.cuh"
+#include "kernels_ax3d.cuh"
 
 namespace axp {
 cudaError_t fused_dispatch_f64(int mode, int set, const fused::Params<double> &P, int nchunks, cudaStream_t s,
@@ -12,5 +13,10 @@ cudaError_t fused_dispatch_f64(int mode, int set, const fused::Params<double> &P
 cudaError_t tm2d_dispatch_f64(const fused::Params<double> &P, int nchunks, cudaStream_t s, int *occ)
 {
     return tm2d::launch<double, false>(P, nchunks, s, occ);
+}
+
+cudaError_t ax3d_dispatch_f64(const fused::Params<double> &P, int nchunks, cudaStream_t s, int *occ)
+{
+    return ax3d::launch<double, false>(P, nchunks, s, occ);
 }
 }  // namespace axp

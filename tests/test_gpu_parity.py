@@ -245,7 +245,12 @@ def test_fused_vs_oracle(case, prec):
     g = axp.Grid(grid)
     g.set_kernel(axp.AXP_KERNEL_AUTO)
     g.load(st)
-    expect = axp.AXP_KERNEL_GENERAL if (case.startswith("3d") and prec == "fp64") else axp.AXP_KERNEL_FUSED
+    if case == "3d_periodic":
+        expect = axp.AXP_KERNEL_AX3D  # periodic 3D without laser fields: the specialised kernel
+    elif case.startswith("3d") and prec == "fp64":
+        expect = axp.AXP_KERNEL_GENERAL
+    else:
+        expect = axp.AXP_KERNEL_FUSED
     assert g.kernel_path() == expect
     og.step(12)
     g.step(12)
@@ -329,3 +334,64 @@ def test_tm2d_refuses_unsupported_grids():
         g.step(1)
     assert e.value.status == axp.AXP_E_STATE
     g.close()
+
+
+AX3D_CASES = {
+    "ragged": dict(n=(70, 37, 45), B_ext=(0.2, -0.5, 0.7), d=(0.05, 0.07, 0.06)),
+    "cube": dict(n=(40, 40, 40), B_ext=(0.0, 1.0, 0.0), d=(0.06, 0.06, 0.06)),
+    "thin_z": dict(n=(33, 20, 3), B_ext=(1.0, 0.5, -0.2), d=(0.05, 0.05, 0.08)),
+}
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("case", sorted(AX3D_CASES))
+def test_ax3d_kernel_vs_oracle_and_generic(case, prec):
+    """The 3D kernel specialised for an axion box (periodic, order-1 fields, phi,
+    uniform B) against the oracle on random states: several x/y tiles with
+    ragged tails and many short z chunks, all fields after 12 steps; in FP32
+    also against the generic single-pass kernel to FP32 rounding."""
+    axp = axp_mod()
+    grid = periodic_grid(g=0.7, m=1.1, **AX3D_CASES[case]).replace(precision=prec)
+    st = W.random_state(grid, seed=505, active=[n for n in W.FIELD_NAMES if n[1] == "1"])
+    og = oracle.OracleGrid(grid.replace(precision="fp64"))
+    og.load(st)
+    g = axp.Grid(grid)
+    g.set_kernel(axp.AXP_KERNEL_AX3D)
+    g.load(st)
+    assert g.kernel_path() == axp.AXP_KERNEL_AX3D
+    og.step(12)
+    g.step(12)
+    ref, got = og.fields(), g.fields()
+    tol = 1e-12 if prec == "fp64" else 1e-4
+    for k in NAMES:
+        assert rel(got[k], ref[k]) < tol, (case, prec, k, rel(got[k], ref[k]))
+    if prec == "fp32":
+        f = axp.Grid(grid)
+        f.set_kernel(axp.AXP_KERNEL_FUSED)
+        f.load(st)
+        assert f.kernel_path() == axp.AXP_KERNEL_FUSED
+        f.step(12)
+        gen = f.fields()
+        for k in NAMES:
+            assert rel(got[k], gen[k]) < 2e-6, (case, k, rel(got[k], gen[k]))
+        f.close()
+    g.close()
+
+
+def test_ax3d_refuses_grids_with_laser_fields_or_absorbing_sides():
+    axp = axp_mod()
+    grid = periodic_grid(g=0.7, m=1.1, n=(20, 18, 16), B_ext=(0.0, 1.0, 0.0)).replace(precision="fp32")
+    g = axp.Grid(grid)
+    g.write("E0y", W.random_state(grid, seed=1)["E0y"])  # an order-0 field makes the set non-empty
+    g.set_kernel(axp.AXP_KERNEL_AX3D)
+    assert g.kernel_path() == axp.AXP_KERNEL_GENERAL
+    with pytest.raises(axp.AxpError) as e:
+        g.step(1)
+    assert e.value.status == axp.AXP_E_STATE
+    g.close()
+    pml = periodic_grid(g=0.7, m=1.1, n=(20, 18, 16), B_ext=(0.0, 1.0, 0.0), axion_bc=W._bcs("periodic", "periodic", "pml"),
+                        em_bc=W._bcs("periodic", "periodic", "pml"), pml_cells=3).replace(precision="fp32")
+    h = axp.Grid(pml)
+    h.set_kernel(axp.AXP_KERNEL_AX3D)
+    assert h.kernel_path() == axp.AXP_KERNEL_GENERAL
+    h.close()
