@@ -389,6 +389,7 @@ axp_status axp_destroy_grid(axp_grid *grid)
 {
     if (!grid) return AXP_E_INVAL;
     if (grid->group) return AXP_E_STATE;
+    release_step_graphs(grid, true);
     delete grid;
     return AXP_OK;
 }
@@ -397,6 +398,7 @@ axp_status axp_set_background_field(axp_grid *g, const double B_ext[3], const do
 {
     if (!g) return AXP_E_INVAL;
     if (g->group) return AXP_E_STATE;
+    g->cfg_version++;
     for (int a = 0; a < 3; a++) {
         if (B_ext && !std::isfinite(B_ext[a])) return AXP_E_INVAL;
         if (E_ext && !std::isfinite(E_ext[a])) return AXP_E_INVAL;
@@ -415,6 +417,7 @@ axp_status axp_inject_laser(axp_grid *g, const axp_laser_desc *L)
 {
     if (!g || !L) return AXP_E_INVAL;
     if (g->group) return AXP_E_STATE;
+    g->cfg_version++;
     double kk = 0;
     for (int a = 0; a < 3; a++) {
         if (!std::isfinite(L->k[a]) || !std::isfinite(L->pol[a]) || !std::isfinite(L->centre[a])) return AXP_E_INVAL;
@@ -437,6 +440,7 @@ axp_status axp_inject_axion(axp_grid *g, const axp_axion_desc *A)
 {
     if (!g || !A) return AXP_E_INVAL;
     if (g->group) return AXP_E_STATE;
+    g->cfg_version++;
     for (int a = 0; a < 3; a++)
         if (!std::isfinite(A->k[a]) || !std::isfinite(A->centre[a])) return AXP_E_INVAL;
     if (!std::isfinite(A->amplitude) || A->waist < 0 || A->length < 0) return AXP_E_INVAL;
@@ -542,6 +546,7 @@ axp_status axp_write_field(axp_grid *g, int32_t which, const double *src, size_t
 {
     if (!g || !src || which < 0 || which > AXP_PHI_OLD) return AXP_E_INVAL;
     if (g->group) return AXP_E_STATE;
+    g->cfg_version++;
     const int64_t N = cells(g->desc);
     if (bytes != (size_t)N * 8) return AXP_E_INVAL;
     cudaError_t e = ensure_integer(g);
@@ -616,6 +621,7 @@ axp_status axp_write_ghost(axp_grid *g, int32_t axis, int32_t side, int32_t leve
 {
     if (!src) return AXP_E_INVAL;
     if (g && g->group) return AXP_E_STATE;
+    if (g) g->cfg_version++;
     return ghost_io(g, axis, side, level, nullptr, src, bytes);
 }
 
@@ -685,6 +691,7 @@ axp_status axp_load_state(axp_grid *g, const void *src, size_t bytes)
     size_t need;
     if (!g || !src || axp_state_bytes(g, &need) != AXP_OK || bytes != need) return AXP_E_INVAL;
     if (g->group) return AXP_E_STATE;
+    g->cfg_version++;
     StateHeader h;
     std::memcpy(&h, src, sizeof(h));
     if (h.magic != kStateMagic || h.bytes != need || std::memcmp(&h.desc, &g->desc, sizeof(axp_grid_desc)) != 0)
@@ -723,6 +730,7 @@ axp_status axp_set_kernel(axp_grid *g, int32_t kernel)
 {
     if (!g || kernel < AXP_KERNEL_AUTO || kernel > AXP_KERNEL_AX3D) return AXP_E_INVAL;
     if (g->group) return AXP_E_STATE;
+    g->cfg_version++;
     g->kernel_choice = kernel;
     return AXP_OK;
 }

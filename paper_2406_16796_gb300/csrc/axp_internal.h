@@ -83,6 +83,13 @@ struct axp_grid {
     uint32_t active;       // bit per field array that may be non-zero
     bool phi_active;
     void *group;           // the axp_group stepping this grid, or null
+    // CUDA graphs of consecutive fused 1D steps, one per buffer-role configuration;
+    // cfg_version changes whenever fields, background or kernel choice change
+    int64_t cfg_version;
+    cudaStream_t capture_stream;
+    int n_step_graphs;
+    int64_t step_graph_key[8];
+    cudaGraphExec_t step_graph[8];
 };
 
 namespace axp {
@@ -124,6 +131,8 @@ uint32_t order0_closure(const axp_grid *g);
 cudaError_t ensure_integer(axp_grid *g);
 // buffer roles after one more fused step (field sets and axion slots alternate)
 void rotate_roles(axp_grid *g);
+// destroy the cached step graphs (and the capture stream when `all`)
+void release_step_graphs(axp_grid *g, bool all);
 
 axp_diag *ring_slot(axp_grid *g, int64_t index);
 

@@ -218,6 +218,61 @@ int32_t fused_path(const axp_grid *g)
     return tm ? AXP_KERNEL_TM2D : (ax ? AXP_KERNEL_AX3D : (fu ? AXP_KERNEL_FUSED : AXP_KERNEL_GENERAL));
 }
 
+// Fused 1D steps are short (microseconds), so runs of them replay from CUDA
+// graphs of kGraphSteps launches.  kGraphSteps is a multiple of the periods of
+// the buffer-role rotation (2 for the field sets and the FP32 axion slots, 3 for
+// the FP64 axion slots), so a graph leaves the roles as it found them and one
+// graph serves every replay from the same role configuration.
+constexpr int kGraphSteps = 48;
+
+int64_t roles_key(const axp_grid *g)
+{
+    return ((((g->cfg_version * 2 + g->fset) * 4 + g->phi_cur_slot) * 4 + g->phi_b_slot) * 4 + g->phi_next_slot) * 4 +
+           g->phi_next_b_slot;
+}
+
+template <typename T, typename Launch>
+cudaError_t step_graph(axp_grid *g, Launch &&launch_one, cudaGraphExec_t *out)
+{
+    const int64_t key = roles_key(g);
+    for (int i = 0; i < g->n_step_graphs; i++)
+        if (g->step_graph_key[i] == key) {
+            *out = g->step_graph[i];
+            return cudaSuccess;
+        }
+    if (g->n_step_graphs == 8) release_step_graphs(g, false);
+    cudaError_t e = cudaSuccess;
+    if (!g->capture_stream) e = cudaStreamCreateWithFlags(&g->capture_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    const int fset = g->fset, s0 = g->phi_cur_slot, s1 = g->phi_b_slot, s2 = g->phi_next_slot, s3 = g->phi_next_b_slot;
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(g->capture_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    cudaError_t le = cudaSuccess;
+    for (int k = 0; k < kGraphSteps && le == cudaSuccess; k++) {
+        le = launch_one(make_params<T>(g), g->capture_stream);
+        rotate_roles(g);
+    }
+    e = cudaStreamEndCapture(g->capture_stream, &graph);
+    g->fset = fset;  // (kGraphSteps rotations are the identity; restored regardless)
+    g->phi_cur_slot = s0;
+    g->phi_b_slot = s1;
+    g->phi_next_slot = s2;
+    g->phi_next_b_slot = s3;
+    if (le != cudaSuccess || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return le != cudaSuccess ? le : e;
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return e;
+    g->step_graph_key[g->n_step_graphs] = key;
+    g->step_graph[g->n_step_graphs++] = exec;
+    *out = exec;
+    return cudaSuccess;
+}
+
 template <typename T>
 cudaError_t fused_step(axp_grid *g, int64_t nsteps, bool *handled)
 {
@@ -273,7 +328,20 @@ cudaError_t fused_step(axp_grid *g, int64_t nsteps, bool *handled)
         nchunks = (int)((nm + chunk - 1) / chunk);
         P.chunk = (int)chunk;
     }
-    for (int64_t it = 0; it < nsteps; it++) {
+    int64_t it = 0;
+    if (mode == 1 && !tm && !ax && g->desc.diag_every == 0 && nsteps >= kGraphSteps) {
+        auto one = [&](const fused::Params<T> &Pl, cudaStream_t st) {
+            return dispatch<T>(mode, set, Pl, nchunks, st, nullptr);
+        };
+        for (; it + kGraphSteps <= nsteps; it += kGraphSteps) {
+            cudaGraphExec_t exec = nullptr;
+            if ((e = step_graph<T>(g, one, &exec)) != cudaSuccess) return e;
+            if ((e = cudaGraphLaunch(exec, g->stream)) != cudaSuccess) return e;
+            g->launches += kGraphSteps;
+            g->step += kGraphSteps;
+        }
+    }
+    for (; it < nsteps; it++) {
         if (it > 0) {
             const int ch = P.chunk;
             P = make_params<T>(g);
@@ -292,6 +360,17 @@ cudaError_t fused_step(axp_grid *g, int64_t nsteps, bool *handled)
     }
     g->J_valid = false;
     return cudaGetLastError();
+}
+
+void release_step_graphs(axp_grid *g, bool all)
+{
+    if (g->n_step_graphs > 0) cudaStreamSynchronize(g->stream);  // no replay may still be running
+    for (int i = 0; i < g->n_step_graphs; i++) cudaGraphExecDestroy(g->step_graph[i]);
+    g->n_step_graphs = 0;
+    if (all && g->capture_stream) {
+        cudaStreamDestroy(g->capture_stream);
+        g->capture_stream = nullptr;
+    }
 }
 
 void rotate_roles(axp_grid *g)

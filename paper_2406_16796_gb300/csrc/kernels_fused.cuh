@@ -42,7 +42,9 @@ constexpr int HL = 2, HR = 3;
 
 template <typename T, int MODE>
 struct Tile {
-    static constexpr int TX = MODE == 3 ? 32 : (sizeof(T) == 8 ? 128 : 256);
+    // 1D grids are short (the state of a 4096-cell run is 256 KB): narrow tiles
+    // spread one step over more SMs
+    static constexpr int TX = MODE == 3 ? 32 : (MODE == 1 ? (sizeof(T) == 8 ? 32 : 64) : (sizeof(T) == 8 ? 128 : 256));
     static constexpr int TY = MODE == 3 ? 16 : 1;
     static constexpr int NT = TX * TY;
     static constexpr int VX = TX - HL - HR;  // valid outputs per tile along x

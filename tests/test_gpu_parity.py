@@ -395,3 +395,34 @@ def test_ax3d_refuses_grids_with_laser_fields_or_absorbing_sides():
     h.set_kernel(axp.AXP_KERNEL_AX3D)
     assert h.kernel_path() == axp.AXP_KERNEL_GENERAL
     h.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_1d_graph_replay_matches_single_launches(prec):
+    """Runs of 1D steps replay from CUDA graphs of 48 launches; the states equal
+    those of the same steps launched one by one, also across a field write
+    between runs (which must invalidate the captured parameters)."""
+    axp = axp_mod()
+    grid = periodic_grid(g=0.7, m=1.1, n=(500, 1, 1), B_ext=(0.0, 1.0, 0.3)).replace(precision=prec)
+    st = W.random_state(grid, seed=606, active=["E0y", "B0z"] + [n for n in W.FIELD_NAMES if n[1] == "1"])
+    a, b = axp.Grid(grid), axp.Grid(grid)
+    for x in (a, b):
+        x.load(st)
+    a.step(100)  # two graph replays and four single launches
+    for _ in range(100):
+        b.step(1)
+    fa, fb = a.fields(), b.fields()
+    for k in NAMES:
+        assert np.array_equal(fa[k], fb[k]), k
+    kick = W.random_state(grid, seed=607)["B1y"]
+    for x in (a, b):
+        x.write("B1y", kick)
+    a.step(97)
+    for _ in range(97):
+        b.step(1)
+    fa, fb = a.fields(), b.fields()
+    for k in NAMES:
+        assert np.array_equal(fa[k], fb[k]), k
+    assert a.step_count == b.step_count == 197
+    a.close()
+    b.close()
