@@ -242,6 +242,28 @@ axp_status axp_load_state(axp_grid *grid, const void *host_src, size_t bytes);
 axp_status axp_get_step(const axp_grid *grid, int64_t *step);
 axp_status axp_synchronize(axp_grid *grid);
 
+/* Moving window (Sec. 3.2: the simulation window moves at the speed of light
+ * after the laser has entered it).  A shift by `cells` along `axis` moves the
+ * integer-time state -- every field array of both orders and both axion
+ * levels -- towards lower index along that axis; the `cells` entering at the
+ * high end are vacuum (zero), the ones leaving at the low end are dropped, and
+ * the grid origin moves by cells x d[axis] (later injections and the laser
+ * centroid use the moved origin).  The axis must not be periodic and the grid
+ * must have no outflow axion side (outflow ghost planes do not move); one
+ * window axis per grid.
+ *
+ * axp_shift_window shifts once, now.  axp_set_moving_window makes axp_step
+ * move the window at `velocity` (units of c, in (0, 1]) from step
+ * `start_step` on: the window's travel accumulates velocity x dt / d[axis]
+ * cells per step and each time it reaches `shift_cells` the state is shifted
+ * by shift_cells between two steps.  velocity = 0 stops the window.  The
+ * window state is part of checkpoints. */
+axp_status axp_shift_window(axp_grid *grid, int32_t axis, int64_t cells);
+axp_status axp_set_moving_window(axp_grid *grid, int32_t axis, double velocity, int32_t shift_cells,
+                                 int64_t start_step);
+/* Cells shifted so far. */
+axp_status axp_get_window_offset(const axp_grid *grid, int64_t *cells);
+
 /* Kernel selection for axp_step.  AXP_KERNEL_AUTO (default) uses the fastest
  * single-pass kernel that supports the grid's shape, boundaries and active
  * field components, else the general multi-pass kernels.

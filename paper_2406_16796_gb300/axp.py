@@ -93,6 +93,9 @@ def lib():
             "axp_get_step": ([_P, C.POINTER(C.c_int64)], C.c_int),
             "axp_synchronize": ([_P], C.c_int),
             "axp_set_kernel": ([_P, C.c_int32], C.c_int),
+            "axp_shift_window": ([_P, C.c_int32, C.c_int64], C.c_int),
+            "axp_set_moving_window": ([_P, C.c_int32, C.c_double, C.c_int32, C.c_int64], C.c_int),
+            "axp_get_window_offset": ([_P, C.POINTER(C.c_int64)], C.c_int),
             "axp_get_kernel_path": ([_P, C.POINTER(C.c_int32)], C.c_int),
             "axp_get_launch_count": ([_P, C.POINTER(C.c_int64)], C.c_int),
         }
@@ -234,6 +237,21 @@ def axp_set_kernel(h, k):
     _check(lib().axp_set_kernel(h, int(k)), "axp_set_kernel")
 
 
+def axp_shift_window(h, axis, cells):
+    _check(lib().axp_shift_window(h, int(axis), int(cells)), "axp_shift_window")
+
+
+def axp_set_moving_window(h, axis, velocity, shift_cells=1, start_step=0):
+    _check(lib().axp_set_moving_window(h, int(axis), float(velocity), int(shift_cells), int(start_step)),
+           "axp_set_moving_window")
+
+
+def axp_get_window_offset(h):
+    n = C.c_int64()
+    _check(lib().axp_get_window_offset(h, C.byref(n)), "axp_get_window_offset")
+    return n.value
+
+
 def axp_get_kernel_path(h):
     p = C.c_int32()
     _check(lib().axp_get_kernel_path(h, C.byref(p)), "axp_get_kernel_path")
@@ -345,6 +363,15 @@ class Grid:
 
     def write_ghost(self, axis, side, level, values):
         axp_write_ghost(self.h, axis, side, level, values)
+
+    def shift_window(self, axis, cells):
+        axp_shift_window(self.h, axis, cells)
+
+    def set_moving_window(self, axis, velocity=1.0, shift_cells=1, start_step=0):
+        axp_set_moving_window(self.h, axis, velocity, shift_cells, start_step)
+
+    def window_offset(self):
+        return axp_get_window_offset(self.h)
 
     def set_kernel(self, k):
         axp_set_kernel(self.h, k)

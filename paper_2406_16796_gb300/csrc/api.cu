@@ -3,6 +3,7 @@
 // Validation, workspace layout in caller-owned device memory, handle state,
 // host<->device transfers and checkpointing.  No device memory is allocated
 // here: every array lives in the caller's workspace.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -155,7 +156,11 @@ struct StateHeader {
     int32_t J_valid;
     uint32_t active;
     int32_t phi_active;
+    int32_t win_axis;    // moving window (-1: none) and its state
+    int32_t win_cells;
     int32_t pad;
+    double win_velocity, win_travel;
+    int64_t win_start, win_offset;
 };
 
 }  // namespace
@@ -252,7 +257,7 @@ View<T> make_view_eset(axp_grid *g, int eset)
         v.sig_ax[a] = (const T *)(g->ws + w.off_sig_ax[a]);
         v.n[a] = d.n[a];
         v.d[a] = (T)d.d[a];
-        v.lo[a] = (T)d.lo[a];
+        v.lo[a] = (T)lo_of(g, a);
         v.Bext[a] = (T)g->B_ext[a];
         v.Eext[a] = (T)g->E_ext[a];
         v.periodic[a] = d.em_bc[a][0] == AXP_BC_PERIODIC;
@@ -371,6 +376,7 @@ axp_status axp_create_grid(const axp_grid_desc *desc, void *dev_workspace, size_
     for (int l = 0; l < 3; l++) g->ghost_level_slot[l] = l;
     g->J_valid = false;
     g->kernel_choice = AXP_KERNEL_AUTO;
+    g->win_axis = -1;
     cudaError_t e = cudaMemsetAsync(g->ws, 0, w.total, g->stream);
     if (e == cudaSuccess) {
         // absorbing-layer profiles and coefficients, computed once on the host
@@ -451,11 +457,8 @@ axp_status axp_inject_axion(axp_grid *g, const axp_axion_desc *A)
     return cuda_status(e);
 }
 
-axp_status axp_step(axp_grid *g, int64_t nsteps)
+static axp_status run_steps(axp_grid *g, int64_t nsteps)
 {
-    if (!g || nsteps < 0) return AXP_E_INVAL;
-    if (g->group) return AXP_E_STATE;
-    if (nsteps == 0) return AXP_OK;
     cudaError_t e;
     bool handled = false;
     if (g->kernel_choice != AXP_KERNEL_GENERAL) {
@@ -470,6 +473,97 @@ axp_status axp_step(axp_grid *g, int64_t nsteps)
         e = cudaSuccess;
     }
     return cuda_status(e);
+}
+
+// Shift the window by `cells` along `axis`: the integer-time state moves towards
+// lower index and vacuum enters at the high end.
+static axp_status shift_now(axp_grid *g, int axis, int64_t cells)
+{
+    cudaError_t e = ensure_integer(g);
+    if (e == cudaSuccess) e = is_fp32(g) ? shift_window<float>(g, axis, cells) : shift_window<double>(g, axis, cells);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (g->win_axis < 0) g->win_axis = axis;
+    g->win_offset += cells;
+    g->cfg_version++;
+    return AXP_OK;
+}
+
+static bool window_axis_ok(const axp_grid *g, int32_t axis)
+{
+    if (axis < 0 || axis > 2 || g->desc.n[axis] < 2) return false;
+    if (g->desc.em_bc[axis][0] == AXP_BC_PERIODIC) return false;
+    if (g->win_axis >= 0 && g->win_axis != axis) return false;  // one window axis per grid
+    for (int a = 0; a < 3; a++)
+        for (int s = 0; s < 2; s++)
+            if (g->desc.axion_bc[a][s] == AXP_BC_OUTFLOW) return false;  // ghost planes do not move
+    return true;
+}
+
+axp_status axp_step(axp_grid *g, int64_t nsteps)
+{
+    if (!g || nsteps < 0) return AXP_E_INVAL;
+    if (g->group) return AXP_E_STATE;
+    if (nsteps == 0) return AXP_OK;
+    if (g->win_velocity <= 0.0) return run_steps(g, nsteps);
+    // moving window: run up to each shift, then shift by win_cells
+    const int a = g->win_axis;
+    const double u = g->win_velocity * g->desc.dt / g->desc.d[a];  // cells per step
+    int64_t left = nsteps;
+    while (left > 0) {
+        int64_t k = left;
+        if (g->step < g->win_start) {
+            k = std::min<int64_t>(left, g->win_start - g->step);
+        } else {
+            const double need = (double)g->win_cells - g->win_travel;
+            k = std::min<int64_t>(left, std::max<int64_t>(1, (int64_t)std::ceil(need / u - 1e-9)));
+        }
+        const int64_t s0 = g->step;
+        axp_status st = run_steps(g, k);
+        if (st != AXP_OK) return st;
+        left -= k;
+        const int64_t moving = g->step - std::max(s0, g->win_start);
+        if (moving > 0) g->win_travel += (double)moving * u;
+        if (g->win_travel >= (double)g->win_cells - 1e-9) {
+            if ((st = shift_now(g, a, g->win_cells)) != AXP_OK) return st;
+            g->win_travel -= (double)g->win_cells;
+        }
+    }
+    return AXP_OK;
+}
+
+axp_status axp_shift_window(axp_grid *g, int32_t axis, int64_t cells)
+{
+    if (!g || cells < 0) return AXP_E_INVAL;
+    if (g->group) return AXP_E_STATE;
+    if (!window_axis_ok(g, axis) || cells >= g->desc.n[axis]) return AXP_E_INVAL;
+    if (cells == 0) return AXP_OK;
+    return shift_now(g, axis, cells);
+}
+
+axp_status axp_set_moving_window(axp_grid *g, int32_t axis, double velocity, int32_t shift_cells, int64_t start_step)
+{
+    if (!g) return AXP_E_INVAL;
+    if (g->group) return AXP_E_STATE;
+    if (velocity == 0.0) {
+        g->win_velocity = 0.0;
+        return AXP_OK;
+    }
+    if (!window_axis_ok(g, axis) || !(velocity > 0.0) || velocity > 1.0 || shift_cells < 1 ||
+        shift_cells >= g->desc.n[axis] || start_step < 0)
+        return AXP_E_INVAL;
+    g->win_axis = axis;
+    g->win_velocity = velocity;
+    g->win_cells = shift_cells;
+    g->win_start = start_step;
+    g->win_travel = 0.0;
+    return AXP_OK;
+}
+
+axp_status axp_get_window_offset(const axp_grid *g, int64_t *cells)
+{
+    if (!g || !cells) return AXP_E_INVAL;
+    *cells = g->win_offset;
+    return AXP_OK;
 }
 
 axp_status axp_synchronize(axp_grid *g)
@@ -674,6 +768,12 @@ axp_status axp_save_state(axp_grid *g, void *dst, size_t bytes)
     h.J_valid = g->J_valid;
     h.active = g->active;
     h.phi_active = g->phi_active;
+    h.win_axis = g->win_axis;
+    h.win_cells = g->win_cells;
+    h.win_velocity = g->win_velocity;
+    h.win_travel = g->win_travel;
+    h.win_start = g->win_start;
+    h.win_offset = g->win_offset;
     std::memcpy(dst, &h, sizeof(h));
     std::vector<std::pair<char *, size_t>> r;
     state_regions(g, &r);
@@ -715,6 +815,12 @@ axp_status axp_load_state(axp_grid *g, const void *src, size_t bytes)
     g->J_valid = h.J_valid != 0;
     g->active = h.active;
     g->phi_active = h.phi_active != 0;
+    g->win_axis = h.win_axis;
+    g->win_cells = h.win_cells;
+    g->win_velocity = h.win_velocity;
+    g->win_travel = h.win_travel;
+    g->win_start = h.win_start;
+    g->win_offset = h.win_offset;
     g->ring_read = g->ring_written;
     return AXP_OK;
 }

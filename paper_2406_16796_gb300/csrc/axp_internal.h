@@ -86,6 +86,14 @@ struct axp_grid {
     // CUDA graphs of consecutive fused 1D steps, one per buffer-role configuration;
     // cfg_version changes whenever fields, background or kernel choice change
     int64_t cfg_version;
+    // moving window: axis (-1: none), speed in units of c, cells per shift, first
+    // step at which it moves, distance travelled since the last shift (cells)
+    int32_t win_axis;
+    double win_velocity;
+    int32_t win_cells;
+    int64_t win_start;
+    double win_travel;
+    int64_t win_offset;  // cells shifted so far
     cudaStream_t capture_stream;
     int n_step_graphs;
     int64_t step_graph_key[8];
@@ -131,6 +139,14 @@ uint32_t order0_closure(const axp_grid *g);
 cudaError_t ensure_integer(axp_grid *g);
 // buffer roles after one more fused step (field sets and axion slots alternate)
 void rotate_roles(axp_grid *g);
+// grid origin along axis a, moved by the window's shifts
+inline double lo_of(const axp_grid *g, int a)
+{
+    return g->desc.lo[a] + (a == g->win_axis ? (double)g->win_offset * g->desc.d[a] : 0.0);
+}
+// shift the integer-time state by s cells along axis (moving window)
+template <typename T>
+cudaError_t shift_window(axp_grid *g, int axis, int64_t s);
 // destroy the cached step graphs (and the capture stream when `all`)
 void release_step_graphs(axp_grid *g, bool all);
 

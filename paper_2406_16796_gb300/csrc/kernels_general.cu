@@ -11,6 +11,7 @@
 //   [J^n if not cached] -> E half (both orders, J^n) -> B half (both orders)
 //   -> S^{n+1/2} and phi^{n+3/2} (PML form in the layer) -> outflow ghosts
 //   -> B half (both orders) -> E0 half -> J^{n+1} -> E1 half (J^{n+1}).
+#include <utility>
 #include "device_common.cuh"
 
 namespace axp {
@@ -241,6 +242,18 @@ __global__ void __launch_bounds__(kThreads) k_e_unhalf(View<T> v, int order, EOu
     }
 }
 
+// Moving window: dst = src shifted by s cells towards lower index along `axis`;
+// the s cells entering at the high end are vacuum.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_shift(const T *__restrict__ src, T *__restrict__ dst, int64_t N,
+                                                     int64_t stride, int64_t na, int64_t s)
+{
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < N; c += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t ca = (c / stride) % na;
+        dst[c] = ca + s < na ? src[c + s * stride] : T(0);
+    }
+}
+
 }  // namespace
 
 template <typename T>
@@ -388,6 +401,45 @@ cudaError_t exit_staggered(axp_grid *g, bool in_place)
     return cudaGetLastError();
 }
 
+// Shift the integer-time state (every field array and both axion levels) by s
+// cells along `axis`, out of place into the spare field set and axion buffers.
+template <typename T>
+cudaError_t shift_window(axp_grid *g, int axis, int64_t s)
+{
+    const int64_t *n = g->desc.n;
+    const int64_t N = n[0] * n[1] * n[2];
+    const int64_t stride = axis == 0 ? 1 : (axis == 1 ? n[0] : n[0] * n[1]);
+    const int nb = grid_for(N);
+    const Workspace &w = g->layout;
+    const int in = g->fset, out = 1 - g->fset;
+    auto at = [&](size_t off) { return (T *)(g->ws + off); };
+    for (int f = 0; f < kFields; f++) {
+        k_shift<T><<<nb, kThreads, 0, g->stream>>>(at(w.off_fields[in][f]), at(w.off_fields[out][f]), N, stride,
+                                                  n[axis], s);
+        g->launches++;
+    }
+    g->fset = out;
+    const int cur = g->phi_cur_slot, b = g->phi_b_slot, nxt = g->phi_next_slot;
+    k_shift<T><<<nb, kThreads, 0, g->stream>>>(at(w.off_phi[cur]), at(w.off_phi[nxt]), N, stride, n[axis], s);
+    if (g->desc.precision == AXP_FP32_SPLIT) {
+        const int nb2 = g->phi_next_b_slot;
+        k_shift<T><<<nb, kThreads, 0, g->stream>>>(at(w.off_phi[b]), at(w.off_phi[nb2]), N, stride, n[axis], s);
+        std::swap(g->phi_cur_slot, g->phi_next_slot);
+        std::swap(g->phi_b_slot, g->phi_next_b_slot);
+    } else {
+        // three buffers: the second level goes into the buffer phi^{n+1/2} just left
+        k_shift<T><<<nb, kThreads, 0, g->stream>>>(at(w.off_phi[b]), at(w.off_phi[cur]), N, stride, n[axis], s);
+        g->phi_cur_slot = nxt;
+        g->phi_b_slot = cur;
+        g->phi_next_slot = b;
+    }
+    g->launches += 2;
+    g->J_valid = false;
+    return cudaGetLastError();
+}
+
+template cudaError_t shift_window<double>(axp_grid *, int, int64_t);
+template cudaError_t shift_window<float>(axp_grid *, int, int64_t);
 template cudaError_t enter_staggered<double>(axp_grid *);
 template cudaError_t enter_staggered<float>(axp_grid *);
 template cudaError_t exit_staggered<double>(axp_grid *, bool);

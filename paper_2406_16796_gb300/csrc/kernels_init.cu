@@ -162,7 +162,7 @@ cudaError_t inject_laser(axp_grid *g, const axp_laser_desc &L)
     W.phase = L.phase;
     W.fscale = L.amplitude / (ch * Kmag);
     View<T> v = make_view<T>(g);
-    k_laser<T><<<blocks_for(v.N), 256, 0, g->stream>>>(v, W, D.lo[0], D.lo[1], D.lo[2], D.d[0], D.d[1], D.d[2]);
+    k_laser<T><<<blocks_for(v.N), 256, 0, g->stream>>>(v, W, lo_of(g, 0), lo_of(g, 1), lo_of(g, 2), D.d[0], D.d[1], D.d[2]);
     g->launches++;
     return cudaGetLastError();
 }
@@ -191,10 +191,10 @@ cudaError_t inject_axion(axp_grid *g, const axp_axion_desc &A)
     W.phase = A.phase;
     View<T> v = make_view<T>(g);
     if (D.precision == AXP_FP32_SPLIT)
-        k_axion_seed<T, true><<<blocks_for(v.N), 256, 0, g->stream>>>(v, W, D.dt, D.lo[0], D.lo[1], D.lo[2], D.d[0],
+        k_axion_seed<T, true><<<blocks_for(v.N), 256, 0, g->stream>>>(v, W, D.dt, lo_of(g, 0), lo_of(g, 1), lo_of(g, 2), D.d[0],
                                                                        D.d[1], D.d[2]);
     else
-        k_axion_seed<T, false><<<blocks_for(v.N), 256, 0, g->stream>>>(v, W, D.dt, D.lo[0], D.lo[1], D.lo[2], D.d[0],
+        k_axion_seed<T, false><<<blocks_for(v.N), 256, 0, g->stream>>>(v, W, D.dt, lo_of(g, 0), lo_of(g, 1), lo_of(g, 2), D.d[0],
                                                                         D.d[1], D.d[2]);
     g->launches++;
     for (int a = 0; a < 3; a++)
@@ -204,7 +204,7 @@ cudaError_t inject_axion(axp_grid *g, const axp_axion_desc &A)
             T *go = (T *)(g->ws + g->layout.off_ghost[a][s][g->ghost_level_slot[1]]);
             const int b = (a + 1) % 3, c = (a + 2) % 3;
             k_axion_seed_ghost<T><<<blocks_for(D.n[b] * D.n[c]), 256, 0, g->stream>>>(
-                v, W, D.dt, a, s, gc, go, D.lo[0], D.lo[1], D.lo[2], D.d[0], D.d[1], D.d[2]);
+                v, W, D.dt, a, s, gc, go, lo_of(g, 0), lo_of(g, 1), lo_of(g, 2), D.d[0], D.d[1], D.d[2]);
             g->launches++;
         }
     return cudaGetLastError();
