@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-3d", action="store_true")
     ap.add_argument("--no-1d", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-bc", action="store_true")
+    ap.add_argument("--no-window", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=120)
     ap.add_argument("--n3d", type=int, default=512, help="edge of the 3D axion box")
     return ap.parse_args()
@@ -380,6 +382,49 @@ def serve_measurement(count, rank, world):
             "speedup_vs_fp64_sequential": cap["sims_per_s"] / (count / seq)}
 
 
+def boundary_measurement():
+    """The Sec. 3.1 boundary benchmark on the paper's grid (400 x 400 cells over
+    [-20, 20]^2 lambda0, pulse w = 5 lambda0, m = 1 meV, t = 30 lambda0 / c),
+    FP64, for the PML and the outflow axion boundary; the paper reports about
+    1% reflectivity for both."""
+    from paper_2406_16796_gb300 import bccheck
+
+    out = {"workload": "bc_check_400x400", "paper_reflectivity": 0.01}
+    for bc in ("pml", "outflow"):
+        r = bccheck.reflectivity(bc, n=400)
+        out[bc] = {k: r[k] for k in ("energy", "amplitude", "steps", "seconds", "cell_updates_per_s", "kernel")}
+    return out
+
+
+def window_measurement(steps=400, shift_cells=16):
+    """Cost of the moving window on the 2D pulse grid in FP32 split: ms/step with
+    the window moving at c in shifts of `shift_cells`, against the fixed box."""
+    import torch
+
+    from paper_2406_16796_gb300 import axp, workloads as W
+
+    w = W.pulse_2d(precision="fp32")
+    res = {}
+    for moving in (False, True):
+        g = axp.Grid(w.grid)
+        g.inject_laser(w.lasers[0])
+        if moving:
+            g.set_moving_window(0, 1.0, shift_cells, 0)
+        g.step(20)
+        g.synchronize()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.step(steps)
+        g.synchronize()
+        res["moving" if moving else "fixed"] = (time.perf_counter() - t0) / steps * 1e3
+        if moving:
+            res["shifts"] = g.window_offset() // shift_cells
+        g.close()
+    return {"workload": w.name, "precision": "fp32_split", "shift_cells": shift_cells, "steps": steps,
+            "ms_per_step_fixed": res["fixed"], "ms_per_step_moving": res["moving"], "shifts": res["shifts"],
+            "overhead": res["moving"] / res["fixed"] - 1.0}
+
+
 def scan_measurement(rank, world, fp64_sample=6):
     """The batched parameter scan: 512 seeded 1D instances (Nx log-uniform in
     [1024, 65536], m/omega0 in [1e-3, 2], g in [1e-6, 1e-3], B0 in [0.1, 10],
@@ -544,6 +589,12 @@ def gpu_arm(args):
     srv = None
     if not args.no_serve:
         srv = serve_measurement(args.serve_requests, rank, world)
+    bcm = None
+    if not args.no_bc and rank == 0:
+        bcm = boundary_measurement()
+    win = None
+    if not args.no_window and rank == 0:
+        win = window_measurement()
     ax3 = None
     if not args.no_3d:
         ax3 = axion3d_measurement(max(20, args.steps // 3), args.warmup, hbm_peak, hbm_src, world, n=args.n3d)
@@ -571,6 +622,10 @@ def gpu_arm(args):
         line["serve"] = srv
     if ax3:
         line["axion_3d"] = ax3
+    if bcm:
+        line["boundary"] = bcm
+    if win:
+        line["moving_window"] = win
     if v1:
         line["vacuum_1d"] = v1
     if rank == 0:
