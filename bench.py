@@ -542,26 +542,34 @@ def gpu_arm(args):
                     "kernel": kern,
                     "peak_source": hbm_src, "algorithmic_bytes_per_cell": bpc}
 
-    # e2e through the C ABI with pinned host buffers: upload the state, run the
-    # steps reading the diagnostics record back after each, download the state
+    # e2e through the C ABI with pinned host buffers, the way a user runs the
+    # workload: upload the state, run the steps with the diagnostics recorded
+    # every 100 steps (the workload's cadence) into the grid's ring, read the
+    # records back, download the final state
     e2e = None
     if not args.no_e2e:
-        nbytes = axp.axp_state_bytes(g.h)
+        ge = axp.Grid(w.grid, diag_every=100, diag_capacity=64)
+        for L in w.lasers:
+            ge.inject_laser(L)
+        nbytes = axp.axp_state_bytes(ge.h)
         host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
-        axp.axp_save_state(g.h, host.data_ptr(), nbytes)
-        k = max(1, min(args.steps, 50))
+        axp.axp_save_state(ge.h, host.data_ptr(), nbytes)
+        ge.step(args.warmup)
+        ge.synchronize()
+        k = max(100, args.steps)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        axp.axp_load_state(g.h, host.data_ptr(), nbytes)
-        for _ in range(k):
-            g.step(1)
-            g.diagnostics()
-        axp.axp_save_state(g.h, host.data_ptr(), nbytes)
+        axp.axp_load_state(ge.h, host.data_ptr(), nbytes)
+        ge.step(k)
+        recs = ge.read_diagnostics()
+        axp.axp_save_state(ge.h, host.data_ptr(), nbytes)
         t1 = time.perf_counter()
-        diag_bytes = 88
+        diag_bytes = 88 * len(recs)
         e2e = {"value": cells * k * world / (t1 - t0), "unit": "cell-updates/s", "h2d_bytes_per_step": nbytes / k,
-               "d2h_bytes_per_step": nbytes / k + diag_bytes, "steps": k,
-               "what": "state upload from pinned host, k steps each followed by a diagnostics read-back, state download"}
+               "d2h_bytes_per_step": (nbytes + diag_bytes) / k, "steps": k, "diagnostics_records": len(recs),
+               "what": "state upload from pinned host, k steps with FP64 diagnostics every 100 steps, "
+                       "diagnostics read-back, state download"}
+        ge.close()
     g.close()
 
     # the FP32 split storage on the same workload, as a second measurement

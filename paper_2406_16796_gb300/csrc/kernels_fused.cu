@@ -13,8 +13,8 @@ cudaError_t fused_dispatch_f64(int mode, int set, const fused::Params<double> &P
                                int *occ);
 cudaError_t fused_dispatch_f32(int mode, int set, const fused::Params<float> &P, int nchunks, cudaStream_t s,
                                int *occ);
-cudaError_t tm2d_dispatch_f64(const fused::Params<double> &P, int nchunks, cudaStream_t s, int *occ);
-cudaError_t tm2d_dispatch_f32(const fused::Params<float> &P, int nchunks, cudaStream_t s, int *occ);
+cudaError_t tm2d_dispatch_f64(const fused::Params<double> &P, int nchunks, cudaStream_t s, int *occ, int tx);
+cudaError_t tm2d_dispatch_f32(const fused::Params<float> &P, int nchunks, cudaStream_t s, int *occ, int tx);
 cudaError_t ax3d_dispatch_f64(const fused::Params<double> &P, int nchunks, cudaStream_t s, int *occ);
 cudaError_t ax3d_dispatch_f32(const fused::Params<float> &P, int nchunks, cudaStream_t s, int *occ);
 
@@ -54,16 +54,16 @@ cudaError_t dispatch<float>(int mode, int set, const fused::Params<float> &P, in
 }
 
 template <typename T>
-cudaError_t dispatch_tm2d(const fused::Params<T> &P, int nchunks, cudaStream_t s, int *occ);
+cudaError_t dispatch_tm2d(const fused::Params<T> &P, int nchunks, cudaStream_t s, int *occ, int tx);
 template <>
-cudaError_t dispatch_tm2d<double>(const fused::Params<double> &P, int nchunks, cudaStream_t s, int *occ)
+cudaError_t dispatch_tm2d<double>(const fused::Params<double> &P, int nchunks, cudaStream_t s, int *occ, int tx)
 {
-    return tm2d_dispatch_f64(P, nchunks, s, occ);
+    return tm2d_dispatch_f64(P, nchunks, s, occ, tx);
 }
 template <>
-cudaError_t dispatch_tm2d<float>(const fused::Params<float> &P, int nchunks, cudaStream_t s, int *occ)
+cudaError_t dispatch_tm2d<float>(const fused::Params<float> &P, int nchunks, cudaStream_t s, int *occ, int tx)
 {
-    return tm2d_dispatch_f32(P, nchunks, s, occ);
+    return tm2d_dispatch_f32(P, nchunks, s, occ, tx);
 }
 
 template <typename T>
@@ -285,8 +285,9 @@ cudaError_t fused_step(axp_grid *g, int64_t nsteps, bool *handled)
     const int set = pick_set(g);
     cudaError_t e = enter_staggered<T>(g);
     if (e != cudaSuccess) return e;
+    int tm_tx = tm2d::TX;  // tile width of the 2D kernel (chosen below)
     auto launch = [&](const fused::Params<T> &Pl, int nch, int *occp) {
-        if (tm) return dispatch_tm2d<T>(Pl, nch, g->stream, occp);
+        if (tm) return dispatch_tm2d<T>(Pl, nch, g->stream, occp, tm_tx);
         if (ax) return dispatch_ax3d<T>(Pl, nch, g->stream, occp);
         return dispatch<T>(mode, set, Pl, nch, g->stream, occp);
     };
@@ -312,10 +313,40 @@ cudaError_t fused_step(axp_grid *g, int64_t nsteps, bool *handled)
                 nchunks = (int)((nz + chunk - 1) / chunk);
             }
         }
+    } else if (tm) {
+        // tile width and march chunks together: the fewest waves of resident blocks
+        // for the work a wave does (planes + pipeline) x columns x blocks per SM
+        int sms = 152;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
+        const int64_t nx = g->desc.n[0], ny = g->desc.n[1];
+        double best = -1.0;
+        for (int tx = tm2d::TX; tx >= 128; tx -= 32) {
+            int o = 0;
+            if ((e = dispatch_tm2d<T>(P, 0, g->stream, &o, tx)) != cudaSuccess) return e;
+            o = o > 0 ? o : 1;
+            const int64_t strips = (nx + (tx - tm2d::HL - tm2d::HR) - 1) / (tx - tm2d::HL - tm2d::HR);
+            const int64_t slots = (int64_t)sms * o;
+            for (int64_t nc = 1; nc <= 64 && ny / nc >= 16; nc++) {
+                const int64_t chunk = (ny + nc - 1) / nc, ctas = strips * ((ny + chunk - 1) / chunk);
+                const int64_t waves = (ctas + slots - 1) / slots;
+                const double cost = (double)waves * (double)(chunk + 6) * tx * o;
+                if (best < 0 || cost < best) {
+                    best = cost;
+                    tm_tx = tx;
+                    P.chunk = (int)chunk;
+                    nchunks = (int)((ny + chunk - 1) / chunk);
+                }
+            }
+        }
+        if (best < 0) {  // grids shorter than 16 planes: one chunk
+            tm_tx = tm2d::TX;
+            P.chunk = (int)ny;
+            nchunks = 1;
+        }
     } else if (mode >= 2) {
         int sms = 152;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
-        const int VX = tm ? tm2d::VX : (mode == 3 ? fused::Tile<T, 3>::VX : fused::Tile<T, 2>::VX);
+        const int VX = mode == 3 ? fused::Tile<T, 3>::VX : fused::Tile<T, 2>::VX;
         const int VY = mode == 3 ? fused::Tile<T, 3>::VY : 1;
         const int64_t strips = ((g->desc.n[0] + VX - 1) / VX) * (mode == 3 ? (g->desc.n[1] + VY - 1) / VY : 1);
         const int64_t nm = g->desc.n[mode == 3 ? 2 : 1];

@@ -10,9 +10,9 @@ cudaError_t fused_dispatch_f32(int mode, int set, const fused::Params<float> &P,
     return fused::dispatch<float, true>(mode, set, P, nchunks, s, occ);
 }
 
-cudaError_t tm2d_dispatch_f32(const fused::Params<float> &P, int nchunks, cudaStream_t s, int *occ)
+cudaError_t tm2d_dispatch_f32(const fused::Params<float> &P, int nchunks, cudaStream_t s, int *occ, int tx)
 {
-    return tm2d::launch<float, true>(P, nchunks, s, occ);
+    return tm2d::launch<float, true>(P, nchunks, s, occ, tx);
 }
 
 cudaError_t ax3d_dispatch_f32(const fused::Params<float> &P, int nchunks, cudaStream_t s, int *occ)

@@ -10,9 +10,9 @@ cudaError_t fused_dispatch_f64(int mode, int set, const fused::Params<double> &P
     return fused::dispatch<double, false>(mode, set, P, nchunks, s, occ);
 }
 
-cudaError_t tm2d_dispatch_f64(const fused::Params<double> &P, int nchunks, cudaStream_t s, int *occ)
+cudaError_t tm2d_dispatch_f64(const fused::Params<double> &P, int nchunks, cudaStream_t s, int *occ, int tx)
 {
-    return tm2d::launch<double, false>(P, nchunks, s, occ);
+    return tm2d::launch<double, false>(P, nchunks, s, occ, tx);
 }
 
 cudaError_t ax3d_dispatch_f64(const fused::Params<double> &P, int nchunks, cudaStream_t s, int *occ)

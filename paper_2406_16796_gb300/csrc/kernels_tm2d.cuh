@@ -26,7 +26,7 @@
 namespace axp {
 namespace tm2d {
 
-constexpr int TX = 256;
+constexpr int TX = 256;     // largest block (tile) width; a launch may use a narrower multiple of 32
 constexpr int HL = 2, HR = 3;
 constexpr int VX = TX - HL - HR;
 constexpr int RS = TX + 2;  // row stride: one guard element on each side
@@ -74,18 +74,19 @@ template <typename T, bool INCR>
 __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, const int by, T (&rows)[2][NROWS][RS],
                                      T *stage)
 {
-    for (int i = threadIdx.x; i < 2 * NROWS * RS; i += TX) (&rows[0][0][0])[i] = T(0);
+    const int ntx = (int)blockDim.x, vx = ntx - HL - HR;  // this launch's tile width
+    for (int i = threadIdx.x; i < 2 * NROWS * RS; i += ntx) (&rows[0][0][0])[i] = T(0);
 
     const int tx = threadIdx.x;
     const int nx = P.n[0], ny = P.n[1];
     const bool perx = P.per[0], pery = P.per[1];
-    const int gx = bx * VX - HL + tx;
+    const int gx = bx * vx - HL + tx;
     int wx = gx;
     if (wx < 0 || wx >= nx) wx = perx ? ((wx % nx) + nx) % nx : -1;
-    const bool write_col = tx >= HL && tx < TX - HR && gx >= 0 && gx < nx;
+    const bool write_col = tx >= HL && tx < ntx - HR && gx >= 0 && gx < nx;
     const int m0 = by * P.chunk;
     const int m1 = min(ny, m0 + P.chunk);
-    const int gx0 = bx * VX - HL;
+    const int gx0 = bx * vx - HL;
     // The plain body is exact for a column inside the grid with no x layer (the
     // edge body adds nothing there), so the choice is made per warp: in a tile
     // at an x edge only the warps over the layer take the edge body.
@@ -385,20 +386,23 @@ __global__ void __launch_bounds__(TX, sizeof(T) == 4 ? 2 : 1) k_tm2d(fused::Para
 }
 
 template <typename T, bool INCR>
-cudaError_t launch(const fused::Params<T> &P, int nchunks, cudaStream_t stream, int *occupancy)
+cudaError_t launch(const fused::Params<T> &P, int nchunks, cudaStream_t stream, int *occupancy, int tx = TX)
 {
-    static int occ = 0;
+    // resident blocks per SM for each tile width (multiples of 32 up to TX)
+    static int occ[TX / 32 + 1] = {};
     auto kern = k_tm2d<T, INCR>;
     const size_t dyn = stage_bytes<T>();
-    if (occ == 0) {
+    if (tx < 64 || tx > TX || tx % 32) return cudaErrorInvalidValue;
+    if (occ[tx / 32] == 0) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TX, dyn);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[tx / 32], kern, tx, dyn);
         if (e != cudaSuccess) return e;
     }
-    if (occupancy) *occupancy = occ;
+    if (occupancy) *occupancy = occ[tx / 32];
     if (nchunks <= 0) return cudaSuccess;
-    dim3 grid((P.n[0] + VX - 1) / VX, nchunks, 1);
-    kern<<<grid, TX, dyn, stream>>>(P);
+    const int vx = tx - HL - HR;
+    dim3 grid((P.n[0] + vx - 1) / vx, nchunks, 1);
+    kern<<<grid, tx, dyn, stream>>>(P);
     return cudaGetLastError();
 }
 
