@@ -93,13 +93,16 @@ void layer_coefficients(const axp_grid_desc &d, const std::vector<double> em[3],
     const double h = d.dt / 2.0, dt = d.dt;
     for (int a = 0; a < 3; a++) {
         const int64_t n = d.n[a];
-        out[a].assign(4 * n, T(0));
+        out[a].assign(6 * n, T(0));
         for (int64_t c = 0; c < n; c++) {
             const double se = em[a][c], sa = ax[a][c];
-            out[a][c] = (T)((1.0 - se * h / 2.0) / (1.0 + se * h / 2.0));
-            out[a][n + c] = (T)(h / (1.0 + se * h / 2.0));
-            out[a][2 * n + c] = (T)(dt * dt / (1.0 + sa * dt));
-            out[a][3 * n + c] = (T)((1.0 - sa * dt) / (1.0 + sa * dt));
+            const double A = (1.0 - se * h / 2.0) / (1.0 + se * h / 2.0), B = h / (1.0 + se * h / 2.0);
+            out[a][c] = (T)A;                      // one damped half-step: a F + b X
+            out[a][n + c] = (T)B;
+            out[a][2 * n + c] = (T)(A * A);        // two: a^2 F + b (1 + a) X
+            out[a][3 * n + c] = (T)(B * (1.0 + A));
+            out[a][4 * n + c] = (T)(dt * dt / (1.0 + sa * dt));
+            out[a][5 * n + c] = (T)((1.0 - sa * dt) / (1.0 + sa * dt));
         }
     }
 }
@@ -206,7 +209,7 @@ bool compute_layout(const axp_grid_desc &d, Workspace *w)
         w->off_sig_ax[a] = off;
         off += align_up((size_t)d.n[a] * e);
         w->off_pml_tab[a] = off;
-        off += align_up((size_t)4 * d.n[a] * e);
+        off += align_up((size_t)6 * d.n[a] * e);
     }
     int64_t nb = (cells(d) + 255) / 256;
     if (nb > 1024) nb = 1024;

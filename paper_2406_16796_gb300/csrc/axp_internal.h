@@ -45,10 +45,10 @@ struct Workspace {
     size_t off_J[3];
     size_t off_ghost[3][2][3];
     size_t off_sig_em[3], off_sig_ax[3];
-    // per axis, 4 x n[a] coefficients of the layer updates as products (fused 2D kernel):
-    // E/B: a = (1 - s h/2)/(1 + s h/2), b = h/(1 + s h/2); axion: c1 = dt^2/(1 + s dt),
-    // c2 = (1 - s dt)/(1 + s dt).  All decrease with s, so the corner value (largest
-    // s of the axes) is the smallest of the axes' values.
+    // per axis, 6 x n[a] coefficients of the layer updates as products (fused 2D kernel):
+    // E/B: a = (1 - s h/2)/(1 + s h/2), b = h/(1 + s h/2), and for two half-steps a^2,
+    // b (1 + a); axion: c1 = dt^2/(1 + s dt), c2 = (1 - s dt)/(1 + s dt).  All decrease
+    // with s, so the corner value (largest s of the axes) is the smallest of the axes'.
     size_t off_pml_tab[3];
     size_t off_partials;
     size_t off_ring;

@@ -107,7 +107,7 @@ struct Params {
     T *Eout[6], *Bout[6];
     T *phi_out, *phib_out;     // phi^{n+3/2}; pi^{n+1} (increment storage only)
     const T *sig_em[3], *sig_ax[3];
-    const T *pml_tab[3];  // per axis 4 x n: layer coefficients a, b (E/B) and c1, c2 (axion)
+    const T *pml_tab[3];  // per axis 6 x n: layer coefficients a, b, a^2, b(1+a) (E/B) and c1, c2 (axion)
     int n[3];
     int per[3];
     int axbc[3][2];

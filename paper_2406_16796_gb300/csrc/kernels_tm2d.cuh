@@ -99,13 +99,36 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
     const T Bx = P.Bext[0], By = P.Bext[1], Bz = P.Bext[2];
     const bool xl = wx >= 0 && P.has_pml;
     const T sxa = xl ? P.sig_ax[0][wx] : T(0);
-    // this column's layer coefficients (the plain update's where there is no layer)
-    const T aex = xl ? P.pml_tab[0][wx] : T(1);
-    const T bex = xl ? P.pml_tab[0][nx + wx] : h;
-    const T c1x = xl ? P.pml_tab[0][2 * nx + wx] : P.dt2;
-    const T c2x = xl ? P.pml_tab[0][3 * nx + wx] : T(1);
+    // this column's layer coefficients (the plain update's where there is no layer):
+    // one half-step a, b; two half-steps a^2, b (1 + a); axion k1, k2
+    const T ax1 = xl ? P.pml_tab[0][wx] : T(1);
+    const T bx1 = xl ? P.pml_tab[0][nx + wx] : h;
+    const T ax2 = xl ? P.pml_tab[0][2 * nx + wx] : T(1);
+    const T bx2 = xl ? P.pml_tab[0][3 * nx + wx] : T(2) * h;
+    const T kx1 = xl ? P.pml_tab[0][4 * nx + wx] : P.dt2;
+    const T kx2 = xl ? P.pml_tab[0][5 * nx + wx] : T(1);
     auto smax = [](T a, T b) { return a > b ? a : b; };
     auto smin = [](T a, T b) { return a < b ? a : b; };
+    // The y values of the same coefficients (and the axion sigma) are the same for
+    // a whole plane: a ring of 8 planes in shared memory, copied asynchronously
+    // with the plane's inputs (NS - 1 planes ahead), keeps their loads off the
+    // per-plane critical path.  Planes t-4 .. t+NS-1 are live at once.
+    enum { Y_A1, Y_B1, Y_A2, Y_B2, Y_K1, Y_K2, Y_SA, NY };
+    __shared__ __align__(16) T yring[8][NY + 1];
+    auto fill_y = [&](int p) {
+        if (tx < NY) {
+            T *dst = &yring[p & 7][tx];
+            if (!pery && P.has_pml && p >= 0 && p < ny) {
+                cp_elem(dst, tx < Y_SA ? P.pml_tab[1] + (tx * ny + p) : P.sig_ax[1] + p, true);
+            } else {  // no layer: the plain update's coefficients
+                *dst = (tx == Y_A1 || tx == Y_A2 || tx == Y_K2) ? T(1)
+                       : tx == Y_B1                              ? h
+                       : tx == Y_B2                              ? T(2) * h
+                       : tx == Y_K1                              ? P.dt2
+                                                                 : T(0);
+            }
+        }
+    };
 
     // column history along y; suffix k = plane t - k of the current iteration
     T E0z0 = 0, E0z1 = 0, E0z2 = 0;
@@ -130,6 +153,7 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
         return (wx < 0 || wp < 0) ? (int64_t)-1 : (int64_t)wx + (int64_t)nx * wp;
     };
     auto prefetch = [&](int p) {
+        fill_y(p);
         const int64_t gi = gidx(p);
         const bool ok = gi >= 0;
         const int64_t o = ok ? gi : 0;
@@ -161,21 +185,24 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
         pb0 = st[10 * TX];
     };
     // Absorbing-layer half-step F <- ((1 - s h/2) F + h X) / (1 + s h/2) written as
-    // a F + b X with per-axis tables of a and b; at a corner s is the largest of
-    // the axes' values, and a, b decrease with s, so the corner's a, b are the
-    // smallest of the axes' table values.  Outside every layer a = 1, b = h and
-    // the update is the plain half-step bit for bit.
-    auto lay_em = [&](bool in, int p, T &a, T &b) {
-        a = aex;
-        b = bex;
-        if (in && !pery && P.has_pml) {
-            a = smin(a, P.pml_tab[1][p]);
-            b = smin(b, P.pml_tab[1][ny + p]);
+    // a F + b X, and two of them as a^2 F + b (1 + a) X, with per-axis tables; at a
+    // corner s is the largest of the axes' values and every coefficient decreases
+    // with s, so the corner's coefficients are the smallest of the axes'.  Where
+    // a = 1 (no layer) the plain half-steps are taken, bit for bit.
+    auto lay = [&](bool in, int p, T &a1, T &b1, T &a2, T &b2) {
+        a1 = ax1;
+        b1 = bx1;
+        a2 = ax2;
+        b2 = bx2;
+        if (in && !pery) {
+            const T *y = yring[p & 7];
+            a1 = smin(a1, y[Y_A1]);
+            b1 = smin(b1, y[Y_B1]);
+            a2 = smin(a2, y[Y_A2]);
+            b2 = smin(b2, y[Y_B2]);
         }
     };
-    auto dmp = [](T F, T X, T a, T b) { return fma(b, X, a * F); };
     auto inside = [&](int p) { return wx >= 0 && (pery || (p >= 0 && p < ny)); };
-    auto sig_y = [&](const T *tab, int p) { return pery ? T(0) : tab[p]; };
 
     // one iteration's four stages; EDGE adds the closure zeros and the layer damping
     auto body = [&](auto edge_tag, int t, int b) {
@@ -197,13 +224,21 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
                 N1y1 = fma(-h, c1y, fma(-h, c1y, B1y1));
                 N1z1 = fma(-h, c1z, fma(-h, c1z, B1z1));
             } else {
-                T a, b;
-                lay_em(in, p, a, b);
-                N0x1 = dmp(dmp(B0x1, -c0x, a, b), -c0x, a, b);
-                N0y1 = dmp(dmp(B0y1, -c0y, a, b), -c0y, a, b);
-                N1x1 = dmp(dmp(B1x1, -c1x, a, b), -c1x, a, b);
-                N1y1 = dmp(dmp(B1y1, -c1y, a, b), -c1y, a, b);
-                N1z1 = dmp(dmp(B1z1, -c1z, a, b), -c1z, a, b);
+                T a1, b1, a2, b2;
+                lay(in, p, a1, b1, a2, b2);
+                if (a2 == T(1)) {
+                    N0x1 = fma(-h, c0x, fma(-h, c0x, B0x1));
+                    N0y1 = fma(-h, c0y, fma(-h, c0y, B0y1));
+                    N1x1 = fma(-h, c1x, fma(-h, c1x, B1x1));
+                    N1y1 = fma(-h, c1y, fma(-h, c1y, B1y1));
+                    N1z1 = fma(-h, c1z, fma(-h, c1z, B1z1));
+                } else {
+                    N0x1 = fma(-b2, c0x, a2 * B0x1);
+                    N0y1 = fma(-b2, c0y, a2 * B0y1);
+                    N1x1 = fma(-b2, c1x, a2 * B1x1);
+                    N1y1 = fma(-b2, c1y, a2 * B1y1);
+                    N1z1 = fma(-b2, c1z, a2 * B1z1);
+                }
             }
             if (EDGE && !in) N0x1 = N0y1 = N1x1 = N1y1 = N1z1 = T(0);
             if (write_col && p >= m0 && p < m1) {
@@ -224,7 +259,7 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
             // mass term kept apart, so that neither rounds against the 2*phi terms
             const T spx = INCR ? (R[R_PHI][tx + 2] - ph2) + (R[R_PHI][tx] - ph2) : R[R_PHI][tx + 2] + R[R_PHI][tx];
             const T spy = INCR ? (ph1 - ph2) + (ph3 - ph2) : ph1 + ph3;
-            const T sa = (EDGE && in && P.has_pml) ? smax(sxa, sig_y(P.sig_ax[1], p)) : T(0);
+            const T sa = (EDGE && in && P.has_pml) ? (pery ? sxa : smax(sxa, yring[p & 7][Y_SA])) : T(0);
             T nw, pin = T(0);
             if (!EDGE || sa == T(0)) {
                 T acc = INCR ? fma(c0, ph2, pb2) : fma(c0, ph2, -pb2);
@@ -243,10 +278,10 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
                 const T Y = ((g * S - P.m2 * ph2) + lap) - sa * sa * ph2;
                 // damped leapfrog (1 + s dt) pi^{n+1} = dt^2 Y + (1 - s dt) pi^n as
                 // pi^{n+1} = c1 Y + c2 pi^n, with the corner's (smallest) coefficients
-                T c1 = c1x, c2 = c2x;
+                T c1 = kx1, c2 = kx2;
                 if (!pery) {
-                    c1 = smin(c1, P.pml_tab[1][2 * ny + p]);
-                    c2 = smin(c2, P.pml_tab[1][3 * ny + p]);
+                    c1 = smin(c1, yring[p & 7][Y_K1]);
+                    c2 = smin(c2, yring[p & 7][Y_K2]);
                 }
                 if (INCR) {
                     pin = fma(c1, Y, c2 * pb2);
@@ -272,9 +307,9 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
             if (!EDGE) {
                 EN2 = fma(h, cB, E0z2);
             } else {
-                T a, b;
-                lay_em(in, p, a, b);
-                EN2 = dmp(E0z2, cB, a, b);
+                T a1, b1, a2, b2;
+                lay(in, p, a1, b1, a2, b2);
+                EN2 = a1 == T(1) ? fma(h, cB, E0z2) : fma(b1, cB, a1 * E0z2);
             }
             if (EDGE && !in) MID2 = DT2 = EN2 = T(0);
         }
@@ -310,12 +345,18 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
                     ez = fma(h, xz, fma(h, xz, E1z4));
                     e0 = fma(h, cb0, EN4);
                 } else {
-                    T a, b;
-                    lay_em(in, p, a, b);
-                    ex = dmp(dmp(E1x4, xx, a, b), xx, a, b);
-                    ey = dmp(dmp(E1y4, xy, a, b), xy, a, b);
-                    ez = dmp(dmp(E1z4, xz, a, b), xz, a, b);
-                    e0 = dmp(EN4, cb0, a, b);
+                    T a1, b1, a2, b2;
+                    lay(in, p, a1, b1, a2, b2);
+                    if (a2 == T(1)) {
+                        ex = fma(h, xx, fma(h, xx, E1x4));
+                        ey = fma(h, xy, fma(h, xy, E1y4));
+                        ez = fma(h, xz, fma(h, xz, E1z4));
+                    } else {
+                        ex = fma(b2, xx, a2 * E1x4);
+                        ey = fma(b2, xy, a2 * E1y4);
+                        ez = fma(b2, xz, a2 * E1z4);
+                    }
+                    e0 = a1 == T(1) ? fma(h, cb0, EN4) : fma(b1, cb0, a1 * EN4);
                 }
                 if (write_col) {
                     const int64_t gi = (int64_t)gx + (int64_t)nx * p;
@@ -330,6 +371,7 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
 
     // planes t0 .. t0+NS-2 in flight, then one more per iteration; after the
     // wait at the end of iteration t everything up to plane t+1 has landed
+    for (int p = t0 - 4; p < t0; p++) fill_y(p);  // joins the first group (plane t0)
     for (int j = 0; j < NS - 1; j++) {
         if (t0 + j <= t1) prefetch(t0 + j);
         cp_commit();
