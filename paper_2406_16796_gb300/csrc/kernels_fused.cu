@@ -1,5 +1,6 @@
 // kernels_fused.cu -- host side of the fused single-pass step: eligibility,
 // parameter setup, launch geometry and the per-step buffer rotation.
+#include <algorithm>
 #include <cmath>
 #include <utility>
 
@@ -167,6 +168,7 @@ fused::Params<T> make_params(axp_grid *g)
     P.g = (T)d.g;
     P.m2 = (T)(d.m * d.m);
     P.chunk = 1;
+    P.chunk_edge = 1;
     return P;
 }
 
@@ -314,35 +316,62 @@ cudaError_t fused_step(axp_grid *g, int64_t nsteps, bool *handled)
             }
         }
     } else if (tm) {
-        // tile width and march chunks together: the fewest waves of resident blocks
-        // for the work a wave does (planes + pipeline) x columns x blocks per SM
+        // Tile width and march chunks: the fewest resident-block waves for the work
+        // a wave does, (planes + pipeline) x columns x blocks per SM.  Strips at a
+        // non-periodic x edge run the edge body over the layers and take about
+        // kEdgeCost times as long per plane; with one wave they may get more,
+        // shorter chunks from the blocks the other strips leave free.
+        const double kEdgeCost = sizeof(T) == 8 ? 1.30 : 1.10;
         int sms = 152;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
         const int64_t nx = g->desc.n[0], ny = g->desc.n[1];
+        const bool xedge = g->desc.em_bc[0][0] != AXP_BC_PERIODIC;
         double best = -1.0;
+        int best_ce = 0, best_rows = 0;
         for (int tx = tm2d::TX; tx >= 128; tx -= 32) {
             int o = 0;
             if ((e = dispatch_tm2d<T>(P, 0, g->stream, &o, tx)) != cudaSuccess) return e;
             o = o > 0 ? o : 1;
             const int64_t strips = (nx + (tx - tm2d::HL - tm2d::HR) - 1) / (tx - tm2d::HL - tm2d::HR);
             const int64_t slots = (int64_t)sms * o;
-            for (int64_t nc = 1; nc <= 64 && ny / nc >= 16; nc++) {
-                const int64_t chunk = (ny + nc - 1) / nc, ctas = strips * ((ny + chunk - 1) / chunk);
-                const int64_t waves = (ctas + slots - 1) / slots;
-                const double cost = (double)waves * (double)(chunk + 6) * tx * o;
+            const double r = xedge ? kEdgeCost : 1.0;
+            for (int64_t nc = 1; nc <= 64 && ny / nc >= 16; nc++) {  // the same chunks everywhere
+                const int64_t chunk = (ny + nc - 1) / nc, rows = (ny + chunk - 1) / chunk;
+                const int64_t waves = (strips * rows + slots - 1) / slots;
+                const double cost = (double)waves * (double)(chunk + 6) * r * tx * o;
                 if (best < 0 || cost < best) {
                     best = cost;
                     tm_tx = tx;
                     P.chunk = (int)chunk;
-                    nchunks = (int)((ny + chunk - 1) / chunk);
+                    best_ce = (int)chunk;
+                    best_rows = (int)rows;
+                }
+            }
+            if (!xedge || strips < 3) continue;
+            for (int64_t ni = 1; ni <= 64 && ny / ni >= 16; ni++) {  // shorter chunks at the x edges
+                const int64_t ci = (ny + ni - 1) / ni, ri = (ny + ci - 1) / ci;
+                const int64_t left = slots - (strips - 2) * ri;
+                if (left < 2) break;
+                int64_t ne = std::min<int64_t>(left / 2, std::max<int64_t>(1, ny / 16));
+                const int64_t ce = (ny + ne - 1) / ne, re = (ny + ce - 1) / ce;
+                const double cost = std::max((double)(ci + 6), (double)(ce + 6) * r) * tx * o;
+                if (cost < best) {
+                    best = cost;
+                    tm_tx = tx;
+                    P.chunk = (int)ci;
+                    best_ce = (int)ce;
+                    best_rows = (int)std::max(ri, re);
                 }
             }
         }
         if (best < 0) {  // grids shorter than 16 planes: one chunk
             tm_tx = tm2d::TX;
             P.chunk = (int)ny;
-            nchunks = 1;
+            best_ce = (int)ny;
+            best_rows = 1;
         }
+        P.chunk_edge = best_ce;
+        nchunks = best_rows;
     } else if (mode >= 2) {
         int sms = 152;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
@@ -374,9 +403,10 @@ cudaError_t fused_step(axp_grid *g, int64_t nsteps, bool *handled)
     }
     for (; it < nsteps; it++) {
         if (it > 0) {
-            const int ch = P.chunk;
+            const int ch = P.chunk, che = P.chunk_edge;
             P = make_params<T>(g);
             P.chunk = ch;
+            P.chunk_edge = che;
         }
         e = launch(P, nchunks, nullptr);
         if (e != cudaSuccess) return e;
@@ -426,6 +456,7 @@ fused::Params<T> tm2d_params(axp_grid *g, int chunk)
 {
     fused::Params<T> P = make_params<T>(g);
     P.chunk = chunk;
+    P.chunk_edge = chunk;
     return P;
 }
 

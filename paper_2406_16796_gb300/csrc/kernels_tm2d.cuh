@@ -84,8 +84,13 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
     int wx = gx;
     if (wx < 0 || wx >= nx) wx = perx ? ((wx % nx) + nx) % nx : -1;
     const bool write_col = tx >= HL && tx < ntx - HR && gx >= 0 && gx < nx;
-    const int m0 = by * P.chunk;
-    const int m1 = min(ny, m0 + P.chunk);
+    // the strips at a non-periodic x edge (which carry the x layers and run the
+    // edge body) may march shorter chunks than the others
+    const int nstrips = (nx + vx - 1) / vx;
+    const int chunk = (!perx && (bx == 0 || bx == nstrips - 1)) ? P.chunk_edge : P.chunk;
+    const int m0 = by * chunk;
+    if (m0 >= ny) return;  // (the whole block: more chunk rows than this strip uses)
+    const int m1 = min(ny, m0 + chunk);
     const int gx0 = bx * vx - HL;
     // The plain body is exact for a column inside the grid with no x layer (the
     // edge body adds nothing there), so the choice is made per warp: in a tile
