@@ -227,9 +227,9 @@ def bytes_per_cell(prec):
 # one-pass stencil grows with the cells); None until a capture of the kernel as
 # it stands exists.  Sources are summarised under profiles/.
 TRAFFIC = {
-    # k_tm2d, 2048 x 2048 captures: FP64 682.2 MB, FP32 split 345.3 MB per launch
-    ("k_tm2d (one launch per step)", "fp64"): 682.2e6 * (4096 * 2048) / (2048 * 2048),
-    ("k_tm2d (one launch per step)", "fp32"): 345.3e6 * (4096 * 2048) / (2048 * 2048),
+    # k_tm2d, 2048 x 2048 captures: FP64 685.0 MB, FP32 split 341.9 MB per launch
+    ("k_tm2d (one launch per step)", "fp64"): 685.0e6 * (4096 * 2048) / (2048 * 2048),
+    ("k_tm2d (one launch per step)", "fp32"): 341.9e6 * (4096 * 2048) / (2048 * 2048),
 }
 # k_ax3d (3D, no order-0 fields), 256^3 capture: 1088.9 MB per launch
 TRAFFIC_3D_PER_CELL = 1088.9e6 / 256 ** 3
