@@ -214,6 +214,15 @@ __device__ __forceinline__ T half_update(T F, T X, T sig, T h)
 
 __device__ __forceinline__ void cell_of(int64_t c, const int64_t n[3], int64_t *i, int64_t *j, int64_t *k)
 {
+    if (c < 0xffffffffLL && n[0] < 0xffffffffLL && n[1] < 0xffffffffLL) {
+        // 32-bit division where the index fits (64-bit division is a long sequence)
+        const uint32_t cc = (uint32_t)c, n0 = (uint32_t)n[0], n1 = (uint32_t)n[1];
+        const uint32_t r = cc / n0;
+        *i = cc - r * n0;
+        *j = r % n1;
+        *k = r / n1;
+        return;
+    }
     *i = c % n[0];
     const int64_t r = c / n[0];
     *j = r % n[1];

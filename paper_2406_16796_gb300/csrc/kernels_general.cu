@@ -46,9 +46,27 @@ __device__ T p_comp(const View<T> &v, const PhiPair<T, INCR> &q, int a, int64_t 
     return Dt * b0_bar(v, a, i, j, k) - cross;
 }
 
-// J_a(c + a/2) = (P_a(c) + P_a(c + a)) / 2, all three components.
+template <typename T>
+struct PBuf {
+    T *p[3];
+};
+
+// P at every cell centre, into scratch (one evaluation per cell and component).
 template <typename T, bool INCR>
-__global__ void __launch_bounds__(kThreads) k_current(View<T> v, PhiPair<T, INCR> q)
+__global__ void __launch_bounds__(kThreads) k_pcell(View<T> v, PhiPair<T, INCR> q, PBuf<T> P)
+{
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < v.N; c += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i, j, k;
+        cell_of(c, v.n, &i, &j, &k);
+        for (int a = 0; a < 3; a++) P.p[a][c] = p_comp<T, INCR>(v, q, a, i, j, k);
+    }
+}
+
+// J_a(c + a/2) = (P_a(c) + P_a(c + a)) / 2, all three components; P(c + a) comes
+// from the scratch where c + a is a grid cell (its periodic image included) and
+// is evaluated in place beyond a non-periodic edge (ghost rules).
+template <typename T, bool INCR>
+__global__ void __launch_bounds__(kThreads) k_current(View<T> v, PhiPair<T, INCR> q, PBuf<T> P)
 {
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < v.N; c += (int64_t)gridDim.x * blockDim.x) {
         int64_t i, j, k;
@@ -56,8 +74,18 @@ __global__ void __launch_bounds__(kThreads) k_current(View<T> v, PhiPair<T, INCR
         for (int a = 0; a < 3; a++) {
             int64_t u[3];
             unit(a, u);
-            const T p0 = p_comp<T, INCR>(v, q, a, i, j, k);
-            const T p1 = p_comp<T, INCR>(v, q, a, i + u[0], j + u[1], k + u[2]);
+            const T p0 = P.p[a][c];
+            int64_t w[3] = {i + u[0], j + u[1], k + u[2]};
+            bool in = true;
+            if (w[a] >= v.n[a]) {
+                // the periodic image is the same evaluation only when both the fields
+                // and the axion wrap along a
+                if (v.periodic[a] && v.axbc[a][0] == AXP_BC_PERIODIC && v.axbc[a][1] == AXP_BC_PERIODIC)
+                    w[a] -= v.n[a];
+                else
+                    in = false;
+            }
+            const T p1 = in ? P.p[a][lin3(v.n, w[0], w[1], w[2])] : p_comp<T, INCR>(v, q, a, w[0], w[1], w[2]);
             v.J[a][c] = T(0.5) * (p0 + p1);
         }
     }
@@ -276,8 +304,13 @@ static cudaError_t launch_current(axp_grid *g, const View<T> &v, const T *hi, co
     q.b = b;
     q.ghi = ghosts_at<T>(g, lev_hi);
     q.glo = ghosts_at<T>(g, lev_lo);
-    k_current<T, INCR><<<grid_for(v.N), kThreads, 0, g->stream>>>(v, q);
-    g->launches++;
+    // scratch for P: the spare field set's B0 arrays, which no caller of this
+    // function holds data in (the spare set carries at most E arrays here)
+    PBuf<T> P;
+    for (int a = 0; a < 3; a++) P.p[a] = (T *)(g->ws + g->layout.off_fields[1 - g->fset][kB0 + a]);
+    k_pcell<T, INCR><<<grid_for(v.N), kThreads, 0, g->stream>>>(v, q, P);
+    k_current<T, INCR><<<grid_for(v.N), kThreads, 0, g->stream>>>(v, q, P);
+    g->launches += 2;
     return cudaGetLastError();
 }
 
