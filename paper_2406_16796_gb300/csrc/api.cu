@@ -196,6 +196,10 @@ bool compute_layout(const axp_grid_desc &d, Workspace *w)
         w->off_J[a] = off;
         off += arr;
     }
+    for (int a = 0; a < 3; a++) {  // P at cell centres (general path scratch)
+        w->off_P[a] = off;
+        off += arr;
+    }
     for (int a = 0; a < 3; a++)
         for (int s = 0; s < 2; s++)
             for (int l = 0; l < 3; l++) {

@@ -43,6 +43,7 @@ struct Workspace {
     size_t off_fields[2][kFields];  // two field sets: the fused step reads one and writes the other
     size_t off_phi[4];              // axion buffers; roles are tracked by the handle
     size_t off_J[3];
+    size_t off_P[3];  // scratch of the general path's current: P at cell centres
     size_t off_ghost[3][2][3];
     size_t off_sig_em[3], off_sig_ax[3];
     // per axis, 6 x n[a] coefficients of the layer updates as products (fused 2D kernel):

@@ -304,10 +304,11 @@ static cudaError_t launch_current(axp_grid *g, const View<T> &v, const T *hi, co
     q.b = b;
     q.ghi = ghosts_at<T>(g, lev_hi);
     q.glo = ghosts_at<T>(g, lev_lo);
-    // scratch for P: the spare field set's B0 arrays, which no caller of this
-    // function holds data in (the spare set carries at most E arrays here)
+    // P at the cell centres goes to its own workspace arrays (the field sets may
+    // not be written: the fused kernels leave inactive arrays untouched, so any
+    // value left in one would become part of the state)
     PBuf<T> P;
-    for (int a = 0; a < 3; a++) P.p[a] = (T *)(g->ws + g->layout.off_fields[1 - g->fset][kB0 + a]);
+    for (int a = 0; a < 3; a++) P.p[a] = (T *)(g->ws + g->layout.off_P[a]);
     k_pcell<T, INCR><<<grid_for(v.N), kThreads, 0, g->stream>>>(v, q, P);
     k_current<T, INCR><<<grid_for(v.N), kThreads, 0, g->stream>>>(v, q, P);
     g->launches += 2;

@@ -426,3 +426,28 @@ def test_1d_graph_replay_matches_single_launches(prec):
     assert a.step_count == b.step_count == 197
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("steps", [1, 3, 7])
+def test_fused_odd_step_counts_keep_inactive_arrays_zero(steps):
+    """After an odd number of fused steps the state lives in the second field set;
+    the arrays the step does not touch (here E0x, E0y, B0z of the TM set) must
+    still be zero there, and the fields equal the oracle's."""
+    axp = axp_mod()
+    grid = periodic_grid(g=1.3, m=2.0, n=(64, 90, 1), B_ext=(0.1, -0.2, -1.0), axion_bc=W._bcs("periodic", "pml"),
+                         em_bc=W._bcs("periodic", "pml"), pml_cells=6)
+    active = ["E0z", "B0x", "B0y"] + [n for n in W.FIELD_NAMES if n[1] == "1"]
+    st = W.random_state(grid, seed=77, active=active)
+    og = oracle.OracleGrid(grid)
+    og.load(st)
+    og.step(steps)
+    g = axp.Grid(grid)
+    g.load(st)
+    g.step(steps)
+    assert g.kernel_path() == axp.AXP_KERNEL_TM2D
+    got, ref = g.fields(), og.fields()
+    for k in ("E0x", "E0y", "B0z"):
+        assert not got[k].any(), k
+    for k in NAMES:
+        assert rel(got[k], ref[k]) < 1e-12, (steps, k, rel(got[k], ref[k]))
+    g.close()
