@@ -100,6 +100,8 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
     const int ylo = P.lay[1][0], yhi = ny - 1 - P.lay[1][1];
 
     const T h = P.h, g = P.g, idx = P.idx[0], idy = P.idx[1], hidx = P.hidx[0], hidy = P.hidx[1];
+    // step constants of the folded updates
+    const T hx = h * idx, hy = h * idy, h2x = T(2) * hx, h2y = T(2) * hy, hg = h * g, h2g = T(2) * hg;
     const T cx = P.lap_c[0], cy = P.lap_c[1], c0 = P.lap_0, dt2g = P.dt2g, inv_dt = P.inv_dt;
     const T Bx = P.Bext[0], By = P.Bext[1], Bz = P.Bext[2];
     const bool xl = wx >= 0 && P.has_pml;
@@ -217,27 +219,30 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
         {
             const int p = t - 1;
             const bool in = !EDGE || inside(p);
-            const T c0x = (E0z0 - E0z1) * idy;                  // (curl E0)_x =  D_y E0z
-            const T c0y = -(R[R_E0Z][tx + 2] - E0z1) * idx;       // (curl E0)_y = -D_x E0z
-            const T c1x = (E1z0 - E1z1) * idy;
-            const T c1y = -(R[R_E1Z][tx + 2] - E1z1) * idx;
-            const T c1z = (R[R_E1Y][tx + 2] - E1y1) * idx - (E1x0 - E1x1) * idy;  // D_x E1y - D_y E1x
+            // differences of E^{n+1/2} (times the cell size)
+            const T d0y = E0z0 - E0z1, d0x = R[R_E0Z][tx + 2] - E0z1;
+            const T d1zy = E1z0 - E1z1, d1zx = R[R_E1Z][tx + 2] - E1z1;
+            const T d1yx = R[R_E1Y][tx + 2] - E1y1, d1xy = E1x0 - E1x1;
+            // B^{n+1} = B^n - 2h curl E^{n+1/2}: the two half-steps as one multiply-add
+            // per difference, (curl E0)_x = D_y E0z, (curl E0)_y = -D_x E0z,
+            // (curl E1)_z = D_x E1y - D_y E1x
+            auto plain = [&]() {
+                N0x1 = fma(-h2y, d0y, B0x1);
+                N0y1 = fma(h2x, d0x, B0y1);
+                N1x1 = fma(-h2y, d1zy, B1x1);
+                N1y1 = fma(h2x, d1zx, B1y1);
+                N1z1 = fma(-h2x, d1yx, fma(h2y, d1xy, B1z1));
+            };
             if (!EDGE) {
-                N0x1 = fma(-h, c0x, fma(-h, c0x, B0x1));
-                N0y1 = fma(-h, c0y, fma(-h, c0y, B0y1));
-                N1x1 = fma(-h, c1x, fma(-h, c1x, B1x1));
-                N1y1 = fma(-h, c1y, fma(-h, c1y, B1y1));
-                N1z1 = fma(-h, c1z, fma(-h, c1z, B1z1));
+                plain();
             } else {
                 T a1, b1, a2, b2;
                 lay(in, p, a1, b1, a2, b2);
                 if (a2 == T(1)) {
-                    N0x1 = fma(-h, c0x, fma(-h, c0x, B0x1));
-                    N0y1 = fma(-h, c0y, fma(-h, c0y, B0y1));
-                    N1x1 = fma(-h, c1x, fma(-h, c1x, B1x1));
-                    N1y1 = fma(-h, c1y, fma(-h, c1y, B1y1));
-                    N1z1 = fma(-h, c1z, fma(-h, c1z, B1z1));
+                    plain();
                 } else {
+                    const T c0x = d0y * idy, c0y = -d0x * idx, c1x = d1zy * idy, c1y = -d1zx * idx;
+                    const T c1z = d1yx * idx - d1xy * idy;
                     N0x1 = fma(-b2, c0x, a2 * B0x1);
                     N0y1 = fma(-b2, c0y, a2 * B0y1);
                     N1x1 = fma(-b2, c1x, a2 * B1x1);
@@ -307,14 +312,15 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
                 P.phi_out[gi] = nw;
                 if (INCR) P.phib_out[gi] = pin;
             }
-            // (curl B0)_z = D_x B0y - D_y B0x at the E0z location, backward differences
-            const T cB = (N0y2 - R[R_N0Y2][tx]) * idx - (N0x2 - N0x3) * idy;
+            // E0z^{n+1} = E0z^{n+1/2} + h (curl B0)_z, (curl B0)_z = D_x B0y - D_y B0x at the
+            // E0z location (backward differences)
+            const T dbx = N0y2 - R[R_N0Y2][tx], dby = N0x2 - N0x3;
             if (!EDGE) {
-                EN2 = fma(h, cB, E0z2);
+                EN2 = fma(hx, dbx, fma(-hy, dby, E0z2));
             } else {
                 T a1, b1, a2, b2;
                 lay(in, p, a1, b1, a2, b2);
-                EN2 = a1 == T(1) ? fma(h, cB, E0z2) : fma(b1, cB, a1 * E0z2);
+                EN2 = a1 == T(1) ? fma(hx, dbx, fma(-hy, dby, E0z2)) : fma(b1, dbx * idx - dby * idy, a1 * E0z2);
             }
             if (EDGE && !in) MID2 = DT2 = EN2 = T(0);
         }
@@ -335,33 +341,36 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
             const int p = t - 4;
             if (p >= m0 && p < m1) {
                 const bool in = !EDGE || inside(p);
-                const T jx = T(0.5) * (PX4 + R[R_PX4][tx + 2]);
-                const T jy = T(0.5) * (PY4 + PY3);
-                const T jz = PZ4;
-                const T cbx = (N1z4 - N1z5) * idy;                                     //  D_y B1z
-                const T cby = -(N1z4 - R[R_N1Z4][tx]) * idx;                           // -D_x B1z
-                const T cbz = (N1y4 - R[R_N1Y4][tx]) * idx - (N1x4 - N1x5) * idy;     //  D_x B1y - D_y B1x
-                const T xx = fma(-g, jx, cbx), xy = fma(-g, jy, cby), xz = fma(-g, jz, cbz);
-                const T cb0 = (N0y4 - R[R_N0Y4][tx]) * idx - (N0x4 - N0x5) * idy;
+                // J^{n+1} = face averages of P; E^{n+3/2} = E^{n+1/2} + 2h (curl B1^{n+1} - g J^{n+1})
+                // with (curl B1)_x = D_y B1z, (curl B1)_y = -D_x B1z, (curl B1)_z = D_x B1y - D_y B1x,
+                // and E0z^{n+3/2} = E0z^{n+1} + h (curl B0^{n+1})_z
+                const T sjx = PX4 + R[R_PX4][tx + 2], sjy = PY4 + PY3;  // 2 J_x, 2 J_y
+                const T e1zy = N1z4 - N1z5, e1zx = N1z4 - R[R_N1Z4][tx];
+                const T e1yx = N1y4 - R[R_N1Y4][tx], e1xy = N1x4 - N1x5;
+                const T e0yx = N0y4 - R[R_N0Y4][tx], e0xy = N0x4 - N0x5;
                 T ex, ey, ez, e0;
+                auto plain = [&]() {
+                    ex = fma(h2y, e1zy, fma(-hg, sjx, E1x4));
+                    ey = fma(-h2x, e1zx, fma(-hg, sjy, E1y4));
+                    ez = fma(h2x, e1yx, fma(-h2y, e1xy, fma(-h2g, PZ4, E1z4)));
+                    e0 = fma(hx, e0yx, fma(-hy, e0xy, EN4));
+                };
                 if (!EDGE) {
-                    ex = fma(h, xx, fma(h, xx, E1x4));
-                    ey = fma(h, xy, fma(h, xy, E1y4));
-                    ez = fma(h, xz, fma(h, xz, E1z4));
-                    e0 = fma(h, cb0, EN4);
+                    plain();
                 } else {
                     T a1, b1, a2, b2;
                     lay(in, p, a1, b1, a2, b2);
                     if (a2 == T(1)) {
-                        ex = fma(h, xx, fma(h, xx, E1x4));
-                        ey = fma(h, xy, fma(h, xy, E1y4));
-                        ez = fma(h, xz, fma(h, xz, E1z4));
+                        plain();
                     } else {
+                        const T xx = fma(-g, T(0.5) * sjx, e1zy * idy);
+                        const T xy = fma(-g, T(0.5) * sjy, -e1zx * idx);
+                        const T xz = fma(-g, PZ4, e1yx * idx - e1xy * idy);
                         ex = fma(b2, xx, a2 * E1x4);
                         ey = fma(b2, xy, a2 * E1y4);
                         ez = fma(b2, xz, a2 * E1z4);
+                        e0 = fma(b1, e0yx * idx - e0xy * idy, a1 * EN4);
                     }
-                    e0 = a1 == T(1) ? fma(h, cb0, EN4) : fma(b1, cb0, a1 * EN4);
                 }
                 if (write_col) {
                     const int64_t gi = (int64_t)gx + (int64_t)nx * p;
