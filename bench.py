@@ -210,7 +210,9 @@ def reference_arm(args):
 #    operations of the fused scheme for this component set (B update 22 ops /
 #    33 FLOPs, axion + E0 16 / 22, axion current 13 / 17, E update 26 / 38).
 #    Every one of them occupies the FP64 pipe for the same issue slot, so the
-#    FP64 roofline is in pipe operations.
+#    FP64 roofline is in pipe operations.  (The 2D kernel executes 57 of them per
+#    cell-update: it folds each pair of half-steps into one multiply-add per
+#    difference.  The roofline counts the scheme's 77.)
 ACTIVE_ARRAYS = 9
 FLOPS_PER_CELL = 110
 FP64_OPS_PER_CELL = 77
@@ -227,9 +229,9 @@ def bytes_per_cell(prec):
 # one-pass stencil grows with the cells); None until a capture of the kernel as
 # it stands exists.  Sources are summarised under profiles/.
 TRAFFIC = {
-    # k_tm2d, 2048 x 2048 captures: FP64 685.0 MB, FP32 split 341.9 MB per launch
-    ("k_tm2d (one launch per step)", "fp64"): 685.0e6 * (4096 * 2048) / (2048 * 2048),
-    ("k_tm2d (one launch per step)", "fp32"): 341.9e6 * (4096 * 2048) / (2048 * 2048),
+    # k_tm2d, 2048 x 2048 captures: FP64 685.6 MB, FP32 split 342.3 MB per launch
+    ("k_tm2d (one launch per step)", "fp64"): 685.6e6 * (4096 * 2048) / (2048 * 2048),
+    ("k_tm2d (one launch per step)", "fp32"): 342.3e6 * (4096 * 2048) / (2048 * 2048),
 }
 # k_ax3d (3D, no order-0 fields), 256^3 capture: 1088.9 MB per launch
 TRAFFIC_3D_PER_CELL = 1088.9e6 / 256 ** 3
