@@ -8,15 +8,16 @@
 //   1. B1^{n+1} = B1^n - h curl E1^{n+1/2} (twice)
 //   2. phi^{n+3/2}, D_t phi^{n+1} = (phi^{n+3/2} - phi^{n+1/2}) / dt
 //   3. E1^{n+3/2} = E1^{n+1/2} + 2 x h (curl B1^{n+1} - g J^{n+1})
-// the same arithmetic, operation for operation, as the generic fused kernel for
-// this component set.
+// the same mathematics as the generic fused kernel for this component set, with
+// the two half-steps of each curl folded into one multiply-add per difference.
 //
 // A block of TX x TY threads owns an (x, y) tile, one column per thread with a
 // halo of one column below and two above along x and y, and marches along z.
 // Stage 1 and 2 work on plane t-1 and stage 3 on plane t-2 while plane t is
 // taken in.  Each thread keeps its column's history along z in registers; the
-// values its x/y neighbours read are published into double-buffered shared
-// planes at the start of an iteration (one barrier per plane).  Inputs are
+// values its y neighbours read are published into double-buffered shared planes
+// at the start of an iteration (one barrier per plane); a warp is one x row of
+// the tile, so x neighbours come by warp shuffles.  Inputs are
 // staged NS planes ahead with cp.async, each thread copying and later reading
 // only its own column.
 #pragma once
@@ -33,7 +34,7 @@ constexpr int VX = TX - HL - HR, VY = TY - HL - HR;
 constexpr int PX = TX + 2, PY = TY + 2, PLANE = PX * PY;  // published planes, one guard cell around
 constexpr int NS = 4;                                     // input staging depth (power of two)
 constexpr int NIN = 8;                                    // E1 xyz, B1 xyz, phi, second axion level
-enum { P_EX, P_EY, P_EZ, P_PHI, P_NX, P_NY, P_NZ, P_DT, NPUB };
+enum { P_EX, P_EZ, P_PHI, P_NX, P_NZ, P_DT, NPUB };  // values read by the y neighbours
 
 template <typename T>
 constexpr size_t smem_bytes()
@@ -62,6 +63,10 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_ax3d(fused::Para
     const T idx = P.idx[0], idy = P.idx[1], idz = P.idx[2];
     const T cx = P.lap_c[0], cy = P.lap_c[1], cz = P.lap_c[2], c0 = P.lap_0;
     const T BEx = P.Bext[0], BEy = P.Bext[1], BEz = P.Bext[2];  // uniform background B
+    // step constants of the folded updates: two half-steps of the curls as one
+    // multiply-add per difference, and 2h g J_a = h g B_ext,a (D_t phi + neighbour)
+    const T h2x = T(2) * h * idx, h2y = T(2) * h * idy, h2z = T(2) * h * idz;
+    const T hgx = h * g * BEx, hgy = h * g * BEy, hgz = h * g * BEz;
 
     // column history along z; suffix k = plane t - k of the current iteration
     T Ex0 = 0, Ex1 = 0, Ex2 = 0, Ey0 = 0, Ey1 = 0, Ey2 = 0, Ez0 = 0, Ez1 = 0, Ez2 = 0;  // E^{n+1/2}
@@ -113,29 +118,32 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_ax3d(fused::Para
         if (t + NS - 1 <= t1) prefetch(t + NS - 1);
         tm2d::cp_commit();
         T *Q = pub + (t & 1) * (NPUB * PLANE);
-        // publish what the x/y neighbours read in this iteration
+        // publish what the y neighbours (other warps) read in this iteration; a
+        // warp is one x row of the tile, so x neighbours come by shuffles
         Q[P_EX * PLANE + me] = Ex1;
-        Q[P_EY * PLANE + me] = Ey1;
         Q[P_EZ * PLANE + me] = Ez1;
         Q[P_PHI * PLANE + me] = ph1;
         Q[P_NX * PLANE + me] = Nx2;
-        Q[P_NY * PLANE + me] = Ny2;
         Q[P_NZ * PLANE + me] = Nz2;
         Q[P_DT * PLANE + me] = D2;
+        const unsigned all = 0xffffffffu;
+        const T Ez_xp = __shfl_down_sync(all, Ez1, 1), Ey_xp = __shfl_down_sync(all, Ey1, 1);
+        const T ph_xp = __shfl_down_sync(all, ph1, 1), ph_xm = __shfl_up_sync(all, ph1, 1);
+        const T D_xp = __shfl_down_sync(all, D2, 1);
+        const T Nz_xm = __shfl_up_sync(all, Nz2, 1), Ny_xm = __shfl_up_sync(all, Ny2, 1);
         __syncthreads();
-        const T *qEx = Q + P_EX * PLANE + me, *qEy = Q + P_EY * PLANE + me, *qEz = Q + P_EZ * PLANE + me;
-        const T *qph = Q + P_PHI * PLANE + me, *qNx = Q + P_NX * PLANE + me, *qNy = Q + P_NY * PLANE + me;
+        const T *qEx = Q + P_EX * PLANE + me, *qEz = Q + P_EZ * PLANE + me;
+        const T *qph = Q + P_PHI * PLANE + me, *qNx = Q + P_NX * PLANE + me;
         const T *qNz = Q + P_NZ * PLANE + me, *qDt = Q + P_DT * PLANE + me;
 
         // ---- stage 1: B^{n+1} on plane t-1 (forward differences of E^{n+1/2}) ----
         {
             const int p = t - 1;
-            const T cEx = (qEz[PX] - Ez1) * idy - (Ey0 - Ey1) * idz;  // D_y E_z - D_z E_y
-            const T cEy = (Ex0 - Ex1) * idz - (qEz[1] - Ez1) * idx;   // D_z E_x - D_x E_z
-            const T cEz = (qEy[1] - Ey1) * idx - (qEx[PX] - Ex1) * idy;  // D_x E_y - D_y E_x
-            Nx1 = fma(-h, cEx, fma(-h, cEx, Bx1));
-            Ny1 = fma(-h, cEy, fma(-h, cEy, By1));
-            Nz1 = fma(-h, cEz, fma(-h, cEz, Bz1));
+            // B^{n+1} = B^n - 2h curl E^{n+1/2}, (curl E)_x = D_y E_z - D_z E_y,
+            // (curl E)_y = D_z E_x - D_x E_z, (curl E)_z = D_x E_y - D_y E_x
+            Nx1 = fma(-h2y, qEz[PX] - Ez1, fma(h2z, Ey0 - Ey1, Bx1));
+            Ny1 = fma(-h2z, Ex0 - Ex1, fma(h2x, Ez_xp - Ez1, By1));
+            Nz1 = fma(-h2x, Ey_xp - Ey1, fma(h2y, qEx[PX] - Ex1, Bz1));
             if (write_col && p >= m0 && p < m1) {
                 const int64_t gi = oidx(p);
                 P.Bout[3][gi] = Nx1;
@@ -149,7 +157,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_ax3d(fused::Para
             T nw, pin = T(0);
             if (INCR) {
                 // second differences from neighbour differences; the mass term apart
-                const T spx = (qph[1] - ph1) + (qph[-1] - ph1);
+                const T spx = (ph_xp - ph1) + (ph_xm - ph1);
                 const T spy = (qph[PX] - ph1) + (qph[-PX] - ph1);
                 const T spz = (ph0 - ph1) + (ph2 - ph1);
                 T acc = fma(c0, ph1, pb1);
@@ -160,7 +168,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_ax3d(fused::Para
                 nw = ph1 + pin;
                 D1 = pin * inv_dt;
             } else {
-                const T spx = qph[1] + qph[-1], spy = qph[PX] + qph[-PX], spz = ph0 + ph2;
+                const T spx = ph_xp + ph_xm, spy = qph[PX] + qph[-PX], spz = ph0 + ph2;
                 T acc = fma(c0, ph1, -pb1);
                 acc = fma(cx, spx, acc);
                 acc = fma(cy, spy, acc);
@@ -178,18 +186,13 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_ax3d(fused::Para
         {
             const int p = t - 2;
             if (write_col && p >= m0 && p < m1) {
-                // J_a = face average of P_a = D_t phi B_ext,a
-                const T jx = T(0.5) * (D2 * BEx + qDt[1] * BEx);
-                const T jy = T(0.5) * (D2 * BEy + qDt[PX] * BEy);
-                const T jz = T(0.5) * (D2 * BEz + D1 * BEz);
-                const T cBx = (Nz2 - qNz[-PX]) * idy - (Ny2 - Ny3) * idz;  // D_y B_z - D_z B_y
-                const T cBy = (Nx2 - Nx3) * idz - (Nz2 - qNz[-1]) * idx;   // D_z B_x - D_x B_z
-                const T cBz = (Ny2 - qNy[-1]) * idx - (Nx2 - qNx[-PX]) * idy;  // D_x B_y - D_y B_x
-                const T xx = fma(-g, jx, cBx), xy = fma(-g, jy, cBy), xz = fma(-g, jz, cBz);
+                // E^{n+3/2} = E^{n+1/2} + 2h (curl B^{n+1} - g J^{n+1}), J_a the face average of
+                // P_a = D_t phi B_ext,a; (curl B)_x = D_y B_z - D_z B_y, (curl B)_y = D_z B_x - D_x B_z,
+                // (curl B)_z = D_x B_y - D_y B_x (backward differences)
                 const int64_t gi = oidx(p);
-                P.Eout[3][gi] = fma(h, xx, fma(h, xx, Ex2));
-                P.Eout[4][gi] = fma(h, xy, fma(h, xy, Ey2));
-                P.Eout[5][gi] = fma(h, xz, fma(h, xz, Ez2));
+                P.Eout[3][gi] = fma(h2y, Nz2 - qNz[-PX], fma(-h2z, Ny2 - Ny3, fma(-hgx, D2 + D_xp, Ex2)));
+                P.Eout[4][gi] = fma(h2z, Nx2 - Nx3, fma(-h2x, Nz2 - Nz_xm, fma(-hgy, D2 + qDt[PX], Ey2)));
+                P.Eout[5][gi] = fma(h2x, Ny2 - Ny_xm, fma(-h2y, Nx2 - qNx[-PX], fma(-hgz, D2 + D1, Ez2)));
             }
         }
         // advance the column history by one plane
