@@ -233,8 +233,8 @@ TRAFFIC = {
     ("k_tm2d (one launch per step)", "fp64"): 685.6e6 * (4096 * 2048) / (2048 * 2048),
     ("k_tm2d (one launch per step)", "fp32"): 342.3e6 * (4096 * 2048) / (2048 * 2048),
 }
-# k_ax3d (3D, no order-0 fields), 256^3 capture: 1088.9 MB per launch
-TRAFFIC_3D_PER_CELL = 1088.9e6 / 256 ** 3
+# k_ax3d (3D, no order-0 fields), 256^3 capture: 1090.2 MB per launch
+TRAFFIC_3D_PER_CELL = 1090.2e6 / 256 ** 3
 
 
 def load_peaks():
