@@ -300,9 +300,9 @@ axp_status axp_get_launch_count(const axp_grid *grid, int64_t *count);
  * coupling, background, laser and step count.  All instances are stored in
  * FP32 split form (as AXP_FP32_SPLIT) and advanced together: one launch
  * advances every unfinished instance by up to `block_steps` steps, each
- * (instance, segment) work item keeping its cells in shared memory for the
- * whole block (time blocking; segments of large instances carry a halo of
- * 3 cells per step).  Diagnostics are accumulated in FP64.
+ * (instance, segment) work item keeping its cells in registers (8 per
+ * thread) for the whole block (time blocking; segments of large instances
+ * carry a halo of 3 cells per step).  Diagnostics are accumulated in FP64.
  *
  * Memory: the caller provides one device workspace sized for a maximum number
  * of instances and a total number of cells; instances are admitted into it
@@ -361,8 +361,9 @@ axp_status axp_batch_result(axp_batch *batch, int32_t slot, axp_diag *out);
 axp_status axp_batch_read_state(axp_batch *batch, int32_t slot, int32_t which, double *host_dst, size_t bytes);
 
 /* Time blocking: steps per launch, core cells per segment, threads per CTA.
- * block_steps in [1, 256]; segment_cells such that a segment and its halo fit
- * in shared memory; threads a multiple of 32 in [64, 1024]. */
+ * block_steps in [1, 256]; threads a multiple of 32 in [64, 512]; a work item
+ * holds 8 cells per thread, so segment_cells + 6 block_steps <= 8 threads
+ * (instances of up to 8 threads cells run whole). */
 axp_status axp_batch_set_tiling(axp_batch *batch, int32_t block_steps, int32_t segment_cells, int32_t threads);
 axp_status axp_batch_get_tiling(const axp_batch *batch, int32_t *block_steps, int32_t *segment_cells,
                                 int32_t *threads);

@@ -172,8 +172,8 @@ class Batch:
         import torch
 
         if candidates is None:
-            candidates = [(bs, seg, th) for bs in (16, 32, 64) for seg in (2048, 4096) for th in (256, 512, 1024)
-                          if seg + 6 * bs <= 5760]
+            candidates = [(bs, seg, th) for bs in (16, 32, 64) for seg in (1536, 3584) for th in (256, 512)
+                          if seg + 6 * bs <= 8 * th]
         times = {}
         for cand in candidates:
             self.set_tiling(*cand)

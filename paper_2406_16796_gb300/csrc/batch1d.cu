@@ -12,10 +12,12 @@
 //      (face averages along the invariant y, z are identities, so J = P);
 //      E1^{n+3/2} = E1^{n+1/2} + 2h (curl B1^{n+1} - g J);  E0y^{n+3/2} = E0y^{n+1} + h curl B0^{n+1}
 //
-// Work items are (instance, segment).  A CTA copies its item's cells into
-// shared memory -- the whole instance with periodic wrap when it fits, else a
-// segment plus a halo of 3 cells per step -- advances T steps there, and
-// writes the valid cells to the other of two global state buffers.  Each
+// Work items are (instance, segment).  A CTA loads its item's cells into
+// registers -- each thread K consecutive cells of the whole instance (periodic
+// wrap) when it fits, else of a segment plus a halo of 3 cells per step --
+// advances T steps there, and writes the valid cells to the other of two
+// global state buffers.  Only the cells at the ends of a thread's run are
+// exchanged, through shared memory, once per stage.  Each
 // cell's arithmetic is the same whatever the segmentation, the block length or
 // the other instances in the batch, so results are bit-identical alone and in
 // the mix.  Work items are taken from an atomic queue by a persistent grid;
@@ -33,10 +35,10 @@
 namespace axp {
 namespace {
 
-constexpr int kArr = 6 + 2;      // E0y B0z E1y E1z B1y B1z phi pi (global, per buffer)
-constexpr int kSmemArr = 10;     // + phi (second buffer) + phi^{n+1} in shared memory
-constexpr size_t kSmemMax = 230400;  // dynamic shared memory (the per-block limit is 232448 with the static part)
-constexpr int kCapCells = (int)(kSmemMax / (kSmemArr * sizeof(float)));  // cells per CTA in shared memory
+constexpr int kArr = 6 + 2;   // E0y B0z E1y E1z B1y B1z phi pi (global, per buffer)
+constexpr int kK = 8;         // consecutive cells per thread (held in registers)
+constexpr int kMaxThreads = 512;
+constexpr int kCapCells = kK * kMaxThreads;  // cells per work item at most
 
 struct Slot {
     int64_t off;        // first cell of this instance in every pool array
@@ -71,14 +73,34 @@ __device__ __forceinline__ float *arr(const Dev &D, int buf, int a, int64_t off)
     return D.pool + ((int64_t)(buf * kArr + a) * D.max_cells + off);
 }
 
-// One launch: every work item advances min(budget, remaining) steps.
-__global__ void __launch_bounds__(1024) k_batch_block(Dev D, int budget, int halo_per_step)
+// a[j] for a run-time j without indexing the register array (which would move
+// it to local memory)
+__device__ __forceinline__ float pick(const float (&a)[kK], int j)
 {
-    extern __shared__ __align__(16) float sm[];
+    float v = a[0];
+#pragma unroll
+    for (int k = 1; k < kK; k++) v = k == j ? a[k] : v;
+    return v;
+}
+
+// One launch: every work item advances min(budget, remaining) steps.
+//
+// Thread t holds cells [t K, t K + K) of the item (of n cells) in registers.
+// Per stage it needs one cell beyond each end of its run; the threads publish
+// their first and last cells' values in shared memory and read their
+// neighbours' after a barrier (the instance's last thread and thread 0 are
+// neighbours when the item is the whole periodic instance; a segment's end
+// cells see themselves, as the halo absorbs what that spoils).
+__global__ void __launch_bounds__(kMaxThreads) k_batch_block(Dev D, int budget, int halo_per_step)
+{
+    __shared__ float fE0[kMaxThreads], fE1y[kMaxThreads], fE1z[kMaxThreads];  // first cells
+    __shared__ float lB0[kMaxThreads], lB1y[kMaxThreads], lB1z[kMaxThreads];  // last cells
+    __shared__ float fMID[kMaxThreads], lMID[kMaxThreads];
+    __shared__ float fPH[2][kMaxThreads], lPH[2][kMaxThreads];  // by step parity
     __shared__ int s_item;
-    const int nt = blockDim.x;
+    const int nt = blockDim.x, t = threadIdx.x;
     for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(D.counter, 1);
+        if (t == 0) s_item = atomicAdd(D.counter, 1);
         __syncthreads();
         const int it = s_item;
         __syncthreads();
@@ -89,94 +111,143 @@ __global__ void __launch_bounds__(1024) k_batch_block(Dev D, int budget, int hal
         const int T = (int)(rem < budget ? rem : budget);
         if (!S.active || T <= 0) continue;
         const int nx = S.nx;
-        const int H = I.whole ? 0 : halo_per_step * T;
-        const int n = I.whole ? nx : I.len + 2 * H;
-        float *E0 = sm, *B0 = sm + n, *E1y = sm + 2 * n, *E1z = sm + 3 * n, *B1y = sm + 4 * n, *B1z = sm + 5 * n;
-        float *PA = sm + 6 * n, *PB = sm + 7 * n, *PI = sm + 8 * n, *MID = sm + 9 * n;
-        const int in = S.parity, out = S.parity ^ 1;
-        // load (global periodic wrap)
-        for (int i = threadIdx.x; i < n; i += nt) {
-            int gx = I.whole ? i : I.x0 - H + i;
-            gx %= nx;
-            if (gx < 0) gx += nx;
-            const int64_t o = S.off + gx;
-            E0[i] = arr(D, in, 0, o)[0];
-            B0[i] = arr(D, in, 1, o)[0];
-            E1y[i] = arr(D, in, 2, o)[0];
-            E1z[i] = arr(D, in, 3, o)[0];
-            B1y[i] = arr(D, in, 4, o)[0];
-            B1z[i] = arr(D, in, 5, o)[0];
-            PA[i] = arr(D, in, 6, o)[0];
-            PI[i] = arr(D, in, 7, o)[0];
-        }
-        __syncthreads();
         const bool wrapc = I.whole != 0;
-        const float h = S.h, idx = S.idx, hidx = S.hidx, cx = S.cx, c0 = S.c0, dt2g = S.dt2g, inv_dt = S.inv_dt;
+        const int H = wrapc ? 0 : halo_per_step * T;
+        const int n = wrapc ? nx : I.len + 2 * H;
+        const int c0 = t * kK;
+        const int cnt = max(0, min(kK, n - c0));  // cells this thread holds
+        const int lastT = (n - 1) / kK;           // thread holding cell n - 1
+        const int tl = t > 0 ? t - 1 : (wrapc ? lastT : -1);  // left neighbour thread (-1: none)
+        const int tr = t < lastT ? t + 1 : (wrapc ? 0 : -1);  // right neighbour thread
+        const int in = S.parity, out = S.parity ^ 1;
+        float E0[kK], B0[kK], E1y[kK], E1z[kK], B1y[kK], B1z[kK], PH[kK], PI[kK], MID[kK];
+#pragma unroll
+        for (int j = 0; j < kK; j++) {
+            E0[j] = B0[j] = E1y[j] = E1z[j] = B1y[j] = B1z[j] = PH[j] = PI[j] = MID[j] = 0.0f;
+            if (j < cnt) {
+                int gx = wrapc ? c0 + j : I.x0 - H + c0 + j;  // periodic wrap in the instance
+                gx %= nx;
+                if (gx < 0) gx += nx;
+                const int64_t o = S.off + gx;
+                E0[j] = arr(D, in, 0, o)[0];
+                B0[j] = arr(D, in, 1, o)[0];
+                E1y[j] = arr(D, in, 2, o)[0];
+                E1z[j] = arr(D, in, 3, o)[0];
+                B1y[j] = arr(D, in, 4, o)[0];
+                B1z[j] = arr(D, in, 5, o)[0];
+                PH[j] = arr(D, in, 6, o)[0];
+                PI[j] = arr(D, in, 7, o)[0];
+            }
+        }
+        const int jl = cnt > 0 ? cnt - 1 : 0;  // this thread's last cell
+        // the first cells' E and the end cells' phi for the first step
+        fE0[t] = E0[0];
+        fE1y[t] = E1y[0];
+        fE1z[t] = E1z[0];
+        fPH[0][t] = PH[0];
+        lPH[0][t] = pick(PH, jl);
+        __syncthreads();
+        const float h = S.h, idx = S.idx, hidx = S.hidx, cx = S.cx, c0m = S.c0, dt2g = S.dt2g, inv_dt = S.inv_dt;
         const float g = S.g, By = S.By, Bz = S.Bz;
-        float *phi = PA, *phin = PB;
-        for (int s = 0; s < T; s++) {
-            // 1. B^{n+1}
-            for (int i = threadIdx.x; i < n; i += nt) {
-                const int ip = wrapc ? (i + 1 == n ? 0 : i + 1) : min(i + 1, n - 1);
-                const float c0z = (E0[ip] - E0[i]) * idx;    // (curl E0)_z = D_x E0y
-                const float c1y = -(E1z[ip] - E1z[i]) * idx;  // (curl E1)_y = -D_x E1z
-                const float c1z = (E1y[ip] - E1y[i]) * idx;   // (curl E1)_z = D_x E1y
-                B0[i] = fmaf(-h, c0z, fmaf(-h, c0z, B0[i]));
-                B1y[i] = fmaf(-h, c1y, fmaf(-h, c1y, B1y[i]));
-                B1z[i] = fmaf(-h, c1z, fmaf(-h, c1z, B1z[i]));
+        for (int st = 0; st < T; st++) {
+            const int pb = st & 1;
+            // 1. B^{n+1}: needs E at i + 1
+            {
+                const float rE0 = tr >= 0 ? fE0[tr] : pick(E0, jl), rE1y = tr >= 0 ? fE1y[tr] : pick(E1y, jl);
+                const float rE1z = tr >= 0 ? fE1z[tr] : pick(E1z, jl);
+#pragma unroll
+                for (int j = 0; j < kK; j++) {
+                    const float e0p = j + 1 < cnt ? E0[j + 1] : rE0;
+                    const float e1zp = j + 1 < cnt ? E1z[j + 1] : rE1z;
+                    const float e1yp = j + 1 < cnt ? E1y[j + 1] : rE1y;
+                    const float c0z = (e0p - E0[j]) * idx;    // (curl E0)_z = D_x E0y
+                    const float c1y = -(e1zp - E1z[j]) * idx;  // (curl E1)_y = -D_x E1z
+                    const float c1z = (e1yp - E1y[j]) * idx;   // (curl E1)_z = D_x E1y
+                    B0[j] = fmaf(-h, c0z, fmaf(-h, c0z, B0[j]));
+                    B1y[j] = fmaf(-h, c1y, fmaf(-h, c1y, B1y[j]));
+                    B1z[j] = fmaf(-h, c1z, fmaf(-h, c1z, B1z[j]));
+                }
+                lB0[t] = pick(B0, jl);
+                lB1y[t] = pick(B1y, jl);
+                lB1z[t] = pick(B1z, jl);
             }
             __syncthreads();
-            // 2. axion; E0y^{n+1}
-            for (int i = threadIdx.x; i < n; i += nt) {
-                const int ip = wrapc ? (i + 1 == n ? 0 : i + 1) : min(i + 1, n - 1);
-                const int im = wrapc ? (i == 0 ? n - 1 : i - 1) : max(i - 1, 0);
-                const float Sg = E0[i] * By;  // Ebar0 . Bbar0 / g: E0y with the background along y
-                const float ph = phi[i];
-                // second difference from neighbour differences and the mass term kept
-                // apart (c0 = -(m dt)^2), so neither rounds against 2*phi
-                const float pin = fmaf(dt2g, Sg, fmaf(cx, (phi[ip] - ph) + (phi[im] - ph), fmaf(c0, ph, PI[i])));
-                PI[i] = pin;
-                phin[i] = ph + pin;
-                MID[i] = fmaf(0.5f, pin, ph);
-                const float cb = -(B0[i] - B0[im]) * idx;  // (curl B0)_y = -D_x B0z
-                E0[i] = fmaf(h, cb, E0[i]);
+            // 2. axion; E0y^{n+1}: needs phi at i +- 1 and B0 at i - 1
+            {
+                const float lph = tl >= 0 ? lPH[pb][tl] : PH[0], rph = tr >= 0 ? fPH[pb][tr] : pick(PH, jl);
+                const float lb0 = tl >= 0 ? lB0[tl] : B0[0];
+                float prevB0 = lb0;
+#pragma unroll
+                for (int j = 0; j < kK; j++) {
+                    const float php = j + 1 < cnt ? PH[j + 1] : rph;
+                    const float phm = j > 0 ? PH[j - 1] : lph;
+                    const float Sg = E0[j] * By;  // Ebar0 . Bbar0 / g: E0y with the background along y
+                    const float ph = PH[j];
+                    // second difference from neighbour differences and the mass term kept
+                    // apart (c0 = -(m dt)^2), so neither rounds against 2*phi
+                    const float pin = fmaf(dt2g, Sg, fmaf(cx, (php - ph) + (phm - ph), fmaf(c0m, ph, PI[j])));
+                    PI[j] = pin;
+                    MID[j] = fmaf(0.5f, pin, ph);
+                    const float cb = -(B0[j] - prevB0) * idx;  // (curl B0)_y = -D_x B0z
+                    prevB0 = B0[j];
+                    E0[j] = fmaf(h, cb, E0[j]);
+                }
+                fMID[t] = MID[0];
+                lMID[t] = pick(MID, jl);
             }
             __syncthreads();
-            // 3. axion current and the E updates
-            for (int i = threadIdx.x; i < n; i += nt) {
-                const int ip = wrapc ? (i + 1 == n ? 0 : i + 1) : min(i + 1, n - 1);
-                const int im = wrapc ? (i == 0 ? n - 1 : i - 1) : max(i - 1, 0);
-                const float Dt = PI[i] * inv_dt;
-                const float Py = Dt * By;
-                const float bz = 0.5f * (B0[i] + B0[im]) + Bz;
-                const float Pz = fmaf(E0[i], (MID[ip] - MID[im]) * hidx, Dt * bz);
-                const float cby = -(B1z[i] - B1z[im]) * idx;  // (curl B1)_y = -D_x B1z
-                const float cbz = (B1y[i] - B1y[im]) * idx;   // (curl B1)_z =  D_x B1y
-                const float xy = fmaf(-g, Py, cby), xz = fmaf(-g, Pz, cbz);
-                E1y[i] = fmaf(h, xy, fmaf(h, xy, E1y[i]));
-                E1z[i] = fmaf(h, xz, fmaf(h, xz, E1z[i]));
-                const float cb = -(B0[i] - B0[im]) * idx;
-                E0[i] = fmaf(h, cb, E0[i]);
+            // 3. axion current and the E updates: needs MID at i +- 1 and B at i - 1
+            {
+                const float lmid = tl >= 0 ? lMID[tl] : MID[0], rmid = tr >= 0 ? fMID[tr] : pick(MID, jl);
+                float pB0 = tl >= 0 ? lB0[tl] : B0[0];
+                float pB1z = tl >= 0 ? lB1z[tl] : B1z[0];
+                float pB1y = tl >= 0 ? lB1y[tl] : B1y[0];
+#pragma unroll
+                for (int j = 0; j < kK; j++) {
+                    const float midp = j + 1 < cnt ? MID[j + 1] : rmid;
+                    const float midm = j > 0 ? MID[j - 1] : lmid;
+                    const float Dt = PI[j] * inv_dt;
+                    const float Py = Dt * By;
+                    const float bz = 0.5f * (B0[j] + pB0) + Bz;
+                    const float Pz = fmaf(E0[j], (midp - midm) * hidx, Dt * bz);
+                    const float cby = -(B1z[j] - pB1z) * idx;  // (curl B1)_y = -D_x B1z
+                    const float cbz = (B1y[j] - pB1y) * idx;   // (curl B1)_z =  D_x B1y
+                    const float xy = fmaf(-g, Py, cby), xz = fmaf(-g, Pz, cbz);
+                    E1y[j] = fmaf(h, xy, fmaf(h, xy, E1y[j]));
+                    E1z[j] = fmaf(h, xz, fmaf(h, xz, E1z[j]));
+                    const float cb = -(B0[j] - pB0) * idx;
+                    E0[j] = fmaf(h, cb, E0[j]);
+                    pB0 = B0[j];
+                    pB1z = B1z[j];
+                    pB1y = B1y[j];
+                }
+#pragma unroll
+                for (int j = 0; j < kK; j++) PH[j] += PI[j];  // phi^{n+3/2} = phi^{n+1/2} + pi^{n+1}
+                fE0[t] = E0[0];
+                fE1y[t] = E1y[0];
+                fE1z[t] = E1z[0];
+                fPH[pb ^ 1][t] = PH[0];
+                lPH[pb ^ 1][t] = pick(PH, jl);
             }
-            float *t = phi;
-            phi = phin;
-            phin = t;
             __syncthreads();
         }
         // write the valid core cells to the other buffer
-        const int lo = I.whole ? 0 : H, cnt = I.whole ? nx : I.len;
-        for (int i = threadIdx.x; i < cnt; i += nt) {
-            const int gx = I.whole ? i : I.x0 + i;
-            const int j = lo + i;
-            const int64_t o = S.off + gx;
-            arr(D, out, 0, o)[0] = E0[j];
-            arr(D, out, 1, o)[0] = B0[j];
-            arr(D, out, 2, o)[0] = E1y[j];
-            arr(D, out, 3, o)[0] = E1z[j];
-            arr(D, out, 4, o)[0] = B1y[j];
-            arr(D, out, 5, o)[0] = B1z[j];
-            arr(D, out, 6, o)[0] = phi[j];
-            arr(D, out, 7, o)[0] = PI[j];
+#pragma unroll
+        for (int j = 0; j < kK; j++) {
+            const int i = c0 + j;  // local cell
+            const int lo = wrapc ? 0 : H, hi = wrapc ? nx : H + I.len;
+            if (j < cnt && i >= lo && i < hi) {
+                const int gx = wrapc ? i : I.x0 + (i - H);
+                const int64_t o = S.off + gx;
+                arr(D, out, 0, o)[0] = E0[j];
+                arr(D, out, 1, o)[0] = B0[j];
+                arr(D, out, 2, o)[0] = E1y[j];
+                arr(D, out, 3, o)[0] = E1z[j];
+                arr(D, out, 4, o)[0] = B1y[j];
+                arr(D, out, 5, o)[0] = B1z[j];
+                arr(D, out, 6, o)[0] = PH[j];
+                arr(D, out, 7, o)[0] = PI[j];
+            }
         }
         __syncthreads();
     }
@@ -385,7 +456,7 @@ axp_status axp_batch_create(int32_t max_instances, int64_t max_cells, void *dev_
     b->free.push_back({0, max_cells});
     b->dirty = true;
     b->block_steps = 32;
-    b->segment_cells = 4096;
+    b->segment_cells = 3584;
     b->threads = 512;
     b->use_graph = false;
     b->graph = nullptr;
@@ -395,7 +466,6 @@ axp_status axp_batch_create(int32_t max_instances, int64_t max_cells, void *dev_
     b->sms = 152;
     cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
     cudaError_t e = cudaMemsetAsync(b->ws + L.slots, 0, L.total - L.slots, b->stream);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_batch_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) {
         delete b;
@@ -512,7 +582,7 @@ axp_status axp_batch_remove(axp_batch *b, int32_t slot)
 
 static axp_status rebuild_items(axp_batch *b)
 {
-    const int cap = kCapCells;
+    const int cap = kK * b->threads;  // cells a work item holds
     const int halo = 3 * b->block_steps;
     int seg = b->segment_cells;
     if (seg + 2 * halo > cap) seg = cap - 2 * halo;
@@ -542,11 +612,13 @@ static axp_status rebuild_items(axp_batch *b)
 static cudaError_t enqueue_run(axp_batch *b, int64_t nsteps)
 {
     const int halo = 3;  // cells of halo per step on each side of a segment
-    const size_t smem = (size_t)kCapCells * kSmemArr * sizeof(float);
-    const int grid = std::min<int>(b->sms, std::max<int>(1, b->D.nitems));
+    int occ = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_block, b->threads, 0) != cudaSuccess || occ < 1)
+        occ = 1;
+    const int grid = std::min<int>(b->sms * occ, std::max<int>(1, b->D.nitems));
     for (int64_t done = 0; done < nsteps; done += b->block_steps) {
         const int budget = (int)std::min<int64_t>(b->block_steps, nsteps - done);
-        k_batch_block<<<grid, b->threads, smem, b->stream>>>(b->D, budget, halo);
+        k_batch_block<<<grid, b->threads, 0, b->stream>>>(b->D, budget, halo);
         k_batch_account<<<(b->max_instances + 255) / 256, 256, 0, b->stream>>>(b->D, b->max_instances, budget);
         b->launches += 2;
         const cudaError_t e = cudaGetLastError();
@@ -653,8 +725,9 @@ axp_status axp_batch_read_state(axp_batch *b, int32_t slot, int32_t which, doubl
 
 axp_status axp_batch_set_tiling(axp_batch *b, int32_t block_steps, int32_t segment_cells, int32_t threads)
 {
-    if (!b || block_steps < 1 || block_steps > 256 || threads < 64 || threads > 1024 || threads % 32) return AXP_E_INVAL;
-    if (segment_cells < 64 || segment_cells + 6 * block_steps > kCapCells) return AXP_E_INVAL;
+    if (!b || block_steps < 1 || block_steps > 256 || threads < 64 || threads > kMaxThreads || threads % 32)
+        return AXP_E_INVAL;
+    if (segment_cells < 64 || segment_cells + 6 * block_steps > kK * threads) return AXP_E_INVAL;
     b->block_steps = block_steps;
     b->segment_cells = segment_cells;
     b->threads = threads;

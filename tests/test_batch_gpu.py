@@ -53,7 +53,7 @@ def test_batch_matches_oracle_with_segmented_instances():
     steps = 120
     insts = [inst(steps=steps, **d) for d in INSTANCES]
     b = B.Batch(8, sum(int(i.nx) for i in insts) + 100)
-    b.set_tiling(32, 2048, 256)  # 6400 and 9000 run as segments with halos
+    b.set_tiling(32, 1536, 256)  # 6400 and 9000 run as segments with halos
     slots = [b.add(i) for i in insts]
     b.run(steps)
     assert list(b.progress()[slots]) == [steps] * len(slots)
@@ -79,7 +79,7 @@ def test_batch_instance_is_identical_alone_and_in_the_mix():
     x = inst(nx=9000, m=0.3, g=1e-2, By=1.0, Bz=0.1, steps=200)
     alone = B.Batch(1, 9000)
     sa = alone.add(x)
-    alone.set_tiling(16, 4096, 512)
+    alone.set_tiling(16, 3584, 512)
     alone.run(200)
     mix = B.Batch(6, 40000)
     others = [inst(nx=n, m=0.1 * j, g=1e-3, By=2.0, Bz=0.0, steps=150 + 10 * j) for j, n in enumerate((100, 3000, 7000, 12000))]
@@ -88,7 +88,7 @@ def test_batch_instance_is_identical_alone_and_in_the_mix():
     sm = mix.add(x)
     for o in others[2:]:
         mix.add(o)
-    mix.set_tiling(64, 2048, 1024)
+    mix.set_tiling(64, 1536, 256)
     mix.run(200)
     for which in range(8):
         assert np.array_equal(alone.read_state(sa, which), mix.read_state(sm, which)), which
