@@ -28,6 +28,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "axp_internal.h"
@@ -149,86 +150,96 @@ __global__ void __launch_bounds__(kMaxThreads) k_batch_block(Dev D, int budget, 
         __syncthreads();
         const float h = S.h, idx = S.idx, hidx = S.hidx, cx = S.cx, c0m = S.c0, dt2g = S.dt2g, inv_dt = S.inv_dt;
         const float g = S.g, By = S.By, Bz = S.Bz;
+        const float hx = h * idx, h2x = 2.0f * hx, h2g = 2.0f * h * g;  // folded step constants
+        // The stage bodies, for a thread holding K cells (F: the run is full, so
+        // the tests on the run's length are known at compile time) or fewer.
+        auto stage1 = [&](auto fullc) {  // B^{n+1}: needs E at i + 1
+            constexpr bool F = decltype(fullc)::value;
+            const int cn = F ? kK : cnt, jlast = F ? kK - 1 : jl;
+            const float rE0 = tr >= 0 ? fE0[tr] : pick(E0, jlast), rE1y = tr >= 0 ? fE1y[tr] : pick(E1y, jlast);
+            const float rE1z = tr >= 0 ? fE1z[tr] : pick(E1z, jlast);
+#pragma unroll
+            for (int j = 0; j < kK; j++) {
+                const float e0p = j + 1 < cn ? E0[j + 1] : rE0;
+                const float e1zp = j + 1 < cn ? E1z[j + 1] : rE1z;
+                const float e1yp = j + 1 < cn ? E1y[j + 1] : rE1y;
+                // B^{n+1} = B^n - 2h curl E^{n+1/2}, one multiply-add per difference:
+                // (curl E0)_z = D_x E0y, (curl E1)_y = -D_x E1z, (curl E1)_z = D_x E1y
+                B0[j] = fmaf(-h2x, e0p - E0[j], B0[j]);
+                B1y[j] = fmaf(h2x, e1zp - E1z[j], B1y[j]);
+                B1z[j] = fmaf(-h2x, e1yp - E1y[j], B1z[j]);
+            }
+            lB0[t] = pick(B0, jlast);
+            lB1y[t] = pick(B1y, jlast);
+            lB1z[t] = pick(B1z, jlast);
+        };
+        auto stage2 = [&](auto fullc, int pb) {  // axion; E0y^{n+1}: needs phi at i +- 1, B0 at i - 1
+            constexpr bool F = decltype(fullc)::value;
+            const int cn = F ? kK : cnt, jlast = F ? kK - 1 : jl;
+            const float lph = tl >= 0 ? lPH[pb][tl] : PH[0], rph = tr >= 0 ? fPH[pb][tr] : pick(PH, jlast);
+            float prevB0 = tl >= 0 ? lB0[tl] : B0[0];
+#pragma unroll
+            for (int j = 0; j < kK; j++) {
+                const float php = j + 1 < cn ? PH[j + 1] : rph;
+                const float phm = j > 0 ? PH[j - 1] : lph;
+                const float Sg = E0[j] * By;  // Ebar0 . Bbar0 / g: E0y with the background along y
+                const float ph = PH[j];
+                // second difference from neighbour differences and the mass term kept
+                // apart (c0 = -(m dt)^2), so neither rounds against 2*phi
+                const float pin = fmaf(dt2g, Sg, fmaf(cx, (php - ph) + (phm - ph), fmaf(c0m, ph, PI[j])));
+                PI[j] = pin;
+                MID[j] = fmaf(0.5f, pin, ph);
+                E0[j] = fmaf(-hx, B0[j] - prevB0, E0[j]);  // + h (curl B0)_y, (curl B0)_y = -D_x B0z
+                prevB0 = B0[j];
+            }
+            fMID[t] = MID[0];
+            lMID[t] = pick(MID, jlast);
+        };
+        auto stage3 = [&](auto fullc, int pb) {  // current and E updates: MID at i +- 1, B at i - 1
+            constexpr bool F = decltype(fullc)::value;
+            const int cn = F ? kK : cnt, jlast = F ? kK - 1 : jl;
+            const float lmid = tl >= 0 ? lMID[tl] : MID[0], rmid = tr >= 0 ? fMID[tr] : pick(MID, jlast);
+            float pB0 = tl >= 0 ? lB0[tl] : B0[0];
+            float pB1z = tl >= 0 ? lB1z[tl] : B1z[0];
+            float pB1y = tl >= 0 ? lB1y[tl] : B1y[0];
+#pragma unroll
+            for (int j = 0; j < kK; j++) {
+                const float midp = j + 1 < cn ? MID[j + 1] : rmid;
+                const float midm = j > 0 ? MID[j - 1] : lmid;
+                const float Dt = PI[j] * inv_dt;
+                const float Py = Dt * By;
+                const float bz = 0.5f * (B0[j] + pB0) + Bz;
+                const float Pz = fmaf(E0[j], (midp - midm) * hidx, Dt * bz);
+                // E1^{n+3/2} = E1^{n+1/2} + 2h (curl B1 - g J), (curl B1)_y = -D_x B1z,
+                // (curl B1)_z = D_x B1y; E0y^{n+3/2} = E0y^{n+1} + h (curl B0)_y
+                E1y[j] = fmaf(-h2x, B1z[j] - pB1z, fmaf(-h2g, Py, E1y[j]));
+                E1z[j] = fmaf(h2x, B1y[j] - pB1y, fmaf(-h2g, Pz, E1z[j]));
+                E0[j] = fmaf(-hx, B0[j] - pB0, E0[j]);
+                pB0 = B0[j];
+                pB1z = B1z[j];
+                pB1y = B1y[j];
+            }
+#pragma unroll
+            for (int j = 0; j < kK; j++) PH[j] += PI[j];  // phi^{n+3/2} = phi^{n+1/2} + pi^{n+1}
+            fE0[t] = E0[0];
+            fE1y[t] = E1y[0];
+            fE1z[t] = E1z[0];
+            fPH[pb ^ 1][t] = PH[0];
+            lPH[pb ^ 1][t] = pick(PH, jlast);
+        };
+        const bool full = cnt == kK;
+        using Full = std::integral_constant<bool, true>;
+        using Part = std::integral_constant<bool, false>;
         for (int st = 0; st < T; st++) {
             const int pb = st & 1;
-            // 1. B^{n+1}: needs E at i + 1
-            {
-                const float rE0 = tr >= 0 ? fE0[tr] : pick(E0, jl), rE1y = tr >= 0 ? fE1y[tr] : pick(E1y, jl);
-                const float rE1z = tr >= 0 ? fE1z[tr] : pick(E1z, jl);
-#pragma unroll
-                for (int j = 0; j < kK; j++) {
-                    const float e0p = j + 1 < cnt ? E0[j + 1] : rE0;
-                    const float e1zp = j + 1 < cnt ? E1z[j + 1] : rE1z;
-                    const float e1yp = j + 1 < cnt ? E1y[j + 1] : rE1y;
-                    const float c0z = (e0p - E0[j]) * idx;    // (curl E0)_z = D_x E0y
-                    const float c1y = -(e1zp - E1z[j]) * idx;  // (curl E1)_y = -D_x E1z
-                    const float c1z = (e1yp - E1y[j]) * idx;   // (curl E1)_z = D_x E1y
-                    B0[j] = fmaf(-h, c0z, fmaf(-h, c0z, B0[j]));
-                    B1y[j] = fmaf(-h, c1y, fmaf(-h, c1y, B1y[j]));
-                    B1z[j] = fmaf(-h, c1z, fmaf(-h, c1z, B1z[j]));
-                }
-                lB0[t] = pick(B0, jl);
-                lB1y[t] = pick(B1y, jl);
-                lB1z[t] = pick(B1z, jl);
-            }
+            if (full) stage1(Full{});
+            else stage1(Part{});
             __syncthreads();
-            // 2. axion; E0y^{n+1}: needs phi at i +- 1 and B0 at i - 1
-            {
-                const float lph = tl >= 0 ? lPH[pb][tl] : PH[0], rph = tr >= 0 ? fPH[pb][tr] : pick(PH, jl);
-                const float lb0 = tl >= 0 ? lB0[tl] : B0[0];
-                float prevB0 = lb0;
-#pragma unroll
-                for (int j = 0; j < kK; j++) {
-                    const float php = j + 1 < cnt ? PH[j + 1] : rph;
-                    const float phm = j > 0 ? PH[j - 1] : lph;
-                    const float Sg = E0[j] * By;  // Ebar0 . Bbar0 / g: E0y with the background along y
-                    const float ph = PH[j];
-                    // second difference from neighbour differences and the mass term kept
-                    // apart (c0 = -(m dt)^2), so neither rounds against 2*phi
-                    const float pin = fmaf(dt2g, Sg, fmaf(cx, (php - ph) + (phm - ph), fmaf(c0m, ph, PI[j])));
-                    PI[j] = pin;
-                    MID[j] = fmaf(0.5f, pin, ph);
-                    const float cb = -(B0[j] - prevB0) * idx;  // (curl B0)_y = -D_x B0z
-                    prevB0 = B0[j];
-                    E0[j] = fmaf(h, cb, E0[j]);
-                }
-                fMID[t] = MID[0];
-                lMID[t] = pick(MID, jl);
-            }
+            if (full) stage2(Full{}, pb);
+            else stage2(Part{}, pb);
             __syncthreads();
-            // 3. axion current and the E updates: needs MID at i +- 1 and B at i - 1
-            {
-                const float lmid = tl >= 0 ? lMID[tl] : MID[0], rmid = tr >= 0 ? fMID[tr] : pick(MID, jl);
-                float pB0 = tl >= 0 ? lB0[tl] : B0[0];
-                float pB1z = tl >= 0 ? lB1z[tl] : B1z[0];
-                float pB1y = tl >= 0 ? lB1y[tl] : B1y[0];
-#pragma unroll
-                for (int j = 0; j < kK; j++) {
-                    const float midp = j + 1 < cnt ? MID[j + 1] : rmid;
-                    const float midm = j > 0 ? MID[j - 1] : lmid;
-                    const float Dt = PI[j] * inv_dt;
-                    const float Py = Dt * By;
-                    const float bz = 0.5f * (B0[j] + pB0) + Bz;
-                    const float Pz = fmaf(E0[j], (midp - midm) * hidx, Dt * bz);
-                    const float cby = -(B1z[j] - pB1z) * idx;  // (curl B1)_y = -D_x B1z
-                    const float cbz = (B1y[j] - pB1y) * idx;   // (curl B1)_z =  D_x B1y
-                    const float xy = fmaf(-g, Py, cby), xz = fmaf(-g, Pz, cbz);
-                    E1y[j] = fmaf(h, xy, fmaf(h, xy, E1y[j]));
-                    E1z[j] = fmaf(h, xz, fmaf(h, xz, E1z[j]));
-                    const float cb = -(B0[j] - pB0) * idx;
-                    E0[j] = fmaf(h, cb, E0[j]);
-                    pB0 = B0[j];
-                    pB1z = B1z[j];
-                    pB1y = B1y[j];
-                }
-#pragma unroll
-                for (int j = 0; j < kK; j++) PH[j] += PI[j];  // phi^{n+3/2} = phi^{n+1/2} + pi^{n+1}
-                fE0[t] = E0[0];
-                fE1y[t] = E1y[0];
-                fE1z[t] = E1z[0];
-                fPH[pb ^ 1][t] = PH[0];
-                lPH[pb ^ 1][t] = pick(PH, jl);
-            }
+            if (full) stage3(Full{}, pb);
+            else stage3(Part{}, pb);
             __syncthreads();
         }
         // write the valid core cells to the other buffer
