@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-bc", action="store_true")
     ap.add_argument("--no-window", action="store_true")
+    ap.add_argument("--scan-tiling", default=None,
+                    help="block_steps,segment_cells,threads for the scan instead of the autotuner's choice")
     ap.add_argument("--serve-requests", type=int, default=120)
     ap.add_argument("--n3d", type=int, default=512, help="edge of the 3D axion box")
     return ap.parse_args()
@@ -430,7 +432,7 @@ def window_measurement(steps=400, shifts=(16, 64)):
     return out
 
 
-def scan_measurement(rank, world, fp64_sample=6):
+def scan_measurement(rank, world, fp64_sample=6, tiling=None):
     """The batched parameter scan: 512 seeded 1D instances (Nx log-uniform in
     [1024, 65536], m/omega0 in [1e-3, 2], g in [1e-6, 1e-3], B0 in [0.1, 10],
     5000-40000 steps), FP32 split, one persistent kernel per block of steps,
@@ -446,7 +448,7 @@ def scan_measurement(rank, world, fp64_sample=6):
 
     insts = W.shard(W.scan_instances(), rank, world)
     cu = sum(i.nx * i.steps for i in insts)
-    res, el, tiling = B.run_scan([B.scan_instance(i) for i in insts])
+    res, el, tiling = B.run_scan([B.scan_instance(i) for i in insts], tiling=tiling)
     el = max_over_ranks(el, world)
     every = W.scan_instances()
     cu_all = sum(i.nx * i.steps for i in every)
@@ -598,7 +600,8 @@ def gpu_arm(args):
 
     scan = None
     if not args.no_scan:
-        scan = scan_measurement(rank, world)
+        tl = tuple(int(x) for x in args.scan_tiling.split(",")) if args.scan_tiling else None
+        scan = scan_measurement(rank, world, tiling=tl)
     srv = None
     if not args.no_serve:
         srv = serve_measurement(args.serve_requests, rank, world)

@@ -16,7 +16,7 @@ import threading
 
 import numpy as np
 
-from paper_2406_16796_gb300.workloads import BC_CODE, FIELD_NAMES, AxionSpec, GridSpec, LaserSpec
+from paper_2406_16796_gb300.workloads import BC_CODE, FIELD_NAMES, AxionSpec, GridSpec, LaserSpec, SourceSpec
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "axp_oracle.c")
@@ -68,6 +68,12 @@ class _Axion(C.Structure):
                 ("waist", C.c_double), ("length", C.c_double), ("speed", C.c_double), ("phase", C.c_double)]
 
 
+class _Source(C.Structure):
+    _fields_ = [("amplitude", C.c_double), ("k", C.c_double), ("pol", C.c_double * 3), ("centre", C.c_double * 3),
+                ("waist", C.c_double), ("duration", C.c_double), ("t_centre", C.c_double), ("phase", C.c_double),
+                ("plane", C.c_int64)]
+
+
 class _Diag(C.Structure):
     _fields_ = [(n, C.c_double) for n in ("t", "H_phi", "H_g0", "H_g1", "P_g2a", "P_a2g", "W", "sum_xB1z2",
                                           "sum_B1z2", "gauss_l2")]
@@ -80,6 +86,7 @@ def lib():
         L = C.CDLL(LIB)
         L.orc_validate.argtypes = [C.POINTER(_Params)]
         L.orc_step.argtypes = [C.POINTER(_Params), C.POINTER(_State), C.c_int64]
+        L.orc_step_src.argtypes = [C.POINTER(_Params), C.POINTER(_State), C.POINTER(_Source), C.c_int64]
         L.orc_current.argtypes = [C.POINTER(_Params), C.POINTER(_State), _DP * 3]
         L.orc_source_now.argtypes = [C.POINTER(_Params), C.POINTER(_State), _DP]
         L.orc_gauss_residual.argtypes = [C.POINTER(_Params), C.POINTER(_State), _DP]
@@ -141,6 +148,7 @@ class OracleGrid:
                 if grid.axion_bc[a][s] == "outflow":
                     self.ghost[a][s] = [np.zeros(plane_shape(grid, a)), np.zeros(plane_shape(grid, a))]
         self.step_count = 0
+        self.src = None  # soft source (_Source) or None
 
     # -- state marshalling --
     def _state(self) -> _State:
@@ -178,8 +186,20 @@ class OracleGrid:
     # -- method --
     def step(self, n: int = 1):
         st = self._state()
-        lib().orc_step(C.byref(self.p), C.byref(st), int(n))
+        src = C.byref(self.src) if self.src is not None else None
+        lib().orc_step_src(C.byref(self.p), C.byref(st), src, int(n))
         self.step_count = st.step
+
+    def set_soft_source(self, S: SourceSpec | None):
+        """Laser entering through an x-plane for the following steps (None: off)."""
+        if S is None:
+            self.src = None
+            return
+        n0 = self.grid.n[0]
+        if not (1 <= S.plane <= n0 - 1) or S.pol[0] != 0 or not S.k > 0:
+            raise ValueError("invalid soft source")
+        self.src = _Source(S.amplitude, S.k, (C.c_double * 3)(*S.pol), (C.c_double * 3)(*S.centre), S.waist,
+                           S.duration, S.t_centre, S.phase, int(S.plane))
 
     def current(self):
         """J^n (without g) at the E locations, shape (3, nz, ny, nx)."""

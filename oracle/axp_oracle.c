@@ -33,6 +33,9 @@
  *  - PML (Sec. 2.4 item 4): sigma = (1 - i/N)^3 sigma_max with i = 0 at the
  *    outermost cell; at corners the largest sigma of the axes; outside the
  *    layer the ghost is 0.
+ *  - A laser "injected" into the box (Sec. 3.2) may enter through an x-plane
+ *    as an electric and a magnetic current sheet on the plane, which launch
+ *    the incident wave towards +x only (orc_step_src).
  */
 #include "axp_oracle.h"
 
@@ -308,7 +311,70 @@ static double half_update(double F, double X, double sig, double h)
     return ((1.0 - sig * h / 2.0) * F + h * X) / (1.0 + sig * h / 2.0);
 }
 
-static void e_half(const orc_params *p, double *E[3], double *const B[3], double *const J[3], double coef_g)
+/* ---- soft source (laser entering through an x-plane) ---- */
+
+static void position(const orc_params *p, int kind, int a, int64_t i, int64_t j, int64_t k, double x[3]);
+
+/* Time-dependent factor of the incident wave at lab position x, time t:
+ * env(t - t_c - (x - x_c)) cos(k (x - x_c) - w (t - t_c) + phase). */
+static double src_wave(const orc_params *p, const orc_source *q, double x, double t)
+{
+    double w = (2.0 / p->dt) * asin((p->dt / p->d[0]) * sin(q->k * p->d[0] / 2.0));
+    double e = 1.0;
+    if (q->duration > 0) {
+        double L = q->duration / sqrt(2.0 * log(2.0));
+        double u = (t - q->t_centre) - (x - q->centre[0]);
+        e = exp(-(u * u) / (L * L));
+    }
+    return e * cos(q->k * (x - q->centre[0]) - w * (t - q->t_centre) + q->phase);
+}
+
+/* Sheet weight of polarisation component a (1 = y, 2 = z) at transverse cell
+ * (j, k): A pol_a f / dx at the E_a location of cell (plane, j, k); its B
+ * partner on the sheet (B_z for E_y, B_y for E_z) has the same y and z.  Zero
+ * where either cell next to the sheet lies in an absorbing layer. */
+static double src_weight(const orc_params *p, const orc_source *q, int a, int64_t j, int64_t k)
+{
+    if (orc_sigma_cell(p, q->plane, j, k, 0) != 0.0 || orc_sigma_cell(p, q->plane - 1, j, k, 0) != 0.0) return 0.0;
+    double f = 1.0;
+    if (q->waist > 0) {
+        double x[3];
+        position(p, 1, a, q->plane, j, k, x);
+        double r2 = 0.0;
+        if (p->n[1] > 1) r2 = r2 + (x[1] - q->centre[1]) * (x[1] - q->centre[1]);
+        if (p->n[2] > 1) r2 = r2 + (x[2] - q->centre[2]) * (x[2] - q->centre[2]);
+        f = exp(-r2 / (q->waist * q->waist));
+    }
+    return ((q->amplitude * q->pol[a]) * f) / p->d[0];
+}
+
+/* Electric sheet, in the E update of cell (plane, j, k) at time t: the update
+ * of E_y uses B_z of the face on the plane, which lies on the incident-free
+ * side, so the incident B_z/dx is added to its curl; likewise E_z takes
+ * -B_y,inc/dx.  With B_inc = xhat x E_inc both terms are +A pol f tau/dx, tau
+ * the wave factor at the face (x = x_p). */
+static double src_e_term(const orc_params *p, const orc_source *q, int a, int64_t i, int64_t j, int64_t k, double t)
+{
+    if (!q || i != q->plane || a == 0) return 0.0;
+    double xp = p->lo[0] + (double)q->plane * p->d[0];
+    return src_weight(p, q, a, j, k) * src_wave(p, q, xp, t);
+}
+
+/* Magnetic sheet, in the B update of the face (plane-1, j, k) at time t: the
+ * curl there reads E of cell `plane`, on the incident side, so the incident
+ * part is taken out: B_y gets -E_z,inc/dx, B_z gets +E_y,inc/dx, with the
+ * wave factor at the E cells (x = x_p + dx/2). */
+static double src_b_term(const orc_params *p, const orc_source *q, int a, int64_t i, int64_t j, int64_t k, double t)
+{
+    if (!q || i != q->plane - 1 || a == 0) return 0.0;
+    double xe = p->lo[0] + ((double)q->plane + 0.5) * p->d[0];
+    double tau = src_wave(p, q, xe, t);
+    if (a == 1) return -(src_weight(p, q, 2, j, k) * tau);
+    return src_weight(p, q, 1, j, k) * tau;
+}
+
+static void e_half(const orc_params *p, double *E[3], double *const B[3], double *const J[3], double coef_g,
+                   const orc_source *src, double t)
 {
     const double h = p->dt / 2.0;
     for (int a = 0; a < 3; a++) {
@@ -317,19 +383,22 @@ static void e_half(const orc_params *p, double *E[3], double *const B[3], double
             CELL_IJK(c);
             double X = curlB(p, B, a, i, j, k);
             if (J) X = X - coef_g * J[a][c];
+            if (src && i == src->plane) X = X + src_e_term(p, src, a, i, j, k, t);
             E[a][c] = half_update(E[a][c], X, orc_sigma_cell(p, i, j, k, 0), h);
         }
     }
 }
 
-static void b_half(const orc_params *p, double *B[3], double *const E[3])
+static void b_half(const orc_params *p, double *B[3], double *const E[3], const orc_source *src, double t)
 {
     const double h = p->dt / 2.0;
     for (int a = 0; a < 3; a++) {
 #pragma omp parallel for schedule(static)
         for (int64_t c = 0; c < ncells(p); c++) {
             CELL_IJK(c);
-            B[a][c] = half_update(B[a][c], -curlE(p, E, a, i, j, k), orc_sigma_cell(p, i, j, k, 0), h);
+            double X = -curlE(p, E, a, i, j, k);
+            if (src && i == src->plane - 1) X = X + src_b_term(p, src, a, i, j, k, t);
+            B[a][c] = half_update(B[a][c], X, orc_sigma_cell(p, i, j, k, 0), h);
         }
     }
 }
@@ -351,9 +420,12 @@ void orc_outflow_solve(double dt, double dxa, double m, double g_cur, double g_o
     *U_out = U;
 }
 
-void orc_step(const orc_params *p, orc_state *s, int64_t nsteps)
+void orc_step(const orc_params *p, orc_state *s, int64_t nsteps) { orc_step_src(p, s, NULL, nsteps); }
+
+void orc_step_src(const orc_params *p, orc_state *s, const orc_source *src, int64_t nsteps)
 {
     if (orc_validate(p)) die("invalid parameters");
+    if (src && (src->plane < 1 || src->plane > p->n[0] - 1 || src->pol[0] != 0.0)) die("invalid soft source");
     const int64_t N = ncells(p);
     double *J[3], *S = malloc(sizeof(double) * N), *phi_new = malloc(sizeof(double) * N);
     for (int a = 0; a < 3; a++) J[a] = malloc(sizeof(double) * N);
@@ -378,11 +450,15 @@ void orc_step(const orc_params *p, orc_state *s, int64_t nsteps)
         phi_pair qn = make_pair(s->phi_cur, s->phi_old, Gcur, Gold);
         current_into(p, &qn, s->E0, s->B0, J);
 
+        /* source times: the E half-steps read B at t_n and t_{n+1}, the B half-steps E at t_{n+1/2} */
+        const double t_n = (double)s->step * dt, t_h = ((double)s->step + 0.5) * dt;
+        const double t_n1 = (double)(s->step + 1) * dt;
+
         /* 2.-5. first half-steps, order 0 before order 1 (Eq. update_E and the B1 half-step) */
-        e_half(p, s->E0, s->B0, NULL, 0.0);
-        e_half(p, s->E1, s->B1, J, p->g);
-        b_half(p, s->B0, s->E0);
-        b_half(p, s->B1, s->E1);
+        e_half(p, s->E0, s->B0, NULL, 0.0, src, t_n);
+        e_half(p, s->E1, s->B1, J, p->g, NULL, 0.0);
+        b_half(p, s->B0, s->E0, src, t_h);
+        b_half(p, s->B1, s->E1, NULL, 0.0);
 
         /* 8.-9. source S^{n+1/2} and the axion leapfrog (Eq. update_axion), PML form in the layer */
 #pragma omp parallel for schedule(static)
@@ -429,14 +505,14 @@ void orc_step(const orc_params *p, orc_state *s, int64_t nsteps)
             }
 
         /* 10.-12. second half-steps of B (both orders) and of E0 */
-        b_half(p, s->B0, s->E0);
-        b_half(p, s->B1, s->E1);
-        e_half(p, s->E0, s->B0, NULL, 0.0);
+        b_half(p, s->B0, s->E0, src, t_h);
+        b_half(p, s->B1, s->E1, NULL, 0.0);
+        e_half(p, s->E0, s->B0, NULL, 0.0, src, t_n1);
 
         /* 13.-14. J^{n+1} from phi^{n+3/2}, phi^{n+1/2}, E0^{n+1}, B0^{n+1}; second E1 half-step */
         phi_pair qn1 = make_pair(phi_new, s->phi_cur, Gnew, Gcur);
         current_into(p, &qn1, s->E0, s->B0, J);
-        e_half(p, s->E1, s->B1, J, p->g);
+        e_half(p, s->E1, s->B1, J, p->g, NULL, 0.0);
 
         /* 17. rotate the axion levels: old <- cur, cur <- new (copies keep the caller's buffers) */
         memcpy(s->phi_old, s->phi_cur, sizeof(double) * N);

@@ -83,8 +83,36 @@ typedef struct {
     double gauss_l2;                 /* sum over cells of R^2 dV, R = div E1 + g Bbar0 . grad_c phi */
 } orc_diag;
 
+/* Laser entering through a fixed x-plane (Sec. 3.2 injects the laser into the
+ * box), as a pair of current sheets on the plane x_p = lo[0] + plane d[0]: an
+ * electric sheet on the E cells at index `plane` and a magnetic sheet on the B
+ * faces at index plane-1 (the faces on x_p).  Together they launch the incident
+ * wave towards +x only (a Huygens source: cells below the plane see the
+ * incident wave removed, cells from `plane` on see it added).  Incident wave,
+ * lab coordinates, t = step dt:
+ *   E_inc = A pol f(y, z) env(t - t_c - (x - x_c)) cos(k (x - x_c) - w (t - t_c) + phase),
+ *   B_inc = xhat x E_inc,
+ * w from the Yee dispersion along x, sin(w dt/2)/dt = sin(k dx/2)/dx, so that a
+ * CW wave is an exact discrete plane wave; f = exp(-r^2/waist^2) over the
+ * active transverse axes (1 for waist = 0); env = exp(-u^2/L^2) with
+ * L = duration/sqrt(2 ln 2) (1 for duration = 0).  The sheets stop where a
+ * transverse absorbing layer begins. */
+typedef struct {
+    double amplitude;
+    double k;            /* carrier wave number along +x, > 0 */
+    double pol[3];       /* unit E polarisation, pol[0] = 0 */
+    double centre[3];    /* x_c (envelope centre at t_c); y_c, z_c (beam axis) */
+    double waist;
+    double duration;     /* intensity FWHM in time (c = 1) */
+    double t_centre;
+    double phase;
+    int64_t plane;       /* first cell on the +x side of the sheet, 1 <= plane <= n[0]-1 */
+} orc_source;
+
 int orc_validate(const orc_params *p);
 void orc_step(const orc_params *p, orc_state *s, int64_t nsteps);
+/* orc_step with a soft source (src may be NULL) */
+void orc_step_src(const orc_params *p, orc_state *s, const orc_source *src, int64_t nsteps);
 void orc_current(const orc_params *p, const orc_state *s, double *J[3]);
 void orc_source_now(const orc_params *p, const orc_state *s, double *S);
 void orc_gauss_residual(const orc_params *p, const orc_state *s, double *R);

@@ -190,10 +190,11 @@ class Batch:
         return best, times
 
 
-def run_scan(instances, max_cells=None, tune=True, chunk_steps=1024, graphs=True):
+def run_scan(instances, max_cells=None, tune=True, chunk_steps=1024, graphs=True, tiling=None):
     """Admit every instance, run them all to completion, return (results per instance
     index, wall seconds from the first admission to the last result, tiling).  The
-    autotuner's probe steps are real steps and are inside the timing."""
+    autotuner's probe steps are real steps and are inside the timing.  A given
+    `tiling` (block_steps, segment_cells, threads) is used as it is, untuned."""
     import torch
 
     total = sum(i.nx for i in instances)
@@ -201,8 +202,9 @@ def run_scan(instances, max_cells=None, tune=True, chunk_steps=1024, graphs=True
     t0 = time.perf_counter()
     b = Batch(len(instances), max_cells or total, graphs=graphs)
     slots = [b.add(i) for i in instances]
-    tiling = None
-    if tune:
+    if tiling is not None:
+        b.set_tiling(*tiling)
+    elif tune:
         tiling, _ = b.autotune()
     while True:
         done = b.progress()

@@ -73,6 +73,22 @@ class LaserSpec:
 
 
 @dataclass
+class SourceSpec:
+    """A laser entering through the x-plane lo + plane*dx (a soft source): E =
+    amplitude pol f(y, z) env(t - t_centre - (x - centre[0])) cos(k (x - centre[0])
+    - w (t - t_centre) + phase), moving towards +x."""
+    amplitude: float
+    k: float
+    pol: Tuple[float, float, float]
+    plane: int
+    centre: Tuple[float, float, float] = (0.0, 0.0, 0.0)
+    waist: float = 0.0  # transverse 1/e field radius, 0 = plane
+    duration: float = 0.0  # intensity FWHM in time, 0 = CW
+    t_centre: float = 0.0
+    phase: float = 0.0
+
+
+@dataclass
 class AxionSpec:
     amplitude: float
     k: Tuple[float, float, float]
