@@ -448,13 +448,14 @@ def scan_measurement(rank, world, fp64_sample=6, tiling=None):
 
     insts = W.shard(W.scan_instances(), rank, world)
     cu = sum(i.nx * i.steps for i in insts)
-    res, el, tiling = B.run_scan([B.scan_instance(i) for i in insts], tiling=tiling)
+    phases = {}
+    res, el, tiling = B.run_scan([B.scan_instance(i) for i in insts], tiling=tiling, phases=phases)
     el = max_over_ranks(el, world)
     every = W.scan_instances()
     cu_all = sum(i.nx * i.steps for i in every)
     out = {"workload": "scan_512x1d", "instances": len(every), "cell_updates": cu_all, "seconds": el,
            "sims_per_s": len(every) / el, "cell_updates_per_s": cu_all / el, "tiling": list(tiling),
-           "graphs": True, "precision": "fp32_split"}
+           "graphs": True, "precision": "fp32_split", "phases_rank0": phases}
     if rank != 0:
         return out
     rng = np.random.default_rng(20240624)

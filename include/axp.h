@@ -178,6 +178,44 @@ axp_status axp_set_background_field(axp_grid *grid, const double B_ext[3], const
 axp_status axp_inject_laser(axp_grid *grid, const axp_laser_desc *laser);
 axp_status axp_inject_axion(axp_grid *grid, const axp_axion_desc *axion);
 
+/* Laser entering through a fixed x-plane (Sec. 3.2: the laser is injected
+ * into the box), as a soft source: an electric current sheet on the E cells
+ * at x index `plane` and a magnetic one on the B faces at index plane-1 (the
+ * faces on the plane x_p = lo + plane d[0]).  Together they launch the
+ * incident wave towards +x only:
+ *   E_inc = A pol f(y, z) env(t - t_centre - (x - centre[0]))
+ *           cos(k (x - centre[0]) - w (t - t_centre) + phase),   B_inc = xhat x E_inc,
+ * with t = step dt, x the lab position (a moving window moves the grid, not
+ * the wave), w from the Yee dispersion along x, sin(w dt/2)/dt =
+ * sin(k dx/2)/dx (a CW wave is then an exact discrete plane wave: nothing
+ * appears behind the plane), f = exp(-r^2/waist^2) over the active
+ * transverse axes around (centre[1], centre[2]) (1 for waist = 0) and env =
+ * exp(-u^2/L^2), L = duration/sqrt(2 ln 2) (1 for duration = 0).  Added to the
+ * order-0 half-steps: E_y, E_z of cell `plane` get +A pol f tau/dx in their
+ * curl (tau the wave factor at x_p, at the time of the B they read); B_y, B_z
+ * on the faces get -A pol_z f tau/dx and +A pol_y f tau/dx (tau at x_p + dx/2,
+ * t_{n+1/2}).  The sheets stop where a transverse absorbing layer begins;
+ * their transverse profile is taken when the source is set.
+ * Requirements: a grid with n[0] >= 2; 1 <= plane <= n[0]-1 with the cells
+ * plane-1 and plane outside the x absorbing layers; pol[0] = 0; k > 0;
+ * finite values; waist, duration >= 0.  Otherwise AXP_E_INVAL, and
+ * AXP_E_STATE for a grid that a group is stepping.  `src` = NULL switches the
+ * source off.  The source is a setting of the handle (like the kernel choice),
+ * not part of the saved state.  Steps with a source run on the general path,
+ * or on the 2D TM kernel when the polarisation is along z. */
+typedef struct {
+    double amplitude;
+    double k;
+    double pol[3];
+    double centre[3];
+    double waist;
+    double duration;
+    double t_centre;
+    double phase;
+    int64_t plane;
+} axp_source_desc;
+axp_status axp_set_soft_source(axp_grid *grid, const axp_source_desc *src);
+
 /* Advance nsteps >= 0 time steps, asynchronously on the grid's stream.  When
  * diag_every > 0, a diagnostic record is appended to the device ring after
  * every step whose new index is a multiple of diag_every (the oldest record
@@ -353,6 +391,11 @@ axp_status axp_batch_progress(axp_batch *batch, int64_t *steps_done, int32_t max
 /* FP64 diagnostics of one slot's present state (same definitions as axp_diag);
  * synchronises. */
 axp_status axp_batch_result(axp_batch *batch, int32_t slot, axp_diag *out);
+/* The same for n slots at once (host array `slots`, n <= max_instances; out[q]
+ * receives slot slots[q]'s record): one launch, one copy, one synchronisation.
+ * Each record is bit-identical to axp_batch_result's.  AXP_E_INVAL if a listed
+ * slot is free, AXP_E_NONFINITE if a record holds NaN/Inf. */
+axp_status axp_batch_results(axp_batch *batch, const int32_t *slots, int32_t n, axp_diag *out);
 
 /* Stored state of one slot as nx doubles: which = 0 E0y, 1 B0z, 2 E1y, 3 E1z,
  * 4 B1y, 5 B1z, 6 phi^{n+1/2}, 7 phi^{n+1/2} - phi^{n-1/2}.  B and phi are at
@@ -398,7 +441,8 @@ axp_status axp_group_create(int32_t max_grids, int32_t max_tiles, void *dev_work
 axp_status axp_group_destroy(axp_group *group);
 /* Join a grid that will run `steps` more steps; *member receives its index.
  * Synchronises the grid's stream.  AXP_E_INVAL for grids the group cannot
- * step, AXP_E_NOMEM when no member index or too few tiles are free. */
+ * step (among them grids with a soft source), AXP_E_NOMEM when no member
+ * index or too few tiles are free. */
 axp_status axp_group_add(axp_group *group, axp_grid *grid, int64_t steps, int32_t *member);
 /* Hand a member's grid back (finished or not); synchronises the group's stream. */
 axp_status axp_group_remove(axp_group *group, int32_t member);

@@ -14,7 +14,7 @@ import os
 import numpy as np
 
 from . import _build
-from .workloads import BC_CODE, AxionSpec, GridSpec, LaserSpec
+from .workloads import BC_CODE, AxionSpec, GridSpec, LaserSpec, SourceSpec
 
 AXP_OK, AXP_E_INVAL, AXP_E_UNSTABLE, AXP_E_NOMEM, AXP_E_CUDA, AXP_E_TIMEOUT, AXP_E_NONFINITE, AXP_E_STATE = range(8)
 AXP_FP64, AXP_FP32_SPLIT = 0, 1
@@ -49,6 +49,12 @@ class axp_axion_desc(C.Structure):
                 ("waist", C.c_double), ("length", C.c_double), ("speed", C.c_double), ("phase", C.c_double)]
 
 
+class axp_source_desc(C.Structure):
+    _fields_ = [("amplitude", C.c_double), ("k", C.c_double), ("pol", C.c_double * 3), ("centre", C.c_double * 3),
+                ("waist", C.c_double), ("duration", C.c_double), ("t_centre", C.c_double), ("phase", C.c_double),
+                ("plane", C.c_int64)]
+
+
 class axp_diag(C.Structure):
     _fields_ = [("step", C.c_int64)] + [(n, C.c_double) for n in (
         "t", "H_phi", "H_g0", "H_g1", "P_g2a", "P_a2g", "W", "sum_xB1z2", "sum_B1z2", "gauss_l2")]
@@ -78,6 +84,7 @@ def lib():
             "axp_set_background_field": ([_P, C.POINTER(C.c_double), C.POINTER(C.c_double)], C.c_int),
             "axp_inject_laser": ([_P, C.POINTER(axp_laser_desc)], C.c_int),
             "axp_inject_axion": ([_P, C.POINTER(axp_axion_desc)], C.c_int),
+            "axp_set_soft_source": ([_P, C.POINTER(axp_source_desc)], C.c_int),
             "axp_step": ([_P, C.c_int64], C.c_int),
             "axp_read_diagnostics": ([_P, C.POINTER(axp_diag), C.c_int64, C.POINTER(C.c_int64)], C.c_int),
             "axp_compute_diagnostics": ([_P, C.POINTER(axp_diag)], C.c_int),
@@ -154,6 +161,10 @@ def axp_inject_laser(h, laser: axp_laser_desc):
 
 def axp_inject_axion(h, ax: axp_axion_desc):
     _check(lib().axp_inject_axion(h, C.byref(ax)), "axp_inject_axion")
+
+
+def axp_set_soft_source(h, src):
+    _check(lib().axp_set_soft_source(h, C.byref(src) if src is not None else None), "axp_set_soft_source")
 
 
 def axp_step(h, nsteps):
@@ -288,6 +299,11 @@ def laser_of(L: LaserSpec) -> axp_laser_desc:
     return axp_laser_desc(L.amplitude, _D3(*L.k), _D3(*L.pol), _D3(*L.centre), L.waist, L.duration, L.phase)
 
 
+def source_of(S: SourceSpec) -> axp_source_desc:
+    return axp_source_desc(S.amplitude, S.k, _D3(*S.pol), _D3(*S.centre), S.waist, S.duration, S.t_centre, S.phase,
+                           int(S.plane))
+
+
 def axion_of(A: AxionSpec) -> axp_axion_desc:
     return axp_axion_desc(A.amplitude, _D3(*A.k), _D3(*A.centre), A.waist, A.length, A.speed, A.phase)
 
@@ -328,6 +344,10 @@ class Grid:
 
     def inject_axion(self, A: AxionSpec):
         axp_inject_axion(self.h, axion_of(A))
+
+    def set_soft_source(self, S: SourceSpec | None):
+        """Laser entering through an x-plane for the following steps (None: off)."""
+        axp_set_soft_source(self.h, source_of(S) if S is not None else None)
 
     def step(self, n=1):
         axp_step(self.h, n)

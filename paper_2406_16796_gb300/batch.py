@@ -39,6 +39,7 @@ def lib():
             "axp_batch_run": ([_P, C.c_int64], C.c_int),
             "axp_batch_progress": ([_P, C.POINTER(C.c_int64), C.c_int32], C.c_int),
             "axp_batch_result": ([_P, C.c_int32, C.POINTER(_axp.axp_diag)], C.c_int),
+            "axp_batch_results": ([_P, C.POINTER(C.c_int32), C.c_int32, C.POINTER(_axp.axp_diag)], C.c_int),
             "axp_batch_read_state": ([_P, C.c_int32, C.c_int32, C.POINTER(C.c_double), C.c_size_t], C.c_int),
             "axp_batch_set_tiling": ([_P, C.c_int32, C.c_int32, C.c_int32], C.c_int),
             "axp_batch_get_tiling": ([_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)], C.c_int),
@@ -149,6 +150,16 @@ class Batch:
         _check(lib().axp_batch_result(self.h, int(slot), C.byref(d)), "axp_batch_result")
         return d.as_dict()
 
+    def results(self, slots):
+        """result() of several slots in one launch and one synchronisation."""
+        slots = [int(x) for x in slots]
+        if not slots:
+            return []
+        arr = (C.c_int32 * len(slots))(*slots)
+        out = (_axp.axp_diag * len(slots))()
+        _check(lib().axp_batch_results(self.h, arr, len(slots), out), "axp_batch_results")
+        return [d.as_dict() for d in out]
+
     def read_state(self, slot, which):
         n = self.nx[slot]
         out = np.empty(n, dtype=np.float64)
@@ -190,11 +201,13 @@ class Batch:
         return best, times
 
 
-def run_scan(instances, max_cells=None, tune=True, chunk_steps=1024, graphs=True, tiling=None):
+def run_scan(instances, max_cells=None, tune=True, chunk_steps=1024, graphs=True, tiling=None, phases=None):
     """Admit every instance, run them all to completion, return (results per instance
     index, wall seconds from the first admission to the last result, tiling).  The
     autotuner's probe steps are real steps and are inside the timing.  A given
-    `tiling` (block_steps, segment_cells, threads) is used as it is, untuned."""
+    `tiling` (block_steps, segment_cells, threads) is used as it is, untuned.  A dict
+    passed as `phases` receives the wall seconds of admission, tuning, stepping and
+    read-out, and the device seconds of the stepping (CUDA events on the batch's stream)."""
     import torch
 
     total = sum(i.nx for i in instances)
@@ -202,17 +215,29 @@ def run_scan(instances, max_cells=None, tune=True, chunk_steps=1024, graphs=True
     t0 = time.perf_counter()
     b = Batch(len(instances), max_cells or total, graphs=graphs)
     slots = [b.add(i) for i in instances]
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
     if tiling is not None:
         b.set_tiling(*tiling)
     elif tune:
         tiling, _ = b.autotune()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(b.stream)
     while True:
         done = b.progress()
         rem = max(int(inst.steps) - int(done[s]) for inst, s in zip(instances, slots))
         if rem <= 0:
             break
         b.run(min(rem, chunk_steps))
-    res = [b.result(s) for s in slots]
+    ev1.record(b.stream)
+    ev1.synchronize()
+    t3 = time.perf_counter()
+    res = b.results(slots)
     el = time.perf_counter() - t0
+    if phases is not None:
+        phases.update(admit_s=t1 - t0, tune_s=t2 - t1, steps_s=t3 - t2, readout_s=el - (t3 - t0),
+                      steps_device_s=ev0.elapsed_time(ev1) / 1e3)
     b.close()
     return res, el, tiling or b.tiling()

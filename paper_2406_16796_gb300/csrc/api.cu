@@ -215,6 +215,10 @@ bool compute_layout(const axp_grid_desc &d, Workspace *w)
         w->off_pml_tab[a] = off;
         off += align_up((size_t)6 * d.n[a] * e);
     }
+    for (int c = 0; c < 2; c++) {  // soft-source sheet weights of E_y and E_z over the plane
+        w->off_src[c] = off;
+        off += align_up((size_t)plane_size(d, 0) * e);
+    }
     int64_t nb = (cells(d) + 255) / 256;
     if (nb > 1024) nb = 1024;
     if (nb < 1) nb = 1;
@@ -323,6 +327,67 @@ uint32_t order0_closure(const axp_grid *g)
 }
 
 }  // namespace axp
+
+namespace axp {
+
+double source_wave(const axp_grid *g, double x, double t)
+{
+    const axp_source_desc &q = g->src;
+    const double dt = g->desc.dt, dx = g->desc.d[0];
+    const double w = (2.0 / dt) * std::asin((dt / dx) * std::sin(q.k * dx / 2.0));
+    double e = 1.0;
+    if (q.duration > 0) {
+        const double L = q.duration / std::sqrt(2.0 * std::log(2.0));
+        const double u = (t - q.t_centre) - (x - q.centre[0]);
+        e = std::exp(-(u * u) / (L * L));
+    }
+    return e * std::cos(q.k * (x - q.centre[0]) - w * (t - q.t_centre) + q.phase);
+}
+
+}  // namespace axp
+
+namespace {
+
+// Sheet weights A pol_a f / dx of E_y (c = 0) and E_z (c = 1) over the (j, k) of
+// the plane, f the transverse Gaussian at each component's own position; zero
+// where the cells next to the sheet lie in a transverse absorbing layer.
+template <typename T>
+cudaError_t upload_source_weights(axp_grid *g)
+{
+    const axp_grid_desc &d = g->desc;
+    const axp_source_desc &q = g->src;
+    std::vector<double> em[3];
+    sigma_tables<double>(d, false, em);
+    const int64_t ny = d.n[1], nz = d.n[2];
+    std::vector<T> w[2];
+    for (int c = 0; c < 2; c++) {
+        const int a = c + 1;
+        w[c].assign(ny * nz, T(0));
+        for (int64_t k = 0; k < nz; k++)
+            for (int64_t j = 0; j < ny; j++) {
+                if (em[1][j] != 0.0 || em[2][k] != 0.0) continue;
+                double f = 1.0;
+                if (q.waist > 0) {
+                    // position of E_a: + d/2 along the other axes, + d along its own
+                    const double y = lo_of(g, 1) + ((double)j + (a == 1 ? 1.0 : 0.5)) * d.d[1];
+                    const double z = lo_of(g, 2) + ((double)k + (a == 2 ? 1.0 : 0.5)) * d.d[2];
+                    double r2 = 0.0;
+                    if (ny > 1) r2 = r2 + (y - q.centre[1]) * (y - q.centre[1]);
+                    if (nz > 1) r2 = r2 + (z - q.centre[2]) * (z - q.centre[2]);
+                    f = std::exp(-r2 / (q.waist * q.waist));
+                }
+                w[c][j + ny * k] = (T)(((q.amplitude * q.pol[a]) * f) / d.d[0]);
+            }
+    }
+    cudaError_t e = cudaSuccess;
+    for (int c = 0; c < 2 && e == cudaSuccess; c++)
+        e = cudaMemcpyAsync(g->ws + g->layout.off_src[c], w[c].data(), w[c].size() * sizeof(T),
+                            cudaMemcpyHostToDevice, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);  // the host vectors must outlive the copies
+    return e;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -447,6 +512,50 @@ axp_status axp_inject_laser(axp_grid *g, const axp_laser_desc *L)
         if ((g->desc.n[b] > 1 && L->pol[c] != 0) || (g->desc.n[c] > 1 && L->pol[b] != 0)) g->active |= 1u << (kB0 + a);
     }
     return cuda_status(e);
+}
+
+
+axp_status axp_set_soft_source(axp_grid *g, const axp_source_desc *q)
+{
+    if (!g) return AXP_E_INVAL;
+    if (g->group) return AXP_E_STATE;
+    if (q) {
+        const axp_grid_desc &d = g->desc;
+        bool ok = std::isfinite(q->amplitude) && std::isfinite(q->k) && q->k > 0 && std::isfinite(q->t_centre) &&
+                  std::isfinite(q->phase) && std::isfinite(q->waist) && q->waist >= 0 &&
+                  std::isfinite(q->duration) && q->duration >= 0 && q->pol[0] == 0.0;
+        for (int a = 0; a < 3; a++) ok = ok && std::isfinite(q->pol[a]) && std::isfinite(q->centre[a]);
+        ok = ok && d.n[0] >= 2 && q->plane >= 1 && q->plane <= d.n[0] - 1;
+        if (ok) {
+            // both cells next to the sheet outside the x absorbing layers
+            const int64_t N = d.pml_cells;
+            const bool lo_abs = d.em_bc[0][0] == AXP_BC_PML || d.axion_bc[0][0] == AXP_BC_PML;
+            const bool hi_abs = d.em_bc[0][1] == AXP_BC_PML || d.axion_bc[0][1] == AXP_BC_PML;
+            if (lo_abs && q->plane - 1 < N) ok = false;
+            if (hi_abs && q->plane > d.n[0] - 1 - N) ok = false;
+        }
+        if (!ok) return AXP_E_INVAL;
+    }
+    g->cfg_version++;
+    // the staggered state was formed with the old source: return to integer time first
+    cudaError_t e = ensure_integer(g);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (!q) {
+        g->src_on = false;
+        return AXP_OK;
+    }
+    g->src = *q;
+    g->src_on = true;
+    e = is_fp32(g) ? upload_source_weights<float>(g) : upload_source_weights<double>(g);
+    if (e != cudaSuccess) {
+        g->src_on = false;
+        return cuda_status(e);
+    }
+    // the sheets drive E_y/B_z (pol_y) and E_z/B_y (pol_z)
+    if (q->pol[1] != 0) g->active |= (1u << (kE0 + 1)) | (1u << (kB0 + 2));
+    if (q->pol[2] != 0) g->active |= (1u << (kE0 + 2)) | (1u << (kB0 + 1));
+    g->J_valid = false;
+    return AXP_OK;
 }
 
 axp_status axp_inject_axion(axp_grid *g, const axp_axion_desc *A)

@@ -51,6 +51,8 @@ struct Workspace {
     // b (1 + a); axion: c1 = dt^2/(1 + s dt), c2 = (1 - s dt)/(1 + s dt).  All decrease
     // with s, so the corner value (largest s of the axes) is the smallest of the axes'.
     size_t off_pml_tab[3];
+    // soft source: per (j, k) of the x-plane, A pol_a f / dx for a = y, z (zero in layers)
+    size_t off_src[2];
     size_t off_partials;
     size_t off_ring;
     size_t off_flag;
@@ -99,6 +101,9 @@ struct axp_grid {
     int n_step_graphs;
     int64_t step_graph_key[8];
     cudaGraphExec_t step_graph[8];
+    // soft source (axp_set_soft_source); its sheet weights sit in off_src
+    bool src_on;
+    axp_source_desc src;
 };
 
 namespace axp {
@@ -145,6 +150,15 @@ inline double lo_of(const axp_grid *g, int a)
 {
     return g->desc.lo[a] + (a == g->win_axis ? (double)g->win_offset * g->desc.d[a] : 0.0);
 }
+// Soft source: the incident wave's time factor env(t - t_c - (x - x_c)) cos(k (x - x_c)
+// - w (t - t_c) + phase) at lab position x and time t (host, FP64).
+double source_wave(const axp_grid *g, double x, double t);
+// lab x of the sheet's B faces (the plane itself) and of its E cells
+inline double source_x_b(const axp_grid *g) { return lo_of(g, 0) + (double)g->src.plane * g->desc.d[0]; }
+inline double source_x_e(const axp_grid *g) { return lo_of(g, 0) + ((double)g->src.plane + 0.5) * g->desc.d[0]; }
+// step times: t_n, t_{n+1/2}, t_{n+1} of step n
+inline double time_n(const axp_grid *g, int64_t n) { return (double)n * g->desc.dt; }
+inline double time_half(const axp_grid *g, int64_t n) { return ((double)n + 0.5) * g->desc.dt; }
 // shift the integer-time state by s cells along axis (moving window)
 template <typename T>
 cudaError_t shift_window(axp_grid *g, int axis, int64_t s);

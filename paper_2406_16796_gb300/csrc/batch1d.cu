@@ -311,7 +311,7 @@ __global__ void k_batch_init(Dev D, int slot, double A, double k)
 
 // FP64 diagnostics of one instance at its present (integer) time, with E
 // taken back from n+1/2 to n.  One block, fixed-order reduction.
-__global__ void __launch_bounds__(256) k_batch_diag(Dev D, int slot, axp_diag *out)
+__device__ void slot_diag(const Dev &D, int slot, axp_diag *out)
 {
     const Slot S = D.slots[slot];
     const int nx = S.nx;
@@ -373,6 +373,13 @@ __global__ void __launch_bounds__(256) k_batch_diag(Dev D, int slot, axp_diag *o
     }
 }
 
+// Diagnostics of the listed slots, one block per slot (each block's reduction is
+// the same fixed order whatever the list).
+__global__ void __launch_bounds__(256) k_batch_diag(Dev D, const int *slots, axp_diag *out)
+{
+    slot_diag(D, slots[blockIdx.x], out + blockIdx.x);
+}
+
 constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
@@ -393,8 +400,8 @@ Layout layout(int32_t max_instances, int64_t max_cells)
     off += align_up(((size_t)max_instances + (size_t)max_cells / 64 + 1) * sizeof(Item));
     L.counter = off;
     off += kAlign;
-    L.diag = off;
-    off += align_up(sizeof(axp_diag));
+    L.diag = off;  // one record per slot, then the list of slots asked for
+    off += align_up((size_t)max_instances * (sizeof(axp_diag) + sizeof(int)));
     L.total = off;
     return L;
 }
@@ -702,18 +709,29 @@ axp_status axp_batch_progress(axp_batch *b, int64_t *steps_done, int32_t max_slo
     return AXP_OK;
 }
 
-axp_status axp_batch_result(axp_batch *b, int32_t slot, axp_diag *out)
+axp_status axp_batch_results(axp_batch *b, const int32_t *slots, int32_t n, axp_diag *out)
 {
-    if (!b || !out || slot < 0 || slot >= b->max_instances || !b->slots[slot].active) return AXP_E_INVAL;
+    if (!b || !slots || !out || n < 1 || n > b->max_instances) return AXP_E_INVAL;
+    for (int32_t q = 0; q < n; q++)
+        if (slots[q] < 0 || slots[q] >= b->max_instances || !b->slots[slots[q]].active) return AXP_E_INVAL;
     axp_diag *dev = (axp_diag *)(b->ws + b->L.diag);
-    k_batch_diag<<<1, 256, 0, b->stream>>>(b->D, slot, dev);
-    cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaMemcpyAsync(out, dev, sizeof(axp_diag), cudaMemcpyDeviceToHost, b->stream);
+    int *dev_slots = (int *)(dev + b->max_instances);
+    cudaError_t e = cudaMemcpyAsync(dev_slots, slots, (size_t)n * sizeof(int), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) {
+        k_batch_diag<<<n, 256, 0, b->stream>>>(b->D, dev_slots, dev);
+        b->launches++;
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, dev, (size_t)n * sizeof(axp_diag), cudaMemcpyDeviceToHost, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return cuda_st(e);
-    if (!std::isfinite(out->H_phi) || !std::isfinite(out->H_g0) || !std::isfinite(out->H_g1)) return AXP_E_NONFINITE;
+    for (int32_t q = 0; q < n; q++)
+        if (!std::isfinite(out[q].H_phi) || !std::isfinite(out[q].H_g0) || !std::isfinite(out[q].H_g1))
+            return AXP_E_NONFINITE;
     return AXP_OK;
 }
+
+axp_status axp_batch_result(axp_batch *b, int32_t slot, axp_diag *out) { return axp_batch_results(b, &slot, 1, out); }
 
 axp_status axp_batch_read_state(axp_batch *b, int32_t slot, int32_t which, double *host_dst, size_t bytes)
 {

@@ -277,6 +277,7 @@ axp_status axp_group_add(axp_group *G, axp_grid *g, int64_t steps, int32_t *memb
     if (!G || !g || !member || steps < 0) return AXP_E_INVAL;
     if (g->group) return AXP_E_STATE;
     if (g->desc.precision != AXP_FP32_SPLIT || g->desc.diag_every != 0 || !tm2d_eligible(g)) return AXP_E_INVAL;
+    if (g->src_on) return AXP_E_INVAL;  // member parameters are fixed per parity; a source varies per step
     int m = -1;
     for (int i = 0; i < G->max_grids; i++)
         if (!G->members[i].active) {

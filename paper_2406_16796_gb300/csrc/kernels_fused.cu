@@ -84,7 +84,7 @@ cudaError_t dispatch_ax3d<float>(const fused::Params<float> &P, int nchunks, cud
 // (E/B and axion), no order-0 field active, no uniform background E.
 bool ax3d_supported(const axp_grid *g)
 {
-    if (grid_mode(g) != 3) return false;
+    if (grid_mode(g) != 3 || g->src_on) return false;
     if (order0_closure(g) != 0) return false;
     for (int a = 0; a < 3; a++) {
         if (g->E_ext[a] != 0.0) return false;
@@ -98,7 +98,8 @@ bool ax3d_supported(const axp_grid *g)
 
 // The 2D kernel specialised for the (E0z; B0x, B0y) laser: 2D grid, order-0
 // closure inside that set, every non-periodic side absorbing for both E/B and
-// the axion, no uniform background E.
+// the axion, no uniform background E.  A soft source is taken when it drives
+// E0z only (its polarisation along z keeps the closure inside the set).
 bool tm2d_supported(const axp_grid *g)
 {
     if (grid_mode(g) != 2) return false;
@@ -169,6 +170,15 @@ fused::Params<T> make_params(axp_grid *g)
     P.m2 = (T)(d.m * d.m);
     P.chunk = 1;
     P.chunk_edge = 1;
+    P.src_x = -1;
+    P.src_w = (const T *)(g->ws + w.off_src[1]);
+    P.src_b = P.src_e = T(0);
+    if (g->src_on) {
+        // the step from n: B^{n+1} from E^{n+1/2}, then E from B^{n+1}
+        P.src_x = (int)g->src.plane;
+        P.src_b = (T)(d.dt * source_wave(g, source_x_e(g), time_half(g, g->step)));
+        P.src_e = (T)(d.dt / 2.0 * source_wave(g, source_x_b(g), time_n(g, g->step + 1)));
+    }
     return P;
 }
 
@@ -194,7 +204,7 @@ template <typename T>
 bool fused_supported(const axp_grid *g)
 {
     const int mode = grid_mode(g);
-    if (mode == 0) return false;
+    if (mode == 0 || g->src_on) return false;
     int optin = 0;
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, g->device) != cudaSuccess) return false;
     if (smem_need<T>(mode, pick_set(g)) > (size_t)optin) return false;

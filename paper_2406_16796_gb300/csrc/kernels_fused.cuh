@@ -121,6 +121,13 @@ struct Params {
     T dt2g;                      // dt^2 g
     T h, dt, dt2, inv_dt, g, m2;
     T Bext[3];
+    // soft source (2D TM kernel): the x column of the sheet's E cells (-1: none), the
+    // electric sheet's weight per row (A pol_z f/dx), and this step's factors
+    // src_b = 2h tau(x_p + dx/2, t_{n+1/2}) (magnetic sheet, both B half-steps) and
+    // src_e = h tau(x_p, t_{n+1}) (electric sheet, each E half-step that reads B^{n+1})
+    int src_x;
+    const T *src_w;
+    T src_b, src_e;
 };
 
 // Compile-time loop: f(integral_constant<int, I>) for I = 0 .. N-1.

@@ -51,6 +51,39 @@ struct PBuf {
     T *p[3];
 };
 
+// Soft-source sheet for one half-step (Sec. 3.2 injection, read as a pair of
+// current sheets on an x-plane): the plane index (-1: no source), the sheet
+// weights A pol_a f/dx of E_y, E_z over (j, k), and the incident wave's factor
+// tau at this half-step's position and time.
+template <typename T>
+struct Sheet {
+    int64_t plane;
+    const T *w[2];
+    T tau;
+};
+
+template <typename T>
+Sheet<T> sheet_at(const axp_grid *g, double x, double t)
+{
+    Sheet<T> s;
+    s.plane = g->src_on ? g->src.plane : -1;
+    s.w[0] = (const T *)(g->ws + g->layout.off_src[0]);
+    s.w[1] = (const T *)(g->ws + g->layout.off_src[1]);
+    s.tau = g->src_on ? (T)source_wave(g, x, t) : T(0);
+    return s;
+}
+// the electric sheet reads B at time t; the magnetic sheet E at t_{n+1/2}
+template <typename T>
+Sheet<T> e_sheet(const axp_grid *g, double t)
+{
+    return sheet_at<T>(g, g->src_on ? source_x_b(g) : 0.0, t);
+}
+template <typename T>
+Sheet<T> b_sheet(const axp_grid *g, double t)
+{
+    return sheet_at<T>(g, g->src_on ? source_x_e(g) : 0.0, t);
+}
+
 // P at every cell centre, into scratch (one evaluation per cell and component).
 template <typename T, bool INCR>
 __global__ void __launch_bounds__(kThreads) k_pcell(View<T> v, PhiPair<T, INCR> q, PBuf<T> P)
@@ -121,8 +154,10 @@ __device__ __forceinline__ T curl_e(const View<T> &v, T *const E[3], int a, int6
 
 // E half-step: orders selected by the mask (bit 0 = order 0, bit 1 = order 1);
 // order 1 includes the axion current: X = curl B1 - g J.
+// Order 0 may carry the electric sheet: E_y, E_z of the cells at the plane add
+// w tau to their curl.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_e_half(View<T> v, int orders)
+__global__ void __launch_bounds__(kThreads) k_e_half(View<T> v, int orders, Sheet<T> s)
 {
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < v.N; c += (int64_t)gridDim.x * blockDim.x) {
         int64_t i, j, k;
@@ -131,7 +166,8 @@ __global__ void __launch_bounds__(kThreads) k_e_half(View<T> v, int orders)
         if (orders & 1) {
             T *const B[3] = {v.f[kB0], v.f[kB0 + 1], v.f[kB0 + 2]};
             for (int a = 0; a < 3; a++) {
-                const T X = curl_b(v, B, a, i, j, k);
+                T X = curl_b(v, B, a, i, j, k);
+                if (i == s.plane && a > 0) X = X + s.w[a - 1][j + v.n[1] * k] * s.tau;
                 v.f[kE0 + a][c] = half_update(v.f[kE0 + a][c], X, sig, v.h);
             }
         }
@@ -146,9 +182,10 @@ __global__ void __launch_bounds__(kThreads) k_e_half(View<T> v, int orders)
     }
 }
 
-// B half-step of both orders: B <- B - h curl E.
+// B half-step of both orders: B <- B - h curl E.  Order 0 may carry the magnetic
+// sheet on the faces at the plane (index plane - 1): B_y adds -w_z tau, B_z +w_y tau.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_b_half(View<T> v)
+__global__ void __launch_bounds__(kThreads) k_b_half(View<T> v, Sheet<T> s)
 {
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < v.N; c += (int64_t)gridDim.x * blockDim.x) {
         int64_t i, j, k;
@@ -156,7 +193,14 @@ __global__ void __launch_bounds__(kThreads) k_b_half(View<T> v)
         const T sig = sigma_of<T>(v.sig_em, i, j, k);
         T *const E0[3] = {v.f[kE0], v.f[kE0 + 1], v.f[kE0 + 2]};
         T *const E1[3] = {v.f[kE1], v.f[kE1 + 1], v.f[kE1 + 2]};
-        for (int a = 0; a < 3; a++) v.f[kB0 + a][c] = half_update(v.f[kB0 + a][c], -curl_e(v, E0, a, i, j, k), sig, v.h);
+        for (int a = 0; a < 3; a++) {
+            T X = -curl_e(v, E0, a, i, j, k);
+            if (i == s.plane - 1 && a > 0) {
+                const int64_t jk = j + v.n[1] * k;
+                X = X + (a == 1 ? -(s.w[1][jk] * s.tau) : s.w[0][jk] * s.tau);
+            }
+            v.f[kB0 + a][c] = half_update(v.f[kB0 + a][c], X, sig, v.h);
+        }
         for (int a = 0; a < 3; a++) v.f[kB1 + a][c] = half_update(v.f[kB1 + a][c], -curl_e(v, E1, a, i, j, k), sig, v.h);
     }
 }
@@ -254,7 +298,7 @@ struct EOut {
 // E^n from E^{n+1/2} of one order: E^n = E^{n+1/2} - h (curl B^n - g J^n) (order 1)
 // or - h curl B^n (order 0), written to `out` (which may alias the input).
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_e_unhalf(View<T> v, int order, EOut<T> out)
+__global__ void __launch_bounds__(kThreads) k_e_unhalf(View<T> v, int order, EOut<T> out, Sheet<T> s)
 {
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < v.N; c += (int64_t)gridDim.x * blockDim.x) {
         int64_t i, j, k;
@@ -265,6 +309,7 @@ __global__ void __launch_bounds__(kThreads) k_e_unhalf(View<T> v, int order, EOu
         for (int a = 0; a < 3; a++) {
             T X = curl_b(v, B, a, i, j, k);
             if (order) X = X - v.g * v.J[a][c];
+            else if (i == s.plane && a > 0) X = X + s.w[a - 1][j + v.n[1] * k] * s.tau;
             out.p[a][c] = half_inverse(v.f[fe + a][c], X, sig, v.h);
         }
     }
@@ -335,8 +380,10 @@ cudaError_t general_step(axp_grid *g, int64_t nsteps)
             g->J_valid = true;
         }
         View<T> v = make_view<T>(g);
-        k_e_half<T><<<nb, kThreads, 0, g->stream>>>(v, 3);
-        k_b_half<T><<<nb, kThreads, 0, g->stream>>>(v);
+        const Sheet<T> se0 = e_sheet<T>(g, time_n(g, g->step)), sb = b_sheet<T>(g, time_half(g, g->step));
+        const Sheet<T> se1 = e_sheet<T>(g, time_n(g, g->step + 1));
+        k_e_half<T><<<nb, kThreads, 0, g->stream>>>(v, 3, se0);
+        k_b_half<T><<<nb, kThreads, 0, g->stream>>>(v, sb);
         Ghosts<T> gcur = ghosts_at<T>(g, 0);
         if (incr)
             k_axion<T, true><<<nb, kThreads, 0, g->stream>>>(v, gcur);
@@ -353,8 +400,8 @@ cudaError_t general_step(axp_grid *g, int64_t nsteps)
                                                                            gnew.p[a][s]);
                 g->launches++;
             }
-        k_b_half<T><<<nb, kThreads, 0, g->stream>>>(v);
-        k_e_half<T><<<nb, kThreads, 0, g->stream>>>(v, 1);
+        k_b_half<T><<<nb, kThreads, 0, g->stream>>>(v, sb);
+        k_e_half<T><<<nb, kThreads, 0, g->stream>>>(v, 1, se1);
         g->launches += 2;
         // J^{n+1} from phi^{n+3/2} (hi) and phi^{n+1/2}
         if (incr) {
@@ -363,7 +410,7 @@ cudaError_t general_step(axp_grid *g, int64_t nsteps)
             e = launch_current<T, false>(g, v, v.phi_b, v.phi_cur, 2, 0);
         }
         if (e != cudaSuccess) return e;
-        k_e_half<T><<<nb, kThreads, 0, g->stream>>>(v, 2);
+        k_e_half<T><<<nb, kThreads, 0, g->stream>>>(v, 2, se1);
         g->launches++;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         // rotate the axion levels and the ghost planes
@@ -398,7 +445,7 @@ cudaError_t enter_staggered(axp_grid *g)
     if (e != cudaSuccess) return e;
     View<T> v = make_view<T>(g);
     const int nb = grid_for(v.N);
-    k_e_half<T><<<nb, kThreads, 0, g->stream>>>(v, 3);
+    k_e_half<T><<<nb, kThreads, 0, g->stream>>>(v, 3, e_sheet<T>(g, time_n(g, g->step)));
     g->launches++;
     g->staggered = true;
     g->J_valid = false;
@@ -414,7 +461,8 @@ cudaError_t exit_staggered(axp_grid *g, bool in_place)
     View<T> vout = make_view_eset<T>(g, oset);
     const int nb = grid_for(vin.N);
     EOut<T> o0{{vout.f[kE0], vout.f[kE0 + 1], vout.f[kE0 + 2]}};
-    k_e_unhalf<T><<<nb, kThreads, 0, g->stream>>>(vin, 0, o0);
+    const Sheet<T> se = e_sheet<T>(g, time_n(g, g->step));
+    k_e_unhalf<T><<<nb, kThreads, 0, g->stream>>>(vin, 0, o0, se);
     g->launches++;
     cudaError_t e;
     // J^n from E0^n (in vout), B0^n and the axion levels
@@ -424,7 +472,7 @@ cudaError_t exit_staggered(axp_grid *g, bool in_place)
         e = launch_current<T, false>(g, vout, vout.phi_cur, vout.phi_b, 0, 1);
     if (e != cudaSuccess) return e;
     EOut<T> o1{{vout.f[kE1], vout.f[kE1 + 1], vout.f[kE1 + 2]}};
-    k_e_unhalf<T><<<nb, kThreads, 0, g->stream>>>(vin, 1, o1);
+    k_e_unhalf<T><<<nb, kThreads, 0, g->stream>>>(vin, 1, o1, se);
     g->launches++;
     if (in_place) {
         g->staggered = false;

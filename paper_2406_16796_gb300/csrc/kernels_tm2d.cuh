@@ -69,8 +69,9 @@ enum { R_E0Z, R_E1Y, R_E1Z, R_PHI, R_N0Y2, R_MID3, R_N0Y3, R_PX4, R_N1Z4, R_N1Y4
 
 // One tile: x strip bx (VX written columns) and march chunk by (P.chunk planes)
 // of the grid P describes.  `rows` is the block's shared staging; the caller
-// separates consecutive tiles of one block with a barrier.
-template <typename T, bool INCR>
+// separates consecutive tiles of one block with a barrier.  SRC compiles in the
+// soft source's sheets (P.src_x >= 0); without it the body has no trace of them.
+template <typename T, bool INCR, bool SRC = false>
 __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, const int by, T (&rows)[2][NROWS][RS],
                                      T *stage)
 {
@@ -104,6 +105,10 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
     const T hx = h * idx, hy = h * idy, h2x = T(2) * hx, h2y = T(2) * hy, hg = h * g, h2g = T(2) * hg;
     const T cx = P.lap_c[0], cy = P.lap_c[1], c0 = P.lap_0, dt2g = P.dt2g, inv_dt = P.inv_dt;
     const T Bx = P.Bext[0], By = P.Bext[1], Bz = P.Bext[2];
+    // soft source: this column holds the sheet's E cells (electric sheet) or the
+    // B faces on the plane (magnetic sheet)
+    const bool src_e_col = SRC && wx == P.src_x;
+    const bool src_b_col = SRC && wx >= 0 && wx == P.src_x - 1;
     const bool xl = wx >= 0 && P.has_pml;
     const T sxa = xl ? P.sig_ax[0][wx] : T(0);
     // this column's layer coefficients (the plain update's where there is no layer):
@@ -120,10 +125,17 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
     // a whole plane: a ring of 8 planes in shared memory, copied asynchronously
     // with the plane's inputs (NS - 1 planes ahead), keeps their loads off the
     // per-plane critical path.  Planes t-4 .. t+NS-1 are live at once.
-    enum { Y_A1, Y_B1, Y_A2, Y_B2, Y_K1, Y_K2, Y_SA, NY };
+    // The ring's last slot holds the soft source's electric-sheet weight of the
+    // plane (zero without a source).
+    enum { Y_A1, Y_B1, Y_A2, Y_B2, Y_K1, Y_K2, Y_SA, NY, Y_W = NY };
     __shared__ __align__(16) T yring[8][NY + 1];
     auto fill_y = [&](int p) {
-        if (tx < NY) {
+        if (SRC && tx == Y_W) {
+            const int pw = pery ? ((p % ny) + ny) % ny : p;
+            T *dst = &yring[p & 7][Y_W];
+            if (P.src_x >= 0 && pw >= 0 && pw < ny) cp_elem(dst, P.src_w + pw, true);
+            else *dst = T(0);
+        } else if (tx < NY) {
             T *dst = &yring[p & 7][tx];
             if (!pery && P.has_pml && p >= 0 && p < ny) {
                 cp_elem(dst, tx < Y_SA ? P.pml_tab[1] + (tx * ny + p) : P.sig_ax[1] + p, true);
@@ -250,6 +262,9 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
                     N1z1 = fma(-b2, c1z, a2 * B1z1);
                 }
             }
+            // magnetic sheet on the B0y faces at the plane: -w tau in each of the two
+            // half-steps (the sheet stops at the transverse layers: w = 0 there)
+            if (src_b_col) N0y1 = fma(-yring[p & 7][Y_W], P.src_b, N0y1);
             if (EDGE && !in) N0x1 = N0y1 = N1x1 = N1y1 = N1z1 = T(0);
             if (write_col && p >= m0 && p < m1) {
                 const int64_t gi = (int64_t)gx + (int64_t)nx * p;
@@ -322,6 +337,7 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
                 lay(in, p, a1, b1, a2, b2);
                 EN2 = a1 == T(1) ? fma(hx, dbx, fma(-hy, dby, E0z2)) : fma(b1, dbx * idx - dby * idy, a1 * E0z2);
             }
+            if (src_e_col) EN2 = fma(yring[p & 7][Y_W], P.src_e, EN2);  // electric sheet
             if (EDGE && !in) MID2 = DT2 = EN2 = T(0);
         }
         // ---- stage 3: P^{n+1} on plane t-3 ----
@@ -372,6 +388,7 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
                         e0 = fma(b1, e0yx * idx - e0xy * idy, a1 * EN4);
                     }
                 }
+                if (src_e_col) e0 = fma(yring[p & 7][Y_W], P.src_e, e0);  // electric sheet
                 if (write_col) {
                     const int64_t gi = (int64_t)gx + (int64_t)nx * p;
                     P.Eout[3][gi] = ex;
@@ -433,20 +450,20 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
     cp_wait<0>();
 }
 
-template <typename T, bool INCR>
+template <typename T, bool INCR, bool SRC>
 __global__ void __launch_bounds__(TX, sizeof(T) == 4 ? 2 : 1) k_tm2d(fused::Params<T> P)
 {
     __shared__ T rows[2][NROWS][RS];
     extern __shared__ __align__(16) unsigned char tm2d_dyn[];
-    tile<T, INCR>(P, (int)blockIdx.x, (int)blockIdx.y, rows, reinterpret_cast<T *>(tm2d_dyn));
+    tile<T, INCR, SRC>(P, (int)blockIdx.x, (int)blockIdx.y, rows, reinterpret_cast<T *>(tm2d_dyn));
 }
 
-template <typename T, bool INCR>
-cudaError_t launch(const fused::Params<T> &P, int nchunks, cudaStream_t stream, int *occupancy, int tx = TX)
+template <typename T, bool INCR, bool SRC>
+cudaError_t launch_variant(const fused::Params<T> &P, int nchunks, cudaStream_t stream, int *occupancy, int tx)
 {
     // resident blocks per SM for each tile width (multiples of 32 up to TX)
     static int occ[TX / 32 + 1] = {};
-    auto kern = k_tm2d<T, INCR>;
+    auto kern = k_tm2d<T, INCR, SRC>;
     const size_t dyn = stage_bytes<T>();
     if (tx < 64 || tx > TX || tx % 32) return cudaErrorInvalidValue;
     if (occ[tx / 32] == 0) {
@@ -460,6 +477,13 @@ cudaError_t launch(const fused::Params<T> &P, int nchunks, cudaStream_t stream, 
     dim3 grid((P.n[0] + vx - 1) / vx, nchunks, 1);
     kern<<<grid, tx, dyn, stream>>>(P);
     return cudaGetLastError();
+}
+
+template <typename T, bool INCR>
+cudaError_t launch(const fused::Params<T> &P, int nchunks, cudaStream_t stream, int *occupancy, int tx = TX)
+{
+    if (P.src_x >= 0) return launch_variant<T, INCR, true>(P, nchunks, stream, occupancy, tx);
+    return launch_variant<T, INCR, false>(P, nchunks, stream, occupancy, tx);
 }
 
 }  // namespace tm2d

@@ -186,9 +186,9 @@ class Server:
                 if d1 > 0:
                     self.rate_1d = 0.5 * self.rate_1d + 0.5 * cells1 * k1 / d1
                 t = now()
-                for s in [s for s in live1 if prog[s] >= requests[live1[s]].steps]:
+                fin = [s for s in live1 if prog[s] >= requests[live1[s]].steps]
+                for s, d in zip(fin, self.batch.results(fin)):
                     i = live1.pop(s)
-                    d = self.batch.result(s)
                     self.batch.remove(s)
                     recs[i].P_g2a, recs[i].H_phi, recs[i].finished = d["P_g2a"], d["H_phi"], now()
                     done.append(i)

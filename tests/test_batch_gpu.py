@@ -189,3 +189,23 @@ def test_scan_draws_meet_the_conversion_probability_tolerance():
         assert g.diagnostics()["P_g2a"] == pytest.approx(want, rel=1e-3), d
         g.close()
     b.close()
+
+
+def test_batched_results_equal_the_per_slot_results():
+    """axp_batch_results: one launch for many slots, each record bit-identical to
+    the slot's own axp_batch_result; a free slot in the list is refused."""
+    from paper_2406_16796_gb300 import axp
+
+    B = batch_mod()
+    xs = [inst(nx=n, m=0.3, g=1e-3, By=1.0, Bz=0.2, steps=150) for n in (700, 3000, 9000, 1500)]
+    b = B.Batch(6, 20000)
+    slots = [b.add(x) for x in xs]
+    b.run(150)
+    many = b.results(slots[::-1])
+    for s, d in zip(slots[::-1], many):
+        assert d == b.result(s)
+    b.remove(slots[1])
+    with pytest.raises(axp.AxpError) as e:
+        b.results([slots[0], slots[1]])
+    assert e.value.status == axp.AXP_E_INVAL
+    b.close()
