@@ -4,7 +4,7 @@
 //
 // Same scheme and staggered state as kernels_fused.cuh: per step
 //   1. B^{n+1} = B^n - h curl E^{n+1/2} (twice)
-//   2. S^{n+1/2}/g = E0z B_ext,z; phi^{n+3/2}; phi^{n+1}, D_t phi^{n+1}; E0z^{n+1}
+//   2. S^{n+1/2}/g = E0z B_ext,z; phi^{n+3/2}; 2 phi^{n+1}, dt D_t phi^{n+1}; E0z^{n+1}
 //   3. P^{n+1} = (D_t phi) Bbar0 - Ebar0 x grad_c phi
 //   4. J^{n+1}; E^{n+3/2} = E^{n+1/2} + 2 x h (curl B^{n+1} - g J^{n+1}); E0z^{n+3/2}
 // A thread owns one x column of a tile (2 halo columns below, 3 above) and
@@ -105,6 +105,13 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
     const T hx = h * idx, hy = h * idy, h2x = T(2) * hx, h2y = T(2) * hy, hg = h * g, h2g = T(2) * hg;
     const T cx = P.lap_c[0], cy = P.lap_c[1], c0 = P.lap_0, dt2g = P.dt2g, inv_dt = P.inv_dt;
     const T Bx = P.Bext[0], By = P.Bext[1], Bz = P.Bext[2];
+    // The axion is carried as SM = 2 phi^{n+1} and DF = dt D_t phi^{n+1} (sum and
+    // difference of its two levels), with 1/2 and 1/dt folded into the constants
+    // that meet them: qidx = hidx/2 (exact), Bbar/dt as (N + N')(1/(2dt)) + B_ext/dt,
+    // and B_ext,z folded into the source and J_z coefficients.
+    const T qidx = T(0.5) * hidx, qidy = T(0.5) * hidy, hinv_dt = T(0.5) * inv_dt;
+    const T Bxi = Bx * inv_dt, Byi = By * inv_dt, dt2gBz = dt2g * Bz, gBzi = g * Bz * inv_dt;
+    const T h2gBzi = h2g * Bz * inv_dt;
     // soft source: this column holds the sheet's E cells (electric sheet) or the
     // B faces on the plane (magnetic sheet)
     const bool src_e_col = SRC && wx == P.src_x;
@@ -150,7 +157,7 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
     };
 
     // column history along y; suffix k = plane t - k of the current iteration
-    T E0z0 = 0, E0z1 = 0, E0z2 = 0;
+    T E0z0 = 0, E0z1 = 0, E0z2 = 0, E0z3 = 0, E0z4 = 0;
     T E1x0 = 0, E1x1 = 0, E1x2 = 0, E1x3 = 0, E1x4 = 0;
     T E1y0 = 0, E1y1 = 0, E1y2 = 0, E1y3 = 0, E1y4 = 0;
     T E1z0 = 0, E1z1 = 0, E1z2 = 0, E1z3 = 0, E1z4 = 0;
@@ -161,9 +168,9 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
     T N1x1 = 0, N1x2 = 0, N1x3 = 0, N1x4 = 0, N1x5 = 0;
     T N1y1 = 0, N1y2 = 0, N1y3 = 0, N1y4 = 0;
     T N1z1 = 0, N1z2 = 0, N1z3 = 0, N1z4 = 0, N1z5 = 0;
-    T MID2 = 0, MID3 = 0, MID4 = 0, DT2 = 0, DT3 = 0;  // phi^{n+1}, D_t phi^{n+1}
+    T SM2 = 0, SM3 = 0, SM4 = 0, DF2 = 0, DF3 = 0, DF4 = 0;  // 2 phi^{n+1}, dt D_t phi^{n+1}
     T EN2 = 0, EN3 = 0, EN4 = 0;                        // E0z^{n+1}
-    T PX3 = 0, PX4 = 0, PY3 = 0, PY4 = 0, PZ3 = 0, PZ4 = 0;
+    T PX3 = 0, PX4 = 0, PY3 = 0, PY4 = 0;
     const int t0 = m0 - 2, t1 = m1 + 3;
 
     auto gidx = [&](int p) -> int64_t {
@@ -279,7 +286,7 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
         {
             const int p = t - 2;
             const bool in = !EDGE || inside(p);
-            const T S = E0z2 * Bz;  // Ebar0 . Bbar0 with only E0z and the background along z
+            // S/g = Ebar0 . Bbar0 = E0z B_ext,z (only E0z and the background along z)
             // FP32 split: second differences formed from neighbour differences and the
             // mass term kept apart, so that neither rounds against the 2*phi terms
             const T spx = INCR ? (R[R_PHI][tx + 2] - ph2) + (R[R_PHI][tx] - ph2) : R[R_PHI][tx + 2] + R[R_PHI][tx];
@@ -290,7 +297,7 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
                 T acc = INCR ? fma(c0, ph2, pb2) : fma(c0, ph2, -pb2);
                 acc = fma(cx, spx, acc);
                 acc = fma(cy, spy, acc);
-                acc = fma(dt2g, S, acc);
+                acc = fma(dt2gBz, E0z2, acc);
                 if (INCR) {
                     pin = acc;
                     nw = ph2 + pin;
@@ -300,6 +307,7 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
             } else {
                 const T lap = INCR ? spx * P.idx2[0] + spy * P.idx2[1]
                                    : (spx - T(2) * ph2) * P.idx2[0] + (spy - T(2) * ph2) * P.idx2[1];
+                const T S = E0z2 * Bz;
                 const T Y = ((g * S - P.m2 * ph2) + lap) - sa * sa * ph2;
                 // damped leapfrog (1 + s dt) pi^{n+1} = dt^2 Y + (1 - s dt) pi^n as
                 // pi^{n+1} = c1 Y + c2 pi^n, with the corner's (smallest) coefficients
@@ -316,11 +324,11 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
                 }
             }
             if (INCR) {
-                MID2 = fma(T(0.5), pin, ph2);
-                DT2 = pin * inv_dt;
+                SM2 = fma(T(2), ph2, pin);
+                DF2 = pin;
             } else {
-                MID2 = T(0.5) * (nw + ph2);
-                DT2 = (nw - ph2) * inv_dt;
+                SM2 = nw + ph2;
+                DF2 = nw - ph2;
             }
             if (write_col && p >= m0 && p < m1) {
                 const int64_t gi = (int64_t)gx + (int64_t)nx * p;
@@ -338,19 +346,19 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
                 EN2 = a1 == T(1) ? fma(hx, dbx, fma(-hy, dby, E0z2)) : fma(b1, dbx * idx - dby * idy, a1 * E0z2);
             }
             if (src_e_col) EN2 = fma(yring[p & 7][Y_W], P.src_e, EN2);  // electric sheet
-            if (EDGE && !in) MID2 = DT2 = EN2 = T(0);
+            if (EDGE && !in) SM2 = DF2 = EN2 = T(0);
         }
         // ---- stage 3: P^{n+1} on plane t-3 ----
         {
             const int p = t - 3;
-            const T bbx = T(0.5) * (N0x3 + N0x4) + Bx;
-            const T bby = T(0.5) * (N0y3 + R[R_N0Y3][tx]) + By;
-            const T dpy = (MID2 - MID4) * hidy;
-            const T dpx = (R[R_MID3][tx + 2] - R[R_MID3][tx]) * hidx;
-            PX3 = fma(EN3, dpy, DT3 * bbx);   // Dt Bbar_x - (Ebar_y dphi_z - Ebar_z dphi_y)
-            PY3 = fma(-EN3, dpx, DT3 * bby);  // Dt Bbar_y - (Ebar_z dphi_x - Ebar_x dphi_z)
-            PZ3 = DT3 * Bz;                   // Dt Bbar_z (no laser B0z, no Ebar_x, Ebar_y)
-            if (EDGE && !inside(p)) PX3 = PY3 = PZ3 = T(0);
+            const T bbx = fma(hinv_dt, N0x3 + N0x4, Bxi);  // Bbar_x / dt
+            const T bby = fma(hinv_dt, N0y3 + R[R_N0Y3][tx], Byi);
+            const T dpy = (SM2 - SM4) * qidy;
+            const T dpx = (R[R_MID3][tx + 2] - R[R_MID3][tx]) * qidx;
+            PX3 = fma(EN3, dpy, DF3 * bbx);   // Dt Bbar_x - (Ebar_y dphi_z - Ebar_z dphi_y)
+            PY3 = fma(-EN3, dpx, DF3 * bby);  // Dt Bbar_y - (Ebar_z dphi_x - Ebar_x dphi_z)
+            // P_z = Dt B_ext,z (no laser B0z, no Ebar_x, Ebar_y): DF B_ext,z/dt, folded into E1z
+            if (EDGE && !inside(p)) PX3 = PY3 = T(0);
         }
         // ---- stage 4: J^{n+1}, E^{n+3/2} on plane t-4 ----
         {
@@ -363,13 +371,14 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
                 const T sjx = PX4 + R[R_PX4][tx + 2], sjy = PY4 + PY3;  // 2 J_x, 2 J_y
                 const T e1zy = N1z4 - N1z5, e1zx = N1z4 - R[R_N1Z4][tx];
                 const T e1yx = N1y4 - R[R_N1Y4][tx], e1xy = N1x4 - N1x5;
-                const T e0yx = N0y4 - R[R_N0Y4][tx], e0xy = N0x4 - N0x5;
                 T ex, ey, ez, e0;
+                // E0z's two half-steps read the same curl of B0^{n+1}: E0z^{n+3/2} =
+                // 2 E0z^{n+1} - E0z^{n+1/2} (an electric sheet's term is in it twice, too)
                 auto plain = [&]() {
                     ex = fma(h2y, e1zy, fma(-hg, sjx, E1x4));
                     ey = fma(-h2x, e1zx, fma(-hg, sjy, E1y4));
-                    ez = fma(h2x, e1yx, fma(-h2y, e1xy, fma(-h2g, PZ4, E1z4)));
-                    e0 = fma(hx, e0yx, fma(-hy, e0xy, EN4));
+                    ez = fma(h2x, e1yx, fma(-h2y, e1xy, fma(-h2gBzi, DF4, E1z4)));
+                    e0 = fma(T(2), EN4, -E0z4);
                 };
                 if (!EDGE) {
                     plain();
@@ -381,14 +390,14 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
                     } else {
                         const T xx = fma(-g, T(0.5) * sjx, e1zy * idy);
                         const T xy = fma(-g, T(0.5) * sjy, -e1zx * idx);
-                        const T xz = fma(-g, PZ4, e1yx * idx - e1xy * idy);
+                        const T xz = fma(-gBzi, DF4, e1yx * idx - e1xy * idy);
+                        const T e0yx = N0y4 - R[R_N0Y4][tx], e0xy = N0x4 - N0x5;
                         ex = fma(b2, xx, a2 * E1x4);
                         ey = fma(b2, xy, a2 * E1y4);
                         ez = fma(b2, xz, a2 * E1z4);
                         e0 = fma(b1, e0yx * idx - e0xy * idy, a1 * EN4);
                     }
                 }
-                if (src_e_col) e0 = fma(yring[p & 7][Y_W], P.src_e, e0);  // electric sheet
                 if (write_col) {
                     const int64_t gi = (int64_t)gx + (int64_t)nx * p;
                     P.Eout[3][gi] = ex;
@@ -420,7 +429,7 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
         rows[b][R_E1Z][tx + 1] = E1z1;
         rows[b][R_PHI][tx + 1] = ph2;
         rows[b][R_N0Y2][tx + 1] = N0y2;
-        rows[b][R_MID3][tx + 1] = MID3;
+        rows[b][R_MID3][tx + 1] = SM3;
         rows[b][R_N0Y3][tx + 1] = N0y3;
         rows[b][R_PX4][tx + 1] = PX4;
         rows[b][R_N1Z4][tx + 1] = N1z4;
@@ -431,7 +440,7 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
         if (fast) body(std::false_type{}, t, b);
         else body(std::true_type{}, t, b);
         // advance the column history by one plane
-        E0z2 = E0z1; E0z1 = E0z0;
+        E0z4 = E0z3; E0z3 = E0z2; E0z2 = E0z1; E0z1 = E0z0;
         E1x4 = E1x3; E1x3 = E1x2; E1x2 = E1x1; E1x1 = E1x0;
         E1y4 = E1y3; E1y3 = E1y2; E1y2 = E1y1; E1y1 = E1y0;
         E1z4 = E1z3; E1z3 = E1z2; E1z2 = E1z1; E1z1 = E1z0;
@@ -442,8 +451,8 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
         N1x5 = N1x4; N1x4 = N1x3; N1x3 = N1x2; N1x2 = N1x1;
         N1y4 = N1y3; N1y3 = N1y2; N1y2 = N1y1;
         N1z5 = N1z4; N1z4 = N1z3; N1z3 = N1z2; N1z2 = N1z1;
-        MID4 = MID3; MID3 = MID2; DT3 = DT2; EN4 = EN3; EN3 = EN2;
-        PX4 = PX3; PY4 = PY3; PZ4 = PZ3;
+        SM4 = SM3; SM3 = SM2; DF4 = DF3; DF3 = DF2; EN4 = EN3; EN3 = EN2;
+        PX4 = PX3; PY4 = PY3;
         cp_wait<NS - 2>();
         if (t < t1) take(t + 1);
     }
