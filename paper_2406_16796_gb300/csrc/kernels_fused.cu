@@ -170,6 +170,7 @@ fused::Params<T> make_params(axp_grid *g)
     P.m2 = (T)(d.m * d.m);
     P.chunk = 1;
     P.chunk_edge = 1;
+    P.chunk_first = 1;
     P.src_x = -1;
     P.src_w = (const T *)(g->ws + w.off_src[1]);
     P.src_b = P.src_e = T(0);
@@ -327,48 +328,78 @@ cudaError_t fused_step(axp_grid *g, int64_t nsteps, bool *handled)
         }
     } else if (tm) {
         // Tile width and march chunks: the fewest resident-block waves for the work
-        // a wave does, (planes + pipeline) x columns x blocks per SM.  Strips at a
-        // non-periodic x edge run the edge body over the layers and take about
-        // kEdgeCost times as long per plane; with one wave they may get more,
-        // shorter chunks from the blocks the other strips leave free.
-        const double kEdgeCost = sizeof(T) == 8 ? 1.30 : 1.10;
+        // a wave does, (planes + pipeline) x columns x blocks per SM, divided by the
+        // share of its issue rate an SM reaches with that many warps resident (below
+        // 8 warps the FP64 pipe's and the loads' latencies are no longer hidden:
+        // sqrt(warps / 8), from measured tile widths).  Measured per-CTA times give
+        // the other two costs: a strip at a non-periodic x edge runs the edge body
+        // over the x layer and takes kEdgeCost times as long per plane (its warps
+        // wait at each plane's barrier for the layer's warp), and a chunk that
+        // crosses a y layer runs the edge body over the layer and the pipeline's
+        // planes next to it, kLayerCost plane-times each.  With one wave the x-edge
+        // strips may get more, shorter chunks from the blocks the other strips
+        // leave free, and the other strips' first and last chunks are shortened by
+        // the y layer's extra cost.
+        const double kEdgeCost = sizeof(T) == 8 ? 1.55 : 1.35;
+        const double kLayerCost = sizeof(T) == 8 ? 0.93 : 0.32;
         int sms = 152;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
         const int64_t nx = g->desc.n[0], ny = g->desc.n[1];
         const bool xedge = g->desc.em_bc[0][0] != AXP_BC_PERIODIC;
+        const bool ylay = g->desc.em_bc[1][0] != AXP_BC_PERIODIC && P.has_pml;
+        const int64_t D = ylay ? (int64_t)std::lround(kLayerCost * (P.lay[1][0] + 7)) : 0;
+        // `rows` chunks over y: returns the costliest chunk in plane-times, with the
+        // first and the middle chunk sizes (the last chunk is what remains, <= cf)
+        auto split = [&](int64_t rows, int64_t *cf, int64_t *cm) -> double {
+            const int64_t u0 = (ny + rows - 1) / rows;
+            *cf = *cm = u0;
+            if (D == 0 || rows < 3) return (double)(u0 + 6 + D);
+            const int64_t c = (ny + 2 * D + rows - 1) / rows, f = c - D;
+            const int64_t last = ny - f - (rows - 2) * c;
+            if (f < 16 || last < 1 || last > f) return (double)(u0 + 6 + D);
+            *cf = f;
+            *cm = c;
+            return (double)(c + 6);
+        };
         double best = -1.0;
-        int best_ce = 0, best_rows = 0;
+        int best_ce = 0, best_rows = 0, best_cf = 0;
         for (int tx = tm2d::TX; tx >= 128; tx -= 32) {
             int o = 0;
             if ((e = dispatch_tm2d<T>(P, 0, g->stream, &o, tx)) != cudaSuccess) return e;
             o = o > 0 ? o : 1;
+            const double warps = (double)o * tx / 32.0;
+            const double u = warps >= 8.0 ? 1.0 : std::sqrt(warps / 8.0);
             const int64_t strips = (nx + (tx - tm2d::HL - tm2d::HR) - 1) / (tx - tm2d::HL - tm2d::HR);
             const int64_t slots = (int64_t)sms * o;
             const double r = xedge ? kEdgeCost : 1.0;
             for (int64_t nc = 1; nc <= 64 && ny / nc >= 16; nc++) {  // the same chunks everywhere
                 const int64_t chunk = (ny + nc - 1) / nc, rows = (ny + chunk - 1) / chunk;
                 const int64_t waves = (strips * rows + slots - 1) / slots;
-                const double cost = (double)waves * (double)(chunk + 6) * r * tx * o;
+                const double cost = (double)waves * (double)(chunk + 6 + D) * r * tx * o / u;
                 if (best < 0 || cost < best) {
                     best = cost;
                     tm_tx = tx;
                     P.chunk = (int)chunk;
+                    best_cf = (int)chunk;
                     best_ce = (int)chunk;
                     best_rows = (int)rows;
                 }
             }
             if (!xedge || strips < 3) continue;
             for (int64_t ni = 1; ni <= 64 && ny / ni >= 16; ni++) {  // shorter chunks at the x edges
-                const int64_t ci = (ny + ni - 1) / ni, ri = (ny + ci - 1) / ci;
+                const int64_t ri = ni;
+                int64_t cf = 0, cm = 0;
+                const double ci_cost = split(ri, &cf, &cm);
                 const int64_t left = slots - (strips - 2) * ri;
                 if (left < 2) break;
                 int64_t ne = std::min<int64_t>(left / 2, std::max<int64_t>(1, ny / 16));
                 const int64_t ce = (ny + ne - 1) / ne, re = (ny + ce - 1) / ce;
-                const double cost = std::max((double)(ci + 6), (double)(ce + 6) * r) * tx * o;
+                const double cost = std::max(ci_cost, (double)(ce + 6) * r + D) * tx * o / u;
                 if (cost < best) {
                     best = cost;
                     tm_tx = tx;
-                    P.chunk = (int)ci;
+                    P.chunk = (int)cm;
+                    best_cf = (int)cf;
                     best_ce = (int)ce;
                     best_rows = (int)std::max(ri, re);
                 }
@@ -377,9 +408,11 @@ cudaError_t fused_step(axp_grid *g, int64_t nsteps, bool *handled)
         if (best < 0) {  // grids shorter than 16 planes: one chunk
             tm_tx = tm2d::TX;
             P.chunk = (int)ny;
+            best_cf = (int)ny;
             best_ce = (int)ny;
             best_rows = 1;
         }
+        P.chunk_first = best_cf;
         P.chunk_edge = best_ce;
         nchunks = best_rows;
     } else if (mode >= 2) {
@@ -413,10 +446,11 @@ cudaError_t fused_step(axp_grid *g, int64_t nsteps, bool *handled)
     }
     for (; it < nsteps; it++) {
         if (it > 0) {
-            const int ch = P.chunk, che = P.chunk_edge;
+            const int ch = P.chunk, che = P.chunk_edge, chf = P.chunk_first;
             P = make_params<T>(g);
             P.chunk = ch;
             P.chunk_edge = che;
+            P.chunk_first = chf;
         }
         e = launch(P, nchunks, nullptr);
         if (e != cudaSuccess) return e;
@@ -467,6 +501,7 @@ fused::Params<T> tm2d_params(axp_grid *g, int chunk)
     fused::Params<T> P = make_params<T>(g);
     P.chunk = chunk;
     P.chunk_edge = chunk;
+    P.chunk_first = chunk;
     return P;
 }
 

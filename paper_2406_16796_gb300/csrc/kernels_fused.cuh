@@ -112,7 +112,8 @@ struct Params {
     int per[3];
     int axbc[3][2];
     int chunk;
-    int chunk_edge;  // march chunk of the strips at a non-periodic x edge (2D TM kernel)
+    int chunk_edge;   // march chunk of the strips at a non-periodic x edge (2D TM kernel)
+    int chunk_first;  // first (and about the last) chunk of the other strips (2D TM kernel)
     int has_pml;
     int lay[3][2];  // cells of absorbing layer at each side (0 where none)
     T idx[3], hidx[3], idx2[3];  // 1/d, 1/(2d), 1/d^2

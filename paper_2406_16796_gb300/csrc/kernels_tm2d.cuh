@@ -86,12 +86,16 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
     if (wx < 0 || wx >= nx) wx = perx ? ((wx % nx) + nx) % nx : -1;
     const bool write_col = tx >= HL && tx < ntx - HR && gx >= 0 && gx < nx;
     // the strips at a non-periodic x edge (which carry the x layers and run the
-    // edge body) may march shorter chunks than the others
+    // edge body) may march shorter chunks than the others; the others' first chunk
+    // (and, by the host's choice of sizes, about the last) may be shorter than the
+    // rest, since they run the edge body over the y layers
     const int nstrips = (nx + vx - 1) / vx;
-    const int chunk = (!perx && (bx == 0 || bx == nstrips - 1)) ? P.chunk_edge : P.chunk;
-    const int m0 = by * chunk;
+    const bool xstrip = !perx && (bx == 0 || bx == nstrips - 1);
+    const int chunk = xstrip ? P.chunk_edge : P.chunk;
+    const int first = xstrip ? P.chunk_edge : P.chunk_first;
+    const int m0 = by == 0 ? 0 : first + (by - 1) * chunk;
     if (m0 >= ny) return;  // (the whole block: more chunk rows than this strip uses)
-    const int m1 = min(ny, m0 + chunk);
+    const int m1 = min(ny, by == 0 ? first : m0 + chunk);
     const int gx0 = bx * vx - HL;
     // The plain body is exact for a column inside the grid with no x layer (the
     // edge body adds nothing there), so the choice is made per warp: in a tile
