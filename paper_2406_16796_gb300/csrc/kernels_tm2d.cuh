@@ -34,15 +34,24 @@ constexpr int RS = TX + 2;  // row stride: one guard element on each side
 // Input staging: each thread copies its own column's 11 input values of a plane
 // into shared memory with asynchronous copies (cp.async, zero-filled outside
 // the grid), NS planes deep, and reads them back when the plane is taken.  No
-// registers hold loads in flight and no barrier is needed for the staging
-// (a thread reads only what it copied itself).
-constexpr int NS = 4;    // planes in the staging ring (power of two)
+// registers hold loads in flight and no barrier is needed for the staging (a
+// thread reads only what it copied itself).  A plane's slot is thread-major (a
+// thread's 11 values together: an odd stride, so a warp's accesses fall in
+// distinct banks) and sized for the launch's tile width.
+//
+// Planes in the staging ring (a power of two): FP32 keeps 7 planes of loads in
+// flight (its two blocks per SM left HBM latency-bound with 3), FP64 3.
+template <typename T>
+__host__ __device__ constexpr int ns()
+{
+    return sizeof(T) == 4 ? 8 : 4;
+}
 constexpr int NIN = 11;  // input arrays per plane
 
 template <typename T>
-constexpr size_t stage_bytes()
+constexpr size_t stage_bytes(int tx = TX)
 {
-    return (size_t)NS * NIN * TX * sizeof(T);
+    return (size_t)ns<T>() * NIN * tx * sizeof(T);
 }
 
 __device__ __forceinline__ void cp_elem(float *dst, const float *src, bool ok)
@@ -75,6 +84,7 @@ template <typename T, bool INCR, bool SRC = false>
 __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, const int by, T (&rows)[2][NROWS][RS],
                                      T *stage)
 {
+    constexpr int NS = ns<T>();
     const int ntx = (int)blockDim.x, vx = ntx - HL - HR;  // this launch's tile width
     for (int i = threadIdx.x; i < 2 * NROWS * RS; i += ntx) (&rows[0][0][0])[i] = T(0);
 
@@ -133,21 +143,26 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
     auto smax = [](T a, T b) { return a > b ? a : b; };
     auto smin = [](T a, T b) { return a < b ? a : b; };
     // The y values of the same coefficients (and the axion sigma) are the same for
-    // a whole plane: a ring of 8 planes in shared memory, copied asynchronously
+    // a whole plane: a ring of planes in shared memory, copied asynchronously
     // with the plane's inputs (NS - 1 planes ahead), keeps their loads off the
-    // per-plane critical path.  Planes t-4 .. t+NS-1 are live at once.
+    // per-plane critical path.
     // The ring's last slot holds the soft source's electric-sheet weight of the
     // plane (zero without a source).
     enum { Y_A1, Y_B1, Y_A2, Y_B2, Y_K1, Y_K2, Y_SA, NY, Y_W = NY };
-    __shared__ __align__(16) T yring[8][NY + 1];
+    // Ring depth: a block's threads are at most one iteration apart (one barrier per
+    // iteration), and the fill for plane t+NS-1 at the top of iteration t happens
+    // before that iteration's barrier, while a thread still in iteration t-1 may
+    // read planes down to t-5: 9 planes live at once, so 16 slots.
+    constexpr int YR = 16;
+    __shared__ __align__(16) T yring[YR][NY + 1];
     auto fill_y = [&](int p) {
         if (SRC && tx == Y_W) {
             const int pw = pery ? ((p % ny) + ny) % ny : p;
-            T *dst = &yring[p & 7][Y_W];
+            T *dst = &yring[p & (YR - 1)][Y_W];
             if (P.src_x >= 0 && pw >= 0 && pw < ny) cp_elem(dst, P.src_w + pw, true);
             else *dst = T(0);
         } else if (tx < NY) {
-            T *dst = &yring[p & 7][tx];
+            T *dst = &yring[p & (YR - 1)][tx];
             if (!pery && P.has_pml && p >= 0 && p < ny) {
                 cp_elem(dst, tx < Y_SA ? P.pml_tab[1] + (tx * ny + p) : P.sig_ax[1] + p, true);
             } else {  // no layer: the plain update's coefficients
@@ -187,32 +202,32 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
         const int64_t gi = gidx(p);
         const bool ok = gi >= 0;
         const int64_t o = ok ? gi : 0;
-        T *st = stage + ((p - t0) & (NS - 1)) * (NIN * TX) + tx;
-        cp_elem(st + 0 * TX, P.Ein[2] + o, ok);
-        cp_elem(st + 1 * TX, P.Ein[3] + o, ok);
-        cp_elem(st + 2 * TX, P.Ein[4] + o, ok);
-        cp_elem(st + 3 * TX, P.Ein[5] + o, ok);
-        cp_elem(st + 4 * TX, P.Bin[0] + o, ok);
-        cp_elem(st + 5 * TX, P.Bin[1] + o, ok);
-        cp_elem(st + 6 * TX, P.Bin[3] + o, ok);
-        cp_elem(st + 7 * TX, P.Bin[4] + o, ok);
-        cp_elem(st + 8 * TX, P.Bin[5] + o, ok);
-        cp_elem(st + 9 * TX, P.phi + o, ok);
-        cp_elem(st + 10 * TX, P.phib + o, ok);
+        T *st = stage + ((p - t0) & (NS - 1)) * (NIN * ntx) + tx * NIN;
+        cp_elem(st + 0, P.Ein[2] + o, ok);
+        cp_elem(st + 1, P.Ein[3] + o, ok);
+        cp_elem(st + 2, P.Ein[4] + o, ok);
+        cp_elem(st + 3, P.Ein[5] + o, ok);
+        cp_elem(st + 4, P.Bin[0] + o, ok);
+        cp_elem(st + 5, P.Bin[1] + o, ok);
+        cp_elem(st + 6, P.Bin[3] + o, ok);
+        cp_elem(st + 7, P.Bin[4] + o, ok);
+        cp_elem(st + 8, P.Bin[5] + o, ok);
+        cp_elem(st + 9, P.phi + o, ok);
+        cp_elem(st + 10, P.phib + o, ok);
     };
     auto take = [&](int p) {
-        const T *st = stage + ((p - t0) & (NS - 1)) * (NIN * TX) + tx;
-        E0z0 = st[0 * TX];
-        E1x0 = st[1 * TX];
-        E1y0 = st[2 * TX];
-        E1z0 = st[3 * TX];
-        B0x0 = st[4 * TX];
-        B0y0 = st[5 * TX];
-        B1x0 = st[6 * TX];
-        B1y0 = st[7 * TX];
-        B1z0 = st[8 * TX];
-        ph0 = st[9 * TX];
-        pb0 = st[10 * TX];
+        const T *st = stage + ((p - t0) & (NS - 1)) * (NIN * ntx) + tx * NIN;
+        E0z0 = st[0];
+        E1x0 = st[1];
+        E1y0 = st[2];
+        E1z0 = st[3];
+        B0x0 = st[4];
+        B0y0 = st[5];
+        B1x0 = st[6];
+        B1y0 = st[7];
+        B1z0 = st[8];
+        ph0 = st[9];
+        pb0 = st[10];
     };
     // Absorbing-layer half-step F <- ((1 - s h/2) F + h X) / (1 + s h/2) written as
     // a F + b X, and two of them as a^2 F + b (1 + a) X, with per-axis tables; at a
@@ -225,7 +240,7 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
         a2 = ax2;
         b2 = bx2;
         if (in && !pery) {
-            const T *y = yring[p & 7];
+            const T *y = yring[p & (YR - 1)];
             a1 = smin(a1, y[Y_A1]);
             b1 = smin(b1, y[Y_B1]);
             a2 = smin(a2, y[Y_A2]);
@@ -275,7 +290,7 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
             }
             // magnetic sheet on the B0y faces at the plane: -w tau in each of the two
             // half-steps (the sheet stops at the transverse layers: w = 0 there)
-            if (src_b_col) N0y1 = fma(-yring[p & 7][Y_W], P.src_b, N0y1);
+            if (src_b_col) N0y1 = fma(-yring[p & (YR - 1)][Y_W], P.src_b, N0y1);
             if (EDGE && !in) N0x1 = N0y1 = N1x1 = N1y1 = N1z1 = T(0);
             if (write_col && p >= m0 && p < m1) {
                 const int64_t gi = (int64_t)gx + (int64_t)nx * p;
@@ -295,7 +310,7 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
             // mass term kept apart, so that neither rounds against the 2*phi terms
             const T spx = INCR ? (R[R_PHI][tx + 2] - ph2) + (R[R_PHI][tx] - ph2) : R[R_PHI][tx + 2] + R[R_PHI][tx];
             const T spy = INCR ? (ph1 - ph2) + (ph3 - ph2) : ph1 + ph3;
-            const T sa = (EDGE && in && P.has_pml) ? (pery ? sxa : smax(sxa, yring[p & 7][Y_SA])) : T(0);
+            const T sa = (EDGE && in && P.has_pml) ? (pery ? sxa : smax(sxa, yring[p & (YR - 1)][Y_SA])) : T(0);
             T nw, pin = T(0);
             if (!EDGE || sa == T(0)) {
                 T acc = INCR ? fma(c0, ph2, pb2) : fma(c0, ph2, -pb2);
@@ -317,8 +332,8 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
                 // pi^{n+1} = c1 Y + c2 pi^n, with the corner's (smallest) coefficients
                 T c1 = kx1, c2 = kx2;
                 if (!pery) {
-                    c1 = smin(c1, yring[p & 7][Y_K1]);
-                    c2 = smin(c2, yring[p & 7][Y_K2]);
+                    c1 = smin(c1, yring[p & (YR - 1)][Y_K1]);
+                    c2 = smin(c2, yring[p & (YR - 1)][Y_K2]);
                 }
                 if (INCR) {
                     pin = fma(c1, Y, c2 * pb2);
@@ -349,7 +364,7 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
                 lay(in, p, a1, b1, a2, b2);
                 EN2 = a1 == T(1) ? fma(hx, dbx, fma(-hy, dby, E0z2)) : fma(b1, dbx * idx - dby * idy, a1 * E0z2);
             }
-            if (src_e_col) EN2 = fma(yring[p & 7][Y_W], P.src_e, EN2);  // electric sheet
+            if (src_e_col) EN2 = fma(yring[p & (YR - 1)][Y_W], P.src_e, EN2);  // electric sheet
             if (EDGE && !in) SM2 = DF2 = EN2 = T(0);
         }
         // ---- stage 3: P^{n+1} on plane t-3 ----
@@ -423,10 +438,15 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
     cp_wait<NS - 2>();
     take(t0);
     __syncthreads();
+    // FP32: unrolled by 4, so that the column history shifts become register
+    // renaming and the row buffer and staging slot indices (taken relative to t0)
+    // become constants; FP64 is bound by its FP64 pipe and keeps the rolled loop
+    // (its registers are at the limit)
+#pragma unroll(sizeof(T) == 4 ? 4 : 1)
     for (int t = t0; t <= t1; ++t) {
         if (t + NS - 1 <= t1) prefetch(t + NS - 1);
         cp_commit();
-        const int b = t & 1;
+        const int b = (t - t0) & 1;
         // publish what the x neighbours read in this iteration
         rows[b][R_E0Z][tx + 1] = E0z1;
         rows[b][R_E1Y][tx + 1] = E1y1;
@@ -477,10 +497,11 @@ cudaError_t launch_variant(const fused::Params<T> &P, int nchunks, cudaStream_t 
     // resident blocks per SM for each tile width (multiples of 32 up to TX)
     static int occ[TX / 32 + 1] = {};
     auto kern = k_tm2d<T, INCR, SRC>;
-    const size_t dyn = stage_bytes<T>();
+    // the staging ring is sized for the launch's tile width
+    const size_t dyn = stage_bytes<T>(tx);
     if (tx < 64 || tx > TX || tx % 32) return cudaErrorInvalidValue;
     if (occ[tx / 32] == 0) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stage_bytes<T>());
         if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[tx / 32], kern, tx, dyn);
         if (e != cudaSuccess) return e;
     }
