@@ -28,10 +28,17 @@
 namespace axp {
 namespace ax3d {
 
-constexpr int TX = 32, TY = 16, NT = TX * TY;
+constexpr int TX = 32;
 constexpr int HL = 1, HR = 2;
-constexpr int VX = TX - HL - HR, VY = TY - HL - HR;
-constexpr int PX = TX + 2, PY = TY + 2, PLANE = PX * PY;  // published planes, one guard cell around
+constexpr int VX = TX - HL - HR;
+constexpr int PX = TX + 2;  // published planes: one guard cell around the tile
+// Tile height: FP32 takes 32 rows (one 1024-thread block per SM at <= 64
+// registers; the y halo is 3 of 32 rows instead of 3 of 16), FP64 16 rows.
+template <typename T>
+struct Geo {
+    static constexpr int TY = sizeof(T) == 4 ? 32 : 16, NT = TX * TY, VY = TY - HL - HR;
+    static constexpr int PY = TY + 2, PLANE = PX * PY;
+};
 constexpr int NS = 4;                                     // input staging depth (power of two)
 constexpr int NIN = 8;                                    // E1 xyz, B1 xyz, phi, second axion level
 enum { P_EX, P_EZ, P_PHI, P_NX, P_NZ, P_DT, NPUB };  // values read by the y neighbours
@@ -39,12 +46,13 @@ enum { P_EX, P_EZ, P_PHI, P_NX, P_NZ, P_DT, NPUB };  // values read by the y nei
 template <typename T>
 constexpr size_t smem_bytes()
 {
-    return ((size_t)2 * NPUB * PLANE + (size_t)NS * NIN * NT) * sizeof(T);
+    return ((size_t)2 * NPUB * Geo<T>::PLANE + (size_t)NS * NIN * Geo<T>::NT) * sizeof(T);
 }
 
 template <typename T, bool INCR>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_ax3d(fused::Params<T> P)
+__global__ void __launch_bounds__(Geo<T>::NT, 1) k_ax3d(fused::Params<T> P)
 {
+    constexpr int TY = Geo<T>::TY, NT = Geo<T>::NT, VY = Geo<T>::VY, PLANE = Geo<T>::PLANE;
     extern __shared__ __align__(16) unsigned char ax3d_dyn[];
     T *pub = reinterpret_cast<T *>(ax3d_dyn);  // [2][NPUB][PY][PX]
     T *stage = pub + 2 * NPUB * PLANE;         // [NS][NIN][NT]
@@ -215,13 +223,13 @@ cudaError_t launch(const fused::Params<T> &P, int nchunks, cudaStream_t stream, 
     const size_t dyn = smem_bytes<T>();
     if (occ == 0) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, dyn);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, Geo<T>::NT, dyn);
         if (e != cudaSuccess) return e;
     }
     if (occupancy) *occupancy = occ;
     if (nchunks <= 0) return cudaSuccess;
-    dim3 grid((P.n[0] + VX - 1) / VX, (P.n[1] + VY - 1) / VY, nchunks);
-    kern<<<grid, NT, dyn, stream>>>(P);
+    dim3 grid((P.n[0] + VX - 1) / VX, (P.n[1] + Geo<T>::VY - 1) / Geo<T>::VY, nchunks);
+    kern<<<grid, Geo<T>::NT, dyn, stream>>>(P);
     return cudaGetLastError();
 }
 
