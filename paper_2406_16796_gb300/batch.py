@@ -183,8 +183,8 @@ class Batch:
         import torch
 
         if candidates is None:
-            candidates = [(bs, seg, th) for bs in (16, 32, 64) for seg in (1536, 3584) for th in (256, 512)
-                          if seg + 6 * bs <= 8 * th]
+            # segments that fill a block's 8 cells per thread with their halo
+            candidates = [(bs, 8 * th - 6 * bs, th) for th in (256, 512) for bs in (16, 32, 48, 64)]
         times = {}
         for cand in candidates:
             self.set_tiling(*cand)

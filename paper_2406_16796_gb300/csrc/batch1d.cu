@@ -227,19 +227,21 @@ __global__ void __launch_bounds__(kMaxThreads) k_batch_block(Dev D, int budget, 
             fPH[pb ^ 1][t] = PH[0];
             lPH[pb ^ 1][t] = pick(PH, jlast);
         };
-        const bool full = cnt == kK;
+        // Threads past the item's last cell only keep the barriers: no thread that
+        // holds cells has them as neighbours (the item's last thread clamps or wraps).
+        const bool full = cnt == kK, idle = cnt == 0;
         using Full = std::integral_constant<bool, true>;
         using Part = std::integral_constant<bool, false>;
         for (int st = 0; st < T; st++) {
             const int pb = st & 1;
             if (full) stage1(Full{});
-            else stage1(Part{});
+            else if (!idle) stage1(Part{});
             __syncthreads();
             if (full) stage2(Full{}, pb);
-            else stage2(Part{}, pb);
+            else if (!idle) stage2(Part{}, pb);
             __syncthreads();
             if (full) stage3(Full{}, pb);
-            else stage3(Part{}, pb);
+            else if (!idle) stage3(Part{}, pb);
             __syncthreads();
         }
         // write the valid core cells to the other buffer
