@@ -282,6 +282,8 @@ View<T> make_view_eset(axp_grid *g, int eset)
         v.region_hi[a] = rhi;
     }
     v.N = cells(d);
+    v.vaxis = -1;
+    v.Nv = v.N;
     v.dt = (T)d.dt;
     v.h = (T)(d.dt / 2.0);
     v.g = (T)d.g;
@@ -595,8 +597,13 @@ static axp_status run_steps(axp_grid *g, int64_t nsteps)
 // lower index and vacuum enters at the high end.
 static axp_status shift_now(axp_grid *g, int axis, int64_t cells)
 {
-    cudaError_t e = ensure_integer(g);
-    if (e == cudaSuccess) e = is_fp32(g) ? shift_window<float>(g, axis, cells) : shift_window<double>(g, axis, cells);
+    bool done = false;
+    cudaError_t e = is_fp32(g) ? shift_staggered<float>(g, axis, cells, &done)
+                               : shift_staggered<double>(g, axis, cells, &done);
+    if (e == cudaSuccess && !done) {
+        e = ensure_integer(g);
+        if (e == cudaSuccess) e = is_fp32(g) ? shift_window<float>(g, axis, cells) : shift_window<double>(g, axis, cells);
+    }
     if (e != cudaSuccess) return cuda_status(e);
     if (g->win_axis < 0) g->win_axis = axis;
     g->win_offset += cells;

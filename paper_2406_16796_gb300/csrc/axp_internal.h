@@ -37,6 +37,10 @@ struct View {
     int periodic[3];
     int axbc[3][2];
     int region_lo[3], region_hi[3];  // diagnostics region [lo, hi) per axis
+    // cells a general kernel visits: all (vaxis < 0), or those whose index along
+    // vaxis lies in [vlo, vhi); Nv of them
+    int vaxis;
+    int64_t vlo, vhi, Nv;
 };
 
 struct Workspace {
@@ -162,6 +166,10 @@ inline double time_half(const axp_grid *g, int64_t n) { return ((double)n + 0.5)
 // shift the integer-time state by s cells along axis (moving window)
 template <typename T>
 cudaError_t shift_window(axp_grid *g, int axis, int64_t s);
+// the same shift applied to the staggered state with only the bands at the ends
+// of the axis taken through integer time; *done = false where it does not apply
+template <typename T>
+cudaError_t shift_staggered(axp_grid *g, int axis, int64_t s, bool *done);
 // destroy the cached step graphs (and the capture stream when `all`)
 void release_step_graphs(axp_grid *g, bool all);
 

@@ -229,4 +229,22 @@ __device__ __forceinline__ void cell_of(int64_t c, const int64_t n[3], int64_t *
     *k = r / n[1];
 }
 
+// The q-th cell a general kernel visits (x fastest): every cell, or only those
+// with vlo <= index < vhi along vaxis.  Returns the cell's linear index.
+template <typename T>
+__device__ __forceinline__ int64_t visit(const View<T> &v, int64_t q, int64_t *i, int64_t *j, int64_t *k)
+{
+    if (v.vaxis < 0) {
+        cell_of(q, v.n, i, j, k);
+        return q;
+    }
+    int64_t m[3] = {v.n[0], v.n[1], v.n[2]};
+    m[v.vaxis] = v.vhi - v.vlo;
+    cell_of(q, m, i, j, k);
+    if (v.vaxis == 0) *i += v.vlo;
+    else if (v.vaxis == 1) *j += v.vlo;
+    else *k += v.vlo;
+    return lin3(v.n, *i, *j, *k);
+}
+
 }  // namespace axp

@@ -88,9 +88,9 @@ Sheet<T> b_sheet(const axp_grid *g, double t)
 template <typename T, bool INCR>
 __global__ void __launch_bounds__(kThreads) k_pcell(View<T> v, PhiPair<T, INCR> q, PBuf<T> P)
 {
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < v.N; c += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t qv = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; qv < v.Nv; qv += (int64_t)gridDim.x * blockDim.x) {
         int64_t i, j, k;
-        cell_of(c, v.n, &i, &j, &k);
+        const int64_t c = visit(v, qv, &i, &j, &k);
         for (int a = 0; a < 3; a++) P.p[a][c] = p_comp<T, INCR>(v, q, a, i, j, k);
     }
 }
@@ -101,9 +101,9 @@ __global__ void __launch_bounds__(kThreads) k_pcell(View<T> v, PhiPair<T, INCR> 
 template <typename T, bool INCR>
 __global__ void __launch_bounds__(kThreads) k_current(View<T> v, PhiPair<T, INCR> q, PBuf<T> P)
 {
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < v.N; c += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t qv = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; qv < v.Nv; qv += (int64_t)gridDim.x * blockDim.x) {
         int64_t i, j, k;
-        cell_of(c, v.n, &i, &j, &k);
+        const int64_t c = visit(v, qv, &i, &j, &k);
         for (int a = 0; a < 3; a++) {
             int64_t u[3];
             unit(a, u);
@@ -159,9 +159,9 @@ __device__ __forceinline__ T curl_e(const View<T> &v, T *const E[3], int a, int6
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_e_half(View<T> v, int orders, Sheet<T> s)
 {
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < v.N; c += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t qv = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; qv < v.Nv; qv += (int64_t)gridDim.x * blockDim.x) {
         int64_t i, j, k;
-        cell_of(c, v.n, &i, &j, &k);
+        const int64_t c = visit(v, qv, &i, &j, &k);
         const T sig = sigma_of<T>(v.sig_em, i, j, k);
         if (orders & 1) {
             T *const B[3] = {v.f[kB0], v.f[kB0 + 1], v.f[kB0 + 2]};
@@ -300,9 +300,9 @@ struct EOut {
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_e_unhalf(View<T> v, int order, EOut<T> out, Sheet<T> s)
 {
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < v.N; c += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t qv = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; qv < v.Nv; qv += (int64_t)gridDim.x * blockDim.x) {
         int64_t i, j, k;
-        cell_of(c, v.n, &i, &j, &k);
+        const int64_t c = visit(v, qv, &i, &j, &k);
         const T sig = sigma_of<T>(v.sig_em, i, j, k);
         const int fb = order ? kB1 : kB0, fe = order ? kE1 : kE0;
         T *const B[3] = {v.f[fb], v.f[fb + 1], v.f[fb + 2]};
@@ -354,8 +354,15 @@ static cudaError_t launch_current(axp_grid *g, const View<T> &v, const T *hi, co
     // value left in one would become part of the state)
     PBuf<T> P;
     for (int a = 0; a < 3; a++) P.p[a] = (T *)(g->ws + g->layout.off_P[a]);
-    k_pcell<T, INCR><<<grid_for(v.N), kThreads, 0, g->stream>>>(v, q, P);
-    k_current<T, INCR><<<grid_for(v.N), kThreads, 0, g->stream>>>(v, q, P);
+    // J at a cell averages P there and one cell up along each axis: on a slab, P is
+    // formed one cell further along the slab's axis
+    View<T> vp = v;
+    if (v.vaxis >= 0 && v.vhi < v.n[v.vaxis]) {
+        vp.vhi = v.vhi + 1;
+        vp.Nv = v.Nv / (v.vhi - v.vlo) * (vp.vhi - vp.vlo);
+    }
+    k_pcell<T, INCR><<<grid_for(vp.Nv), kThreads, 0, g->stream>>>(vp, q, P);
+    k_current<T, INCR><<<grid_for(v.Nv), kThreads, 0, g->stream>>>(v, q, P);
     g->launches += 2;
     return cudaGetLastError();
 }
@@ -483,6 +490,95 @@ cudaError_t exit_staggered(axp_grid *g, bool in_place)
     return cudaGetLastError();
 }
 
+// View of the cells whose index along `axis` lies in [lo, hi).
+template <typename T>
+static View<T> slab_view(axp_grid *g, int axis, int64_t lo, int64_t hi)
+{
+    View<T> v = make_view<T>(g);
+    v.vaxis = axis;
+    v.vlo = lo;
+    v.vhi = hi;
+    v.Nv = v.N / g->desc.n[axis] * (hi - lo);
+    return v;
+}
+
+template <typename T>
+static cudaError_t slab_current(axp_grid *g, const View<T> &v)
+{
+    if (g->desc.precision == AXP_FP32_SPLIT) return launch_current<T, true>(g, v, v.phi_cur, v.phi_b, 0, 1);
+    return launch_current<T, false>(g, v, v.phi_cur, v.phi_b, 0, 1);
+}
+
+// E^{n+1/2} -> E^n in place on a slab, the other cells left as they are.
+template <typename T>
+static cudaError_t exit_slab(axp_grid *g, int axis, int64_t lo, int64_t hi)
+{
+    const View<T> v = slab_view<T>(g, axis, lo, hi);
+    const Sheet<T> se = e_sheet<T>(g, time_n(g, g->step));
+    EOut<T> o0{{v.f[kE0], v.f[kE0 + 1], v.f[kE0 + 2]}};
+    k_e_unhalf<T><<<grid_for(v.Nv), kThreads, 0, g->stream>>>(v, 0, o0, se);
+    g->launches++;
+    cudaError_t e = slab_current<T>(g, v);
+    if (e != cudaSuccess) return e;
+    EOut<T> o1{{v.f[kE1], v.f[kE1 + 1], v.f[kE1 + 2]}};
+    k_e_unhalf<T><<<grid_for(v.Nv), kThreads, 0, g->stream>>>(v, 1, o1, se);
+    g->launches++;
+    return cudaGetLastError();
+}
+
+// E^n -> E^{n+1/2} in place on a slab.
+template <typename T>
+static cudaError_t enter_slab(axp_grid *g, int axis, int64_t lo, int64_t hi)
+{
+    const View<T> v = slab_view<T>(g, axis, lo, hi);
+    cudaError_t e = slab_current<T>(g, v);
+    if (e != cudaSuccess) return e;
+    k_e_half<T><<<grid_for(v.Nv), kThreads, 0, g->stream>>>(v, 3, e_sheet<T>(g, time_n(g, g->step)));
+    g->launches++;
+    return cudaGetLastError();
+}
+
+// Moving-window shift of the staggered state (E^{n+1/2}, B^n, phi) without a
+// round trip of the whole grid through integer time.  Away from the ends of the
+// window axis the shift commutes with the local conversion E^{n+1/2} = E^n +
+// h X(E0^n, B^n, phi) (X = curl B - g J, boundary closure included: the cells
+// entering at the high end are vacuum, as the zero closure outside the grid
+// was).  It does not commute where the absorbing layer's sigma differs between a
+// cell's old and new position, nor at the low end, where a cell loses its lower
+// neighbour.  So only the bands there go through integer time: the source
+// bands are converted to E^n in place, everything is shifted, and the
+// destination bands are converted back.  The bands reach r = 2 cells beyond the
+// layers (the current's stencil) and m = 3 more; at a band's inner edge both
+// conversions read the same (translated) neighbours outside the band, so they
+// cancel there.  Returns false (and does nothing) where the bands would meet or
+// a soft source is set (its sheet cells would need bands of their own): the
+// caller then converts the whole grid.
+template <typename T>
+cudaError_t shift_staggered(axp_grid *g, int axis, int64_t s, bool *done)
+{
+    *done = false;
+    const axp_grid_desc &d = g->desc;
+    const int64_t n = d.n[axis];
+    if (!g->staggered || g->src_on || s <= 0 || s >= n) return cudaSuccess;
+    auto layer = [&](int side) -> int64_t {
+        return (d.em_bc[axis][side] == AXP_BC_PML || d.axion_bc[axis][side] == AXP_BC_PML) ? d.pml_cells : 0;
+    };
+    const int64_t r = 2, m = 3;
+    const int64_t d0_hi = layer(0) + r + m;          // destination band at the low end: [0, d0_hi)
+    const int64_t d1_lo = n - layer(1) - s - r - m;  // at the high end, with the entering cells: [d1_lo, n)
+    const int64_t s0_lo = std::max<int64_t>(0, s - r), s0_hi = d0_hi + s;  // their sources
+    const int64_t s1_lo = d1_lo + s;
+    if (d1_lo < d0_hi + 4 || s1_lo < s0_hi + 4) return cudaSuccess;
+    cudaError_t e = exit_slab<T>(g, axis, s0_lo, s0_hi);
+    if (e == cudaSuccess) e = exit_slab<T>(g, axis, s1_lo, n);
+    if (e == cudaSuccess) e = shift_window<T>(g, axis, s);
+    if (e == cudaSuccess) e = enter_slab<T>(g, axis, 0, d0_hi);
+    if (e == cudaSuccess) e = enter_slab<T>(g, axis, d1_lo, n);
+    g->J_valid = false;
+    *done = e == cudaSuccess;
+    return e;
+}
+
 // Shift the integer-time state (every field array and both axion levels) by s
 // cells along `axis`, out of place into the spare field set and axion buffers.
 template <typename T>
@@ -520,6 +616,8 @@ cudaError_t shift_window(axp_grid *g, int axis, int64_t s)
     return cudaGetLastError();
 }
 
+template cudaError_t shift_staggered<double>(axp_grid *, int, int64_t, bool *);
+template cudaError_t shift_staggered<float>(axp_grid *, int, int64_t, bool *);
 template cudaError_t shift_window<double>(axp_grid *, int, int64_t);
 template cudaError_t shift_window<float>(axp_grid *, int, int64_t);
 template cudaError_t enter_staggered<double>(axp_grid *);

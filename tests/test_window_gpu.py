@@ -169,3 +169,41 @@ def test_window_refuses_periodic_axes_outflow_and_bad_speeds():
     with pytest.raises(axp.AxpError):
         o.shift_window(0, 1)
     o.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("axis,s", [(0, 4), (0, 16), (1, 7)])
+def test_staggered_shift_matches_the_integer_time_shift(prec, axis, s):
+    """A shift of a grid held in the fused path's staggered state takes only the
+    bands at the ends of the window axis through integer time; it gives the state
+    of the same shift done in integer time (the grid converted as a whole first),
+    to rounding, and the runs that follow stay together."""
+    axp = axp_mod()
+    w = W.pulse_2d(nx=300, ny=160, m=0.5 * W.K0, g=1e-2, precision=prec)
+    grid = w.grid.replace(pml_cells=10)
+    L = W.LaserSpec(amplitude=0.01, k=(W.K0, 0.0, 0.0), pol=(0.0, 0.0, 1.0), centre=(4.0, 0.0, 0.0), waist=0.8,
+                    duration=1.0)
+    a, b = axp.Grid(grid), axp.Grid(grid)
+    for x in (a, b):
+        x.inject_laser(L)
+        x.step(25)
+    assert a.kernel_path() == axp.AXP_KERNEL_TM2D
+    n0 = a.launches()
+    a.shift_window(axis, s)                # staggered: banded
+    banded = a.launches() - n0
+    axp.axp_set_background_field(b.h, grid.B_ext, grid.E_ext)  # converts the whole grid to integer time
+    n1 = b.launches()
+    b.shift_window(axis, s)
+    # a whole-grid conversion before the shift would add 4 launches; the two bands'
+    # round trips add 14
+    assert banded - (b.launches() - n1) > 4
+    tol = 1e-12 if prec == "fp64" else 1e-5
+    for steps in (0, 20):
+        a.step(steps)
+        b.step(steps)
+        fa, fb = a.fields(), b.fields()
+        for k in NAMES:
+            nb = np.linalg.norm(fb[k])
+            assert np.linalg.norm(fa[k] - fb[k]) <= tol * (nb if nb > 0 else 1.0), (steps, k)
+    for x in (a, b):
+        x.close()
