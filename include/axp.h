@@ -403,7 +403,8 @@ axp_status axp_batch_results(axp_batch *batch, const int32_t *slots, int32_t n, 
  * state the batch advances).  Synchronises. */
 axp_status axp_batch_read_state(axp_batch *batch, int32_t slot, int32_t which, double *host_dst, size_t bytes);
 
-/* Time blocking: steps per launch, core cells per segment, threads per CTA.
+/* Time blocking: steps per launch, core cells per segment, threads per CTA
+ * (default 32, 1856, 256: a segment and its halo fill the block).
  * block_steps in [1, 256]; threads a multiple of 32 in [64, 512]; a work item
  * holds 8 cells per thread, so segment_cells + 6 block_steps <= 8 threads
  * (instances of up to 8 threads cells run whole). */

@@ -475,9 +475,10 @@ axp_status axp_batch_create(int32_t max_instances, int64_t max_cells, void *dev_
     std::memset(b->slots.data(), 0, sizeof(Slot) * max_instances);
     b->free.push_back({0, max_cells});
     b->dirty = true;
+    // default tiling: a segment and its halo fill a 256-thread block, two blocks per SM
     b->block_steps = 32;
-    b->segment_cells = 3584;
-    b->threads = 512;
+    b->segment_cells = 8 * 256 - 6 * 32;
+    b->threads = 256;
     b->use_graph = false;
     b->graph = nullptr;
     b->graph_steps = -1;
