@@ -12,7 +12,9 @@
 // neighbour value a stage reads along x was produced in an earlier iteration,
 // so each thread keeps its column's history along y in registers and publishes
 // only the values its x neighbours need into double-buffered shared rows at the
-// start of an iteration: one barrier per plane, no shared-memory rings.
+// start of an iteration: one barrier per plane, and no shared-memory rings for
+// the stages' results (the inputs and the y layer coefficients are staged ahead
+// in rings of their own, below).
 //
 // On the PML edges every quantity outside the grid is zero (the E/B closure and
 // the PML ghost of phi), so the edge version of the body only zeroes what it
