@@ -1,0 +1,70 @@
+"""The 2D pulse workload at its full size (4096 x 2048 cells), stepped by the
+grid API in the launch configuration the bench times, checked against the
+oracle on sampled sub-boxes.
+
+After N steps a cell depends only on cells within a few cells per step of it,
+so the oracle steps a 256 x 256 sub-box cut out of the same initial state.  Its
+cut sides get an absorbing layer like the grid's edges.  Its cells farther than
+layer + 3 N + 2 cells from every cut side (a conservative reach: the current's
+stencil adds one cell per step to the curls' two) must equal the full-size run's:
+1e-12 normwise in FP64 (the fused path's tolerance), 1e-4 in FP32 split.  Sides
+that lie on the grid's own edges keep their true layer.  The initial state is
+random, so every sub-box carries non-trivial fields, layers included."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2406_16796_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+NAMES = list(W.FIELD_NAMES) + ["phi_cur", "phi_old"]
+N_STEPS = 20
+S = 256  # sub-box edge, cells
+
+
+def boxes(nx, ny):
+    """(x0, y0) of the sampled sub-boxes: two corners, an x edge, the interior, the top edge."""
+    return [(0, 0), (nx - S, 0), (0, ny // 2 - S // 2), (nx // 2 - S // 2, ny // 2 - S // 2), (nx // 3, ny - S)]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_full_size_pulse_grid_matches_the_oracle_on_sub_boxes(prec):
+    from paper_2406_16796_gb300 import axp
+
+    w = W.pulse_2d(precision=prec)  # 4096 x 2048, PML of 20 cells on every side
+    grid = w.grid
+    nx, ny, L = grid.n[0], grid.n[1], grid.pml_cells
+    g = axp.Grid(grid)
+    # the workload's component set: laser (E0z; B0x, B0y), every order-1 array, phi
+    active = ["E0z", "B0x", "B0y"] + [n for n in W.FIELD_NAMES if n[1] == "1"]
+    g.load(W.random_state(grid, seed=20240624 + 1, active=active))
+    start = g.fields()
+    g.step(N_STEPS)
+    assert g.kernel_path() == axp.AXP_KERNEL_TM2D
+    end = g.fields()
+    g.close()
+    margin = L + 3 * N_STEPS + 2
+    tol = 1e-12 if prec == "fp64" else 1e-4
+    for x0, y0 in boxes(nx, ny):
+        sl = (0, slice(y0, y0 + S), slice(x0, x0 + S))
+        sub = grid.replace(n=(S, S, 1), precision="fp64")
+        og = oracle.OracleGrid(sub)
+        og.load({k: start[k][sl][None] for k in NAMES})
+        og.step(N_STEPS)
+        ref = og.fields()
+        # the exact region: away from the cut sides (a side on the grid's edge is not cut)
+        xlo = 0 if x0 == 0 else margin
+        xhi = S if x0 + S == nx else S - margin
+        ylo = 0 if y0 == 0 else margin
+        yhi = S if y0 + S == ny else S - margin
+        assert xhi - xlo >= 64 and yhi - ylo >= 64
+        for k in NAMES:
+            a = end[k][sl][ylo:yhi, xlo:xhi]
+            b = ref[k][0, ylo:yhi, xlo:xhi]
+            nb = np.linalg.norm(b)
+            if k in ("E0x", "E0y", "B0z"):  # outside the component set: stay zero
+                assert not np.any(a) and nb == 0, (x0, y0, k)
+                continue
+            assert nb > 0, (x0, y0, k)
+            assert np.linalg.norm(a - b) <= tol * nb, (prec, x0, y0, k, np.linalg.norm(a - b) / nb)
