@@ -451,3 +451,49 @@ def test_fused_odd_step_counts_keep_inactive_arrays_zero(steps):
     for k in NAMES:
         assert rel(got[k], ref[k]) < 1e-12, (steps, k, rel(got[k], ref[k]))
     g.close()
+
+
+TM_ACTIVE = ["E0z", "B0x", "B0y"] + [n for n in W.FIELD_NAMES if n[1] == "1"]
+BOX_ACTIVE = [n for n in W.FIELD_NAMES if n[1] == "1"]
+TINY = {
+    # name: (n, boundary on each active axis, pml cells, active arrays or None for all,
+    #        the kernel the automatic choice takes in FP64 and in FP32)
+    "1d_2": ((2, 1, 1), "periodic", 0, None, ("FUSED", "FUSED")),
+    "1d_7_pml": ((7, 1, 1), "pml", 2, None, ("FUSED", "FUSED")),
+    "2d_5x3_tm": ((5, 3, 1), "periodic", 0, TM_ACTIVE, ("TM2D", "TM2D")),
+    "2d_8x16_tm_pml": ((8, 16, 1), "pml", 2, TM_ACTIVE, ("TM2D", "TM2D")),
+    "2d_3x4_all": ((3, 4, 1), "periodic", 0, None, ("FUSED", "FUSED")),
+    "3d_3_box": ((3, 3, 3), "periodic", 0, BOX_ACTIVE, ("AX3D", "AX3D")),
+    "3d_2x3x4_box": ((2, 3, 4), "periodic", 0, BOX_ACTIVE, ("AX3D", "AX3D")),
+    "3d_4_all": ((4, 4, 4), "periodic", 0, None, ("GENERAL", "GENERAL")),  # rings too large: general
+}
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("case", sorted(TINY))
+def test_tiny_grids_match_the_oracle(case, prec):
+    """Degenerate sizes: grids of 2 to 16 cells per axis, far narrower than a tile,
+    whose halos wrap more than once around a periodic axis, on whichever kernel the
+    automatic choice takes and on the general path, against the oracle."""
+    axp = axp_mod()
+    n, bc, pml, active, paths = TINY[case]
+    b = W._bcs(*[bc if n[a] > 1 else "periodic" for a in range(3)])
+    grid = periodic_grid(n, B_ext=(0.3, -0.2, 0.9), m=1.3, g=0.6, axion_bc=b, em_bc=b, pml_cells=pml,
+                         precision=prec)
+    st = W.random_state(grid, seed=4321, active=active)
+    tol = 1e-12 if prec == "fp64" else 1e-4
+    for kernel in (axp.AXP_KERNEL_AUTO, axp.AXP_KERNEL_GENERAL):
+        g = axp.Grid(grid)
+        g.set_kernel(kernel)
+        g.load(st)
+        og = oracle.OracleGrid(grid.replace(precision="fp64"))
+        og.load(st)
+        g.step(5)
+        og.step(5)
+        if kernel == axp.AXP_KERNEL_AUTO:
+            want = paths[0 if prec == "fp64" else 1]
+            assert g.kernel_path() == getattr(axp, "AXP_KERNEL_" + want), (case, g.kernel_path(), want)
+        got, ref = g.fields(), og.fields()
+        for k in list(W.FIELD_NAMES) + ["phi_cur", "phi_old"]:
+            assert rel(got[k], ref[k]) <= tol, (case, kernel, k, rel(got[k], ref[k]))
+        g.close()
