@@ -209,3 +209,27 @@ def test_batched_results_equal_the_per_slot_results():
         b.results([slots[0], slots[1]])
     assert e.value.status == axp.AXP_E_INVAL
     b.close()
+
+
+@pytest.mark.parametrize("tiling", [(32, 1856, 256), (8, 4000, 512)])
+def test_smallest_instances_match_the_oracle(tiling):
+    """Instances of 8 to 33 cells: one to five threads hold cells (the last with a
+    partial run of fewer than 8), the periodic neighbours wrap within those threads,
+    and the rest of the block is idle."""
+    B = batch_mod()
+    steps = 90
+    insts = [inst(nx=n, m=0.4 * j, g=2e-2, By=1.0, Bz=0.3 * j, steps=steps, waves=1)
+             for j, n in enumerate((8, 9, 13, 16, 17, 33))]
+    b = B.Batch(8, 200)
+    b.set_tiling(*tiling)
+    slots = [b.add(i) for i in insts]
+    b.run(steps)
+    for i, s, d in zip(insts, slots, b.results(slots)):
+        og = oracle_run(i, steps)
+        ref = og.fields()
+        got = {"B0z": b.read_state(s, 1), "B1y": b.read_state(s, 4), "B1z": b.read_state(s, 5),
+               "phi_cur": b.read_state(s, 6)}
+        for k, v in got.items():
+            assert rel(v, ref[k].ravel()) < 1e-4, (int(i.nx), k, rel(v, ref[k].ravel()))
+        assert d["P_g2a"] == pytest.approx(og.diagnostics()["P_g2a"], rel=1e-3), int(i.nx)
+    b.close()
