@@ -309,10 +309,11 @@ axp_status axp_get_window_offset(const axp_grid *grid, int64_t *cells);
  * time scheme, in the oracle's operation order); AXP_KERNEL_FUSED forces the
  * generic single-pass kernel (1D/2D/3D, periodic, reflect and PML edges);
  * AXP_KERNEL_TM2D forces the single-pass kernel specialised for 2D grids with
- * an (E0z; B0x, B0y) laser and periodic or PML edges; AXP_KERNEL_AX3D forces
- * the single-pass kernel specialised for periodic 3D grids with no laser
- * fields and no uniform E (an axion wave in a uniform B).  Forcing a kernel
- * that does not support the grid makes axp_step return AXP_E_STATE. */
+ * an (E0z; B0x, B0y) laser and periodic or PML edges (at most 2^32 cells);
+ * AXP_KERNEL_AX3D forces the single-pass kernel specialised for periodic 3D
+ * grids with no laser fields and no uniform E (an axion wave in a uniform B).
+ * Forcing a kernel that does not support the grid makes axp_step return
+ * AXP_E_STATE. */
 typedef enum {
     AXP_KERNEL_AUTO = 0,
     AXP_KERNEL_GENERAL = 1,

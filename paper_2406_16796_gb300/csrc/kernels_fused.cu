@@ -98,8 +98,9 @@ bool ax3d_supported(const axp_grid *g)
 
 // The 2D kernel specialised for the (E0z; B0x, B0y) laser: 2D grid, order-0
 // closure inside that set, every non-periodic side absorbing for both E/B and
-// the axion, no uniform background E.  A soft source is taken when it drives
-// E0z only (its polarisation along z keeps the closure inside the set).
+// the axion, no uniform background E, at most 2^32 cells.  A soft source is
+// taken when it drives E0z only (its polarisation along z keeps the closure
+// inside the set).
 bool tm2d_supported(const axp_grid *g)
 {
     if (grid_mode(g) != 2) return false;
@@ -111,7 +112,7 @@ bool tm2d_supported(const axp_grid *g)
         for (int s = 0; s < 2; s++)
             if (g->desc.axion_bc[a][s] != AXP_BC_PML || g->desc.em_bc[a][s] != AXP_BC_PML) return false;
     }
-    return true;
+    return (int64_t)g->desc.n[0] * g->desc.n[1] <= ((int64_t)1 << 32);  // 32-bit element offsets
 }
 
 template <typename T>

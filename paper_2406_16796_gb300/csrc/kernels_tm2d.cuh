@@ -194,16 +194,14 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
     T PX3 = 0, PX4 = 0, PY3 = 0, PY4 = 0;
     const int t0 = m0 - 2, t1 = m1 + 3;
 
-    auto gidx = [&](int p) -> int64_t {
-        int wp = p;
-        if (wp < 0 || wp >= ny) wp = pery ? ((wp % ny) + ny) % ny : -1;
-        return (wx < 0 || wp < 0) ? (int64_t)-1 : (int64_t)wx + (int64_t)nx * wp;
-    };
+    // Element offsets within an array are 32-bit: the host takes this kernel only
+    // for grids of at most 2^32 cells.
     auto prefetch = [&](int p) {
         fill_y(p);
-        const int64_t gi = gidx(p);
-        const bool ok = gi >= 0;
-        const int64_t o = ok ? gi : 0;
+        int wp = p;
+        if (wp < 0 || wp >= ny) wp = pery ? ((wp % ny) + ny) % ny : -1;
+        const bool ok = wx >= 0 && wp >= 0;
+        const unsigned o = ok ? (unsigned)wx + (unsigned)nx * (unsigned)wp : 0u;
         T *st = stage + ((p - t0) & (NS - 1)) * (NIN * ntx) + tx * NIN;
         cp_elem(st + 0, P.Ein[2] + o, ok);
         cp_elem(st + 1, P.Ein[3] + o, ok);
@@ -295,7 +293,7 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
             if (src_b_col) N0y1 = fma(-yring[p & (YR - 1)][Y_W], P.src_b, N0y1);
             if (EDGE && !in) N0x1 = N0y1 = N1x1 = N1y1 = N1z1 = T(0);
             if (write_col && p >= m0 && p < m1) {
-                const int64_t gi = (int64_t)gx + (int64_t)nx * p;
+                const unsigned gi = (unsigned)gx + (unsigned)nx * (unsigned)p;
                 P.Bout[0][gi] = N0x1;
                 P.Bout[1][gi] = N0y1;
                 P.Bout[3][gi] = N1x1;
@@ -352,7 +350,7 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
                 DF2 = nw - ph2;
             }
             if (write_col && p >= m0 && p < m1) {
-                const int64_t gi = (int64_t)gx + (int64_t)nx * p;
+                const unsigned gi = (unsigned)gx + (unsigned)nx * (unsigned)p;
                 P.phi_out[gi] = nw;
                 if (INCR) P.phib_out[gi] = pin;
             }
@@ -420,7 +418,7 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
                     }
                 }
                 if (write_col) {
-                    const int64_t gi = (int64_t)gx + (int64_t)nx * p;
+                    const unsigned gi = (unsigned)gx + (unsigned)nx * (unsigned)p;
                     P.Eout[3][gi] = ex;
                     P.Eout[4][gi] = ey;
                     P.Eout[5][gi] = ez;
