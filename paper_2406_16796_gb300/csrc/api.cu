@@ -288,6 +288,7 @@ View<T> make_view_eset(axp_grid *g, int eset)
     v.h = (T)(d.dt / 2.0);
     v.g = (T)d.g;
     v.m2 = (T)(d.m * d.m);
+    set_reciprocals(v);
     return v;
 }
 

@@ -8,6 +8,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
+
 #include "axp.h"
 
 namespace axp {
@@ -30,6 +32,10 @@ struct View {
     int64_t n[3];
     int64_t N;
     T d[3];
+    // 1/d, 1/(2d) and 1/d^2 per axis where d is a power of two, else 0.  Then
+    // x / d and x * (1/d) are the same correctly rounded value, and the general
+    // kernels multiply; otherwise they divide (set by set_reciprocals).
+    T rd[3], rd2[3], rdd[3];
     T lo[3];
     T dt, h;     // h = dt / 2
     T g, m2;
@@ -42,6 +48,25 @@ struct View {
     int vaxis;
     int64_t vlo, vhi, Nv;
 };
+
+// The exact reciprocals of View::rd, rd2 and rdd, from v.d: kept only where
+// both the divisor and its reciprocal are normal numbers and their product is
+// exactly 1 (d a power of two), so that multiplying gives the division's bits.
+template <typename T>
+inline void set_reciprocals(View<T> &v)
+{
+    auto exact = [](T den) -> T {
+        int e = 0;
+        if (!(den > T(0)) || !std::isnormal(den) || std::frexp(den, &e) != T(0.5)) return T(0);
+        const T r = T(1) / den;
+        return std::isnormal(r) && r * den == T(1) ? r : T(0);
+    };
+    for (int a = 0; a < 3; a++) {
+        v.rd[a] = exact(v.d[a]);
+        v.rd2[a] = exact(T(2) * v.d[a]);
+        v.rdd[a] = exact(v.d[a] * v.d[a]);
+    }
+}
 
 struct Workspace {
     size_t off_fields[2][kFields];  // two field sets: the fused step reads one and writes the other

@@ -30,6 +30,25 @@ __host__ __device__ inline int64_t lin3(const int64_t n[3], int64_t i, int64_t j
     return i + n[0] * (j + n[1] * k);
 }
 
+// x / d_a, x / (2 d_a) and x / d_a^2: a multiplication by the exact reciprocal
+// where the view holds one (d_a a power of two: the same correctly rounded
+// value as the division), else the division itself.
+template <typename T>
+__device__ __forceinline__ T over_d(const View<T> &v, T x, int a)
+{
+    return v.rd[a] != T(0) ? x * v.rd[a] : x / v.d[a];
+}
+template <typename T>
+__device__ __forceinline__ T over_2d(const View<T> &v, T x, int a)
+{
+    return v.rd2[a] != T(0) ? x * v.rd2[a] : x / (T(2) * v.d[a]);
+}
+template <typename T>
+__device__ __forceinline__ T over_dd(const View<T> &v, T x, int a)
+{
+    return v.rdd[a] != T(0) ? x * v.rdd[a] : x / (v.d[a] * v.d[a]);
+}
+
 // Linear index after periodic wrap (offsets of at most one period), or -1 when
 // the point lies outside the grid along a non-periodic axis.
 template <typename T>

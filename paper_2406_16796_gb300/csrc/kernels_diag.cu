@@ -36,16 +36,21 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_partial(View<T> v, PhiPai
         phi_mid_dt<T, INCR>(v, q, i, j, k, &midT, &DtT);
         const double mid = midT, Dt = DtT;
         double g2 = 0.0, R = 0.0, bg = 0.0;
+        // divisions by d and 2d (a multiplication where the reciprocal is exact)
+        auto od = [&](double x, int a) { return v.rd[a] != T(0) ? x * (double)v.rd[a] : x / (double)v.d[a]; };
+        auto o2d = [&](double x, int a) {
+            return v.rd2[a] != T(0) ? x * (double)v.rd2[a] : x / (2.0 * (double)v.d[a]);
+        };
         for (int a = 0; a < 3; a++) {
             int64_t u[3];
             unit(a, u);
             const double up = (double)phi_mid<T, INCR>(v, q, i + u[0], j + u[1], k + u[2]);
             const double dn = (double)phi_mid<T, INCR>(v, q, i - u[0], j - u[1], k - u[2]);
-            const double fw = (up - mid) / (double)v.d[a];
+            const double fw = od(up - mid, a);
             g2 += fw * fw;
             const T *E1 = v.f[kE1 + a];
-            R += ((double)E1[c] - (double)ld(v, E1, i - u[0], j - u[1], k - u[2])) / (double)v.d[a];
-            bg += (double)b0_bar(v, a, i, j, k) * ((up - dn) / (2.0 * (double)v.d[a]));
+            R += od((double)E1[c] - (double)ld(v, E1, i - u[0], j - u[1], k - u[2]), a);
+            bg += (double)b0_bar(v, a, i, j, k) * o2d(up - dn, a);
         }
         R += (double)v.g * bg;
         acc[0] += 0.5 * ((Dt * Dt + g2) + m2 * mid * mid) * dV;
@@ -267,6 +272,7 @@ extern "C" axp_status axp_diagnostics_noalloc(const axp_grid_desc *desc, const d
     v.h = desc->dt / 2.0;
     v.g = desc->g;
     v.m2 = desc->m * desc->m;
+    set_reciprocals(v);
     PhiPair<double, false> q;
     memset(&q, 0, sizeof(q));
     q.hi = v.phi_cur;

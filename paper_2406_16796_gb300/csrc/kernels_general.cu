@@ -36,12 +36,14 @@ __device__ T p_comp(const View<T> &v, const PhiPair<T, INCR> &q, int a, int64_t 
     unit(c, uc);
     T mid, Dt;
     phi_mid_dt<T, INCR>(v, q, i, j, k, &mid, &Dt);
-    const T dphi_c = (phi_mid<T, INCR>(v, q, i + uc[0], j + uc[1], k + uc[2]) -
-                      phi_mid<T, INCR>(v, q, i - uc[0], j - uc[1], k - uc[2])) /
-                     (T(2) * v.d[c]);
-    const T dphi_b = (phi_mid<T, INCR>(v, q, i + ub[0], j + ub[1], k + ub[2]) -
-                      phi_mid<T, INCR>(v, q, i - ub[0], j - ub[1], k - ub[2])) /
-                     (T(2) * v.d[b]);
+    const T dphi_c = over_2d(v,
+                             phi_mid<T, INCR>(v, q, i + uc[0], j + uc[1], k + uc[2]) -
+                                 phi_mid<T, INCR>(v, q, i - uc[0], j - uc[1], k - uc[2]),
+                             c);
+    const T dphi_b = over_2d(v,
+                             phi_mid<T, INCR>(v, q, i + ub[0], j + ub[1], k + ub[2]) -
+                                 phi_mid<T, INCR>(v, q, i - ub[0], j - ub[1], k - ub[2]),
+                             b);
     const T cross = e0_bar(v, b, i, j, k) * dphi_c - e0_bar(v, c, i, j, k) * dphi_b;
     return Dt * b0_bar(v, a, i, j, k) - cross;
 }
@@ -129,13 +131,13 @@ template <typename T>
 __device__ __forceinline__ T curl_b(const View<T> &v, T *const B[3], int a, int64_t i, int64_t j, int64_t k)
 {
     if (a == 0)
-        return (ld(v, B[2], i, j, k) - ld(v, B[2], i, j - 1, k)) / v.d[1] -
-               (ld(v, B[1], i, j, k) - ld(v, B[1], i, j, k - 1)) / v.d[2];
+        return over_d(v, ld(v, B[2], i, j, k) - ld(v, B[2], i, j - 1, k), 1) -
+               over_d(v, ld(v, B[1], i, j, k) - ld(v, B[1], i, j, k - 1), 2);
     if (a == 1)
-        return (ld(v, B[0], i, j, k) - ld(v, B[0], i, j, k - 1)) / v.d[2] -
-               (ld(v, B[2], i, j, k) - ld(v, B[2], i - 1, j, k)) / v.d[0];
-    return (ld(v, B[1], i, j, k) - ld(v, B[1], i - 1, j, k)) / v.d[0] -
-           (ld(v, B[0], i, j, k) - ld(v, B[0], i, j - 1, k)) / v.d[1];
+        return over_d(v, ld(v, B[0], i, j, k) - ld(v, B[0], i, j, k - 1), 2) -
+               over_d(v, ld(v, B[2], i, j, k) - ld(v, B[2], i - 1, j, k), 0);
+    return over_d(v, ld(v, B[1], i, j, k) - ld(v, B[1], i - 1, j, k), 0) -
+           over_d(v, ld(v, B[0], i, j, k) - ld(v, B[0], i, j - 1, k), 1);
 }
 
 // (curl E)_a at the B_a location: forward differences.
@@ -143,13 +145,13 @@ template <typename T>
 __device__ __forceinline__ T curl_e(const View<T> &v, T *const E[3], int a, int64_t i, int64_t j, int64_t k)
 {
     if (a == 0)
-        return (ld(v, E[2], i, j + 1, k) - ld(v, E[2], i, j, k)) / v.d[1] -
-               (ld(v, E[1], i, j, k + 1) - ld(v, E[1], i, j, k)) / v.d[2];
+        return over_d(v, ld(v, E[2], i, j + 1, k) - ld(v, E[2], i, j, k), 1) -
+               over_d(v, ld(v, E[1], i, j, k + 1) - ld(v, E[1], i, j, k), 2);
     if (a == 1)
-        return (ld(v, E[0], i, j, k + 1) - ld(v, E[0], i, j, k)) / v.d[2] -
-               (ld(v, E[2], i + 1, j, k) - ld(v, E[2], i, j, k)) / v.d[0];
-    return (ld(v, E[1], i + 1, j, k) - ld(v, E[1], i, j, k)) / v.d[0] -
-           (ld(v, E[0], i, j + 1, k) - ld(v, E[0], i, j, k)) / v.d[1];
+        return over_d(v, ld(v, E[0], i, j, k + 1) - ld(v, E[0], i, j, k), 2) -
+               over_d(v, ld(v, E[2], i + 1, j, k) - ld(v, E[2], i, j, k), 0);
+    return over_d(v, ld(v, E[1], i + 1, j, k) - ld(v, E[1], i, j, k), 0) -
+           over_d(v, ld(v, E[0], i, j + 1, k) - ld(v, E[0], i, j, k), 1);
 }
 
 // E half-step: orders selected by the mask (bit 0 = order 0, bit 1 = order 1);
@@ -227,7 +229,7 @@ __global__ void __launch_bounds__(kThreads) k_axion(View<T> v, Ghosts<T> gcur)
             const T dn = ld_phi(v, v.phi_cur, gcur, i - u[0], j - u[1], k - u[2]);
             // FP32 split: from neighbour differences, which do not round against 2*phi
             const T d2 = INCR ? (up - ph) + (dn - ph) : (up + dn) - T(2) * ph;
-            lap = lap + d2 / (v.d[a] * v.d[a]);
+            lap = lap + over_dd(v, d2, a);
         }
         const T sig = sigma_of<T>(v.sig_ax, i, j, k);
         if (!INCR) {

@@ -75,6 +75,13 @@ CASES = {
                                em_bc=W._bcs("pml", ("reflect", "pml")), pml_cells=5),
     "3d_mixed": dict(n=(14, 12, 10), B_ext=(0.5, 0.2, 0.3), axion_bc=W._bcs("outflow", "periodic", "pml"),
                      em_bc=W._bcs("pml", "periodic", "reflect"), pml_cells=3),
+    # power-of-two cell sizes: the general kernels multiply by the exact reciprocals
+    # instead of dividing, which must leave every bit as the oracle's divisions give it
+    "2d_pml_pow2": dict(n=(48, 40, 1), d=(1 / 32, 1 / 32, 1 / 32), B_ext=(0.0, 0.0, 1.0),
+                        axion_bc=W._bcs("pml", "pml"), em_bc=W._bcs("pml", "pml"), pml_cells=6),
+    "3d_mixed_pow2": dict(n=(14, 12, 10), d=(0.0625, 0.125, 0.03125), B_ext=(0.5, 0.2, 0.3),
+                          E_ext=(0.05, 0.0, -0.1), axion_bc=W._bcs("outflow", "periodic", "pml"),
+                          em_bc=W._bcs("pml", "periodic", "reflect"), pml_cells=3),
 }
 
 
@@ -98,7 +105,7 @@ def test_general_fp64_bitwise_vs_oracle(case):
     g.close()
 
 
-@pytest.mark.parametrize("case", ["1d_periodic", "2d_pml", "3d_mixed"])
+@pytest.mark.parametrize("case", ["1d_periodic", "2d_pml", "3d_mixed", "3d_mixed_pow2"])
 def test_fp32_split_vs_oracle(case):
     grid = periodic_grid(g=0.7, m=1.1, **CASES[case])
     st = W.random_state(grid, seed=102)
