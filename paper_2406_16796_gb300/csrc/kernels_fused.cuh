@@ -646,6 +646,14 @@ struct Kernel {
 template <typename T, bool INCR, int MODE, int E0M, int B0M>
 __global__ void __launch_bounds__(Tile<T, MODE>::NT) k_fused(Params<T> P)
 {
+    if (MODE == 1) {
+        // 1D steps are launched as programmatic dependents of the step before:
+        // the grid may be scheduled while that one drains, and waits here, before
+        // touching any global memory, until it has completed and its writes are
+        // visible; it then lets the next step's grid be scheduled in turn
+        asm volatile("griddepcontrol.wait;\n" ::: "memory");
+        asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+    }
     extern __shared__ __align__(16) unsigned char smraw[];
     // the rings sit between two guard bands of kGuard elements, which absorb the
     // one-cell neighbour reads of the tile's outermost cells
@@ -685,6 +693,21 @@ cudaError_t launch(const Params<T> &P, int nchunks, cudaStream_t stream, int *oc
     if (MODE == 3) {
         grid.y = (P.n[1] + TL::VY - 1) / TL::VY;
         grid.z = nchunks;
+    }
+    if (MODE == 1) {
+        // a 1D step is a few microseconds of work: overlap its launch with the
+        // previous step's tail (programmatic dependent launch, also inside graphs)
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = grid;
+        cfg.blockDim = block;
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, kern, P);
     }
     kern<<<grid, block, smem, stream>>>(P);
     return cudaGetLastError();
