@@ -38,8 +38,7 @@ namespace {
 
 constexpr int kArr = 6 + 2;   // E0y B0z E1y E1z B1y B1z phi pi (global, per buffer)
 constexpr int kK = 8;         // consecutive cells per thread (held in registers)
-constexpr int kMaxThreads = 512;
-constexpr int kCapCells = kK * kMaxThreads;  // cells per work item at most
+constexpr int kMaxThreads = 512;  // a work item spans at most kK * kMaxThreads cells
 
 struct Slot {
     int64_t off;        // first cell of this instance in every pool array
@@ -99,7 +98,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_batch_block(Dev D, int budget, 
     __shared__ float fMID[kMaxThreads], lMID[kMaxThreads];
     __shared__ float fPH[2][kMaxThreads], lPH[2][kMaxThreads];  // by step parity
     __shared__ int s_item;
-    const int nt = blockDim.x, t = threadIdx.x;
+    const int t = threadIdx.x;
     for (;;) {
         if (t == 0) s_item = atomicAdd(D.counter, 1);
         __syncthreads();
