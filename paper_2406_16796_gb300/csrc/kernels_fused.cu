@@ -331,10 +331,11 @@ cudaError_t fused_step(axp_grid *g, int64_t nsteps, bool *handled)
     } else if (tm) {
         // Tile width and march chunks: the fewest resident-block waves for the work
         // a wave does, (planes + pipeline) x columns x blocks per SM, divided by the
-        // share of its issue rate an SM reaches with that many warps resident (below
-        // 8 warps the FP64 pipe's and the loads' latencies are no longer hidden:
-        // sqrt(warps / 8), from measured tile widths; kOneBlock for one block per SM).  Measured per-CTA times give
-        // the other two costs: a strip at a non-periodic x edge runs the edge body
+        // share of its issue rate an SM reaches with that many warps resident.  FP64:
+        // below 8 warps the FP64 pipe's and the loads' latencies are no longer
+        // hidden, sqrt(warps / 8); FP32: warps / 16, and kManyBlocks beyond two blocks
+        // per SM; kOneBlock for one block per SM (all from measured tile widths).
+        // Measured per-CTA times give the other two costs: a strip at a non-periodic x edge runs the edge body
         // over the x layer and takes kEdgeCost times as long per plane (its warps
         // wait at each plane's barrier for the layer's warp), and a chunk that
         // crosses a y layer runs the edge body over the layer and the pipeline's
@@ -346,6 +347,7 @@ cudaError_t fused_step(axp_grid *g, int64_t nsteps, bool *handled)
         // A lone block per SM has nothing else to issue while its warps wait at a
         // plane's barrier: two blocks of half the width ran the 2D pulse 7% faster.
         const double kOneBlock = 0.92;
+        const double kManyBlocks = 0.7;  // FP32 with more than two blocks per SM (measured above)
         const double kLayerCost = sizeof(T) == 8 ? 0.93 : 0.32;
         int sms = 152;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
@@ -374,6 +376,13 @@ cudaError_t fused_step(axp_grid *g, int64_t nsteps, bool *handled)
             o = o > 0 ? o : 1;
             const double warps = (double)o * tx / 32.0;
             double u = warps >= 8.0 ? 1.0 : std::sqrt(warps / 8.0);
+            if (sizeof(T) == 4) {
+                // FP32 waits on memory, and more warps hide more of it: two 256-wide blocks
+                // per SM (16 warps) beat 224 and 192 by 1-8% on 2048^2 to 8192 x 4096 grids,
+                // while three or four narrower blocks per SM ran 15-30% slower
+                u = std::min(warps, 16.0) / 16.0;
+                if (o > 2) u *= kManyBlocks;
+            }
             if (o < 2) u *= kOneBlock;
             const int64_t strips = (nx + (tx - tm2d::HL - tm2d::HR) - 1) / (tx - tm2d::HL - tm2d::HR);
             const int64_t slots = (int64_t)sms * o;

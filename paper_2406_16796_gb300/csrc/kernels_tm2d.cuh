@@ -41,12 +41,14 @@ constexpr int RS = TX + 2;  // row stride: one guard element on each side
 // thread's 11 values together: an odd stride, so a warp's accesses fall in
 // distinct banks) and sized for the launch's tile width.
 //
-// Planes in the staging ring (a power of two): FP32 keeps 7 planes of loads in
-// flight (its two blocks per SM left HBM latency-bound with 3), FP64 3.
+// Planes in the staging ring (a power of two): 3 planes of loads in flight.  In
+// FP32 that is with two 256-wide blocks per SM (16 warps); 7 planes took 226 KB
+// of shared memory per SM for two such blocks, leaving too little L1, and ran
+// 13% slower than 3.
 template <typename T>
 __host__ __device__ constexpr int ns()
 {
-    return sizeof(T) == 4 ? 8 : 4;
+    return 4;
 }
 constexpr int NIN = 11;  // input arrays per plane
 
