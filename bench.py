@@ -234,9 +234,9 @@ def bytes_per_cell(prec):
 # one-pass stencil grows with the cells); None until a capture of the kernel as
 # it stands exists.  Sources are summarised under profiles/.
 TRAFFIC = {
-    # k_tm2d, 2048 x 2048 captures: FP64 688.8 MB, FP32 split 338.3 MB per launch
+    # k_tm2d, 2048 x 2048 captures: FP64 688.8 MB, FP32 split 344.2 MB per launch
     ("k_tm2d (one launch per step)", "fp64"): 688.8e6 * (4096 * 2048) / (2048 * 2048),
-    ("k_tm2d (one launch per step)", "fp32"): 338.3e6 * (4096 * 2048) / (2048 * 2048),
+    ("k_tm2d (one launch per step)", "fp32"): 344.2e6 * (4096 * 2048) / (2048 * 2048),
 }
 # k_ax3d (3D, no order-0 fields), 256^3 capture: 1076.3 MB per launch
 TRAFFIC_3D_PER_CELL = 1076.3e6 / 256 ** 3
