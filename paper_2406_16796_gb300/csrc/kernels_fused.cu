@@ -347,7 +347,7 @@ cudaError_t fused_step(axp_grid *g, int64_t nsteps, bool *handled)
         // A lone block per SM has nothing else to issue while its warps wait at a
         // plane's barrier: two blocks of half the width ran the 2D pulse 7% faster.
         const double kOneBlock = 0.92;
-        const double kManyBlocks = 0.7;  // FP32 with more than two blocks per SM (measured above)
+        const double kManyBlocks = 0.7;  // FP32 with more than two blocks per SM (the FP32 rule below)
         const double kLayerCost = sizeof(T) == 8 ? 0.93 : 0.32;
         int sms = 152;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
