@@ -5,8 +5,8 @@ oracle on sampled sub-boxes.
 After N steps a cell depends only on cells within a few cells per step of it,
 so the oracle steps a 256 x 256 sub-box cut out of the same initial state.  Its
 cut sides get an absorbing layer like the grid's edges.  Its cells farther than
-layer + 3 N + 2 cells from every cut side (a conservative reach: the current's
-stencil adds one cell per step to the curls' two) must equal the full-size run's:
+layer + 3 N + 2 cells from every cut side (a generous margin: one step's reach is
+one cell, and the axion current's stencil adds two once) must equal the full-size run's:
 1e-12 normwise in FP64 (the fused path's tolerance), 1e-4 in FP32 split.  Sides
 that lie on the grid's own edges keep their true layer.  The initial state is
 random, so every sub-box carries non-trivial fields, layers included."""
