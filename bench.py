@@ -164,6 +164,45 @@ def omp_threads():
     return int(v) if v else (os.cpu_count() or 1)
 
 
+def cpu_model():
+    """The host CPU's model name (/proc/cpuinfo, else lscpu, else the machine type)."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+
+    return platform.machine()
+
+
+def oracle_rate_one_thread(args, rows=64, steps=2):
+    """The oracle's rate on one thread: a fresh process with OMP_NUM_THREADS=1 (the
+    OpenMP runtime reads it once, at load) steps a strip of the bench grid."""
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+            "from paper_2406_16796_gb300 import workloads as W; "
+            "w = W.pulse_2d(nx=%d, ny=%d, precision='fp64'); "
+            "r, s, g = bench.oracle_rate(w, %d, rows=%d); print(json.dumps([r, s, g.n[0], g.n[1]]))"
+            % (os.path.dirname(os.path.abspath(__file__)), args.nx, args.ny, steps, rows))
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
+        rate, sec, nx, ny = json.loads(out.stdout.strip().splitlines()[-1])
+    except (OSError, subprocess.SubprocessError, ValueError, IndexError):
+        return None
+    return {"value": rate, "unit": "cell-updates/s", "cores": 1,
+            "sample": "%d oracle steps of a %dx%d strip of the grid (%.1f s)" % (steps, nx, ny, sec)}
+
+
 def reference_arm(args):
     rank, world, local = dist_env()
     from paper_2406_16796_gb300 import workloads as W
@@ -192,7 +231,7 @@ def reference_arm(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w.name, "cells": w.grid.cells, "precision": "fp64", "parallelism": "replicas"},
             "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": omp_threads(), "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -629,7 +668,8 @@ def gpu_arm(args):
         wb = workload(args, "fp64")
         rate, sec, gsp = oracle_rate(wb, steps=2)
         cpu = {"value": rate, "unit": "cell-updates/s", "cores": omp_threads(), "kind": "oracle",
-               "sample": "2 oracle steps of the full %dx%d grid (%.1f s)" % (gsp.n[0], gsp.n[1], sec)}
+               "sample": "2 oracle steps of the full %dx%d grid (%.1f s)" % (gsp.n[0], gsp.n[1], sec),
+               "cpu_model": cpu_model(), "single_thread": oracle_rate_one_thread(args)}
     line = {"metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32", "data": "synthetic",
