@@ -665,11 +665,13 @@ def gpu_arm(args):
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
+        # about 10 s of the oracle on every host core, then about 5 s on one
         wb = workload(args, "fp64")
-        rate, sec, gsp = oracle_rate(wb, steps=2)
+        csteps = 10
+        rate, sec, gsp = oracle_rate(wb, steps=csteps)
         cpu = {"value": rate, "unit": "cell-updates/s", "cores": omp_threads(), "kind": "oracle",
-               "sample": "2 oracle steps of the full %dx%d grid (%.1f s)" % (gsp.n[0], gsp.n[1], sec),
-               "cpu_model": cpu_model(), "single_thread": oracle_rate_one_thread(args)}
+               "sample": "%d oracle steps of the full %dx%d grid (%.1f s)" % (csteps, gsp.n[0], gsp.n[1], sec),
+               "cpu_model": cpu_model(), "single_thread": oracle_rate_one_thread(args, rows=64, steps=10)}
     line = {"metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32", "data": "synthetic",
