@@ -423,6 +423,7 @@ axp_status axp_workspace_bytes(const axp_grid_desc *desc, size_t *bytes)
 axp_status axp_create_grid(const axp_grid_desc *desc, void *dev_workspace, size_t bytes, void *cuda_stream,
                            axp_grid **out)
 {
+    axp::TraceRange trace_("axp_create_grid");
     if (!out || !dev_workspace) return AXP_E_INVAL;
     *out = nullptr;
     axp_status st = validate(desc);
@@ -496,6 +497,7 @@ axp_status axp_set_background_field(axp_grid *g, const double B_ext[3], const do
 
 axp_status axp_inject_laser(axp_grid *g, const axp_laser_desc *L)
 {
+    axp::TraceRange trace_("axp_inject_laser");
     if (!g || !L) return AXP_E_INVAL;
     if (g->group) return AXP_E_STATE;
     g->cfg_version++;
@@ -563,6 +565,7 @@ axp_status axp_set_soft_source(axp_grid *g, const axp_source_desc *q)
 
 axp_status axp_inject_axion(axp_grid *g, const axp_axion_desc *A)
 {
+    axp::TraceRange trace_("axp_inject_axion");
     if (!g || !A) return AXP_E_INVAL;
     if (g->group) return AXP_E_STATE;
     g->cfg_version++;
@@ -625,6 +628,7 @@ static bool window_axis_ok(const axp_grid *g, int32_t axis)
 
 axp_status axp_step(axp_grid *g, int64_t nsteps)
 {
+    axp::TraceRange trace_("axp_step");
     if (!g || nsteps < 0) return AXP_E_INVAL;
     if (g->group) return AXP_E_STATE;
     if (nsteps == 0) return AXP_OK;
@@ -698,6 +702,7 @@ axp_status axp_synchronize(axp_grid *g)
 
 axp_status axp_read_diagnostics(axp_grid *g, axp_diag *out, int64_t max, int64_t *n)
 {
+    axp::TraceRange trace_("axp_read_diagnostics");
     if (!g || !n || max < 0 || (max > 0 && !out)) return AXP_E_INVAL;
     if (g->group) return AXP_E_STATE;
     *n = 0;
@@ -721,6 +726,7 @@ axp_status axp_read_diagnostics(axp_grid *g, axp_diag *out, int64_t max, int64_t
 
 axp_status axp_compute_diagnostics(axp_grid *g, axp_diag *out)
 {
+    axp::TraceRange trace_("axp_compute_diagnostics");
     if (!g || !out) return AXP_E_INVAL;
     if (g->group) return AXP_E_STATE;
     axp_diag *dst = scratch_slot(g);
@@ -874,6 +880,7 @@ axp_status axp_state_bytes(const axp_grid *g, size_t *bytes)
 
 axp_status axp_save_state(axp_grid *g, void *dst, size_t bytes)
 {
+    axp::TraceRange trace_("axp_save_state");
     size_t need;
     if (!g || !dst || axp_state_bytes(g, &need) != AXP_OK || bytes != need) return AXP_E_INVAL;
     if (g->group) return AXP_E_STATE;
@@ -912,6 +919,7 @@ axp_status axp_save_state(axp_grid *g, void *dst, size_t bytes)
 
 axp_status axp_load_state(axp_grid *g, const void *src, size_t bytes)
 {
+    axp::TraceRange trace_("axp_load_state");
     size_t need;
     if (!g || !src || axp_state_bytes(g, &need) != AXP_OK || bytes != need) return AXP_E_INVAL;
     if (g->group) return AXP_E_STATE;

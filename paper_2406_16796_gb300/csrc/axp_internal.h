@@ -10,6 +10,8 @@
 
 #include <cmath>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "axp.h"
 
 namespace axp {
@@ -47,6 +49,16 @@ struct View {
     // vaxis lies in [vlo, vhi); Nv of them
     int vaxis;
     int64_t vlo, vhi, Nv;
+};
+
+// A named NVTX range over one entry point of the C ABI: a span on a profiler's
+// timeline (nsys, ncu's range filters); without a tool attached it costs a
+// check of an unset function pointer.
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
 };
 
 // The exact reciprocals of View::rd, rd2 and rdd, from v.d: kept only where

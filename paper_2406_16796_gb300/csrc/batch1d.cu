@@ -507,6 +507,7 @@ axp_status axp_batch_destroy(axp_batch *b)
 
 axp_status axp_batch_add(axp_batch *b, const axp_batch_instance *in, int32_t *slot)
 {
+    axp::TraceRange trace_("axp_batch_add");
     if (!b || !in || !slot) return AXP_E_INVAL;
     if (in->nx < 8 || in->nx > (1 << 30) || !(in->dx > 0) || !(in->dt > 0) || in->steps < 0 || !std::isfinite(in->g) ||
         !std::isfinite(in->m) || !std::isfinite(in->By) || !std::isfinite(in->Bz) || !std::isfinite(in->amplitude) ||
@@ -649,6 +650,7 @@ static cudaError_t enqueue_run(axp_batch *b, int64_t nsteps)
 
 axp_status axp_batch_run(axp_batch *b, int64_t nsteps)
 {
+    axp::TraceRange trace_("axp_batch_run");
     if (!b || nsteps < 0) return AXP_E_INVAL;
     if (nsteps == 0) return AXP_OK;
     if (b->dirty) {
@@ -713,6 +715,7 @@ axp_status axp_batch_progress(axp_batch *b, int64_t *steps_done, int32_t max_slo
 
 axp_status axp_batch_results(axp_batch *b, const int32_t *slots, int32_t n, axp_diag *out)
 {
+    axp::TraceRange trace_("axp_batch_results");
     if (!b || !slots || !out || n < 1 || n > b->max_instances) return AXP_E_INVAL;
     for (int32_t q = 0; q < n; q++)
         if (slots[q] < 0 || slots[q] >= b->max_instances || !b->slots[slots[q]].active) return AXP_E_INVAL;

@@ -374,6 +374,7 @@ axp_status axp_group_launch_count(const axp_group *G, int64_t *count)
 
 axp_status axp_group_run(axp_group *G, int64_t nsteps)
 {
+    axp::TraceRange trace_("axp_group_run");
     if (!G || nsteps < 0) return AXP_E_INVAL;
     if (nsteps == 0) return AXP_OK;
     if (G->dirty) {
