@@ -237,7 +237,11 @@ axp_status axp_compute_diagnostics(axp_grid *grid, axp_diag *out);
  * instance inside a latency-critical loop where cudaMalloc/cudaFree would
  * implicitly synchronise the device, or in a process whose device memory is
  * entirely handed to another framework's pool.
- *   desc        grid description (precision must be AXP_FP64; no outflow faces)
+ *   desc        grid description (precision must be AXP_FP64; no outflow faces).
+ *               desc->lo must be the grid's present lower corner: after moving
+ *               window shifts, the shifted corner (the regular entry point adds
+ *               the window's offset itself), since the B1z-weighted centroid
+ *               sum uses absolute positions lo + (i+1) dx
  *   dev_fields  14 device pointers, each n0*n1*n2 doubles in the layout above:
  *               E0x E0y E0z B0x B0y B0z E1x E1y E1z B1x B1y B1z,
  *               phi^{n+1/2}, phi^{n-1/2}; E and B at the integer time `step`
@@ -246,8 +250,11 @@ axp_status axp_compute_diagnostics(axp_grid *grid, axp_diag *out);
  * The reduction's scratch is a fixed array inside the library, so grids are
  * limited to 8,388,608 cells (AXP_E_INVAL beyond, with a message on stderr).
  * The array lives on every GPU that loads the library until the process exits.
- * The first call on a device looks up the array's device address; make that
- * first call before any stream capture.  Every call shares the array and
+ * The first call on a device looks up the array's device address (with that
+ * device current) and keeps it for the life of the process; make that first
+ * call before any stream capture.  A cudaDeviceReset of the device discards
+ * the array and so the kept address: do not call this entry point on that
+ * device again in the same process after a reset.  Every call shares the array and
  * rewrites what it uses, so results never depend on earlier calls, but calls
  * that overlap on the GPU (from other threads or streams) race.  The call
  * synchronises `cuda_stream` before returning. */

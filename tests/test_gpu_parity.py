@@ -100,7 +100,7 @@ def test_general_fp64_bitwise_vs_oracle(case):
     for (a, s) in random_ghosts(grid, 7):
         assert np.array_equal(g.read_ghost(a, s, 0).reshape(og.ghost[a][s][0].shape), og.ghost[a][s][0])
     d, dr = g.diagnostics(), og.diagnostics()
-    for key in ("H_phi", "H_g0", "H_g1", "W", "sum_B1z2", "gauss_l2"):
+    for key in ("H_phi", "H_g0", "H_g1", "P_g2a", "P_a2g", "W", "sum_xB1z2", "sum_B1z2", "gauss_l2"):
         assert d[key] == pytest.approx(dr[key], rel=1e-11, abs=1e-300), key
     g.close()
 
@@ -266,7 +266,7 @@ def test_fused_vs_oracle(case, prec):
     for k in NAMES:
         assert rel(got[k], ref[k]) < tol, (case, prec, k, rel(got[k], ref[k]))
     d, dr = g.diagnostics(), og.diagnostics()
-    for key in ("H_phi", "H_g0", "H_g1"):
+    for key in ("H_phi", "H_g0", "H_g1", "P_g2a", "P_a2g", "sum_xB1z2", "sum_B1z2"):
         assert d[key] == pytest.approx(dr[key], rel=1e-10 if prec == "fp64" else 1e-4), key
     g.close()
 

@@ -244,6 +244,140 @@ def test_conversion_probability_massive_sinc2():
         assert abs(tm / (2 * math.pi * j / dw) - 1.0) < 0.03
 
 
+# ---------------------------------------------------------------------------
+# Axion -> photon conversion (Sec. 3.3): the same conversion law read the
+# other way, P_a2g = H_g1 / H_phi
+# ---------------------------------------------------------------------------
+
+def axion_box(n, d, dt, m=0.0, g=1e-4, B=1.0):
+    """Periodic box seeded with nothing but an axion plane wave along x (no laser),
+    B_ext = B y-hat transverse to it."""
+    return W.GridSpec(n=n, d=d, dt=dt, m=m, g=g, B_ext=(0.0, B, 0.0))
+
+
+@pytest.mark.parametrize("dim", [1, 3])
+def test_axion_to_photon_massless_closed_form(dim):
+    """A massless axion plane wave phi = a sin(k x - w t) in a uniform transverse
+    B (E0 = 0, so S = 0 and the axion stays free) drives the order-1 photon
+    resonantly; the paper's law gives P_a2g = (g B t / 2)^2.
+
+    Discrete correction, derived for this scheme.  In the staggered form E1y
+    lives at half-integer times with phi, and the current g J_y^{n+1} =
+    g B (phi^{n+3/2} - phi^{n+1/2}) / dt.  Writing E1y^{n+1/2} = Re[e_n exp(i psi)],
+    B1z^n = Re[b_n exp(i psi)] in the frame of the wave (psi = k x - w t at each
+    field's own position and time), the two updates become
+        b_{n+1} e^{-i th/2} - b_n e^{i th/2} = -2 i s e_n,
+        e_{n+1} e^{-i th/2} - e_n e^{i th/2} = -2 i s b_{n+1} + 2 i g B a s,
+    with th = w dt and s = sin(th/2) = (dt/dx) sin(k dx/2), the common Yee and
+    massless Klein-Gordon dispersion.  The secular solution e_n = p n + p0,
+    b_n = q n + q0 needs q = p and p (e^{-i th/2} + i s) = i g B a s, i.e.
+    |p| = g B a tan(th/2) per step.  At integer time E1y has amplitude
+    |e| cos(th/2) and B1z |e|, so H_g1 = |p n|^2 (1 + cos^2(th/2)) V / 4; the
+    axion energy of the diagnostics (D_t phi, the average phi^n and its forward
+    difference) is H_phi = a^2 K^2 (1 + cos^2(th/2)) V / 4, K = 2 s / dt.  Hence
+    P_a2g = (g B t / 2)^2 sec^2(th/2) (1 + O(1/n)), the same correction as for
+    photon -> axion."""
+    if dim == 1:
+        d = (1 / 32,) * 3
+        grid = axion_box((32, 1, 1), d, 0.95 * d[0])
+    else:
+        d = (1 / 16,) * 3
+        grid = axion_box((16, 2, 2), d, 0.95 * d[0] / math.sqrt(3))
+    og = oracle.OracleGrid(grid)
+    og.inject_axion(W.AxionSpec(amplitude=1e-2, k=(W.K0, 0.0, 0.0)))
+    th = yee_omega((W.K0, 0, 0), grid.d, grid.dt) * grid.dt
+    sec2 = 1.0 / math.cos(th / 2.0) ** 2
+    g, B = grid.g, grid.B_ext[1]
+    chunk = 5000 if dim == 1 else 3000
+    for _ in range(4):
+        og.step(chunk)
+        dg = og.diagnostics()
+        ratio = dg["P_a2g"] / (0.25 * (g * B * dg["t"]) ** 2)
+        assert W.K0 * dg["t"] >= 600
+        assert abs(ratio - 1.0) < 0.02, ratio  # the paper's law within the grid's dispersion error
+        assert abs(ratio / sec2 - 1.0) < 1e-4, (ratio, sec2)  # the derived discrete correction
+        assert dg["P_a2g"] == pytest.approx(dg["H_g1"] / dg["H_phi"], rel=1e-15)
+        assert dg["H_g0"] == 0.0 and dg["P_g2a"] == 0.0  # no laser: nothing of order 0
+
+
+def test_axion_to_photon_massive_sinc2():
+    """A massive axion wave (temporal problem in a periodic box) beats against the
+    photon of the same k: P_a2g(t) = (g B / dw)^2 sin^2(dw t / 2) with
+    dw = sqrt(k^2 + m^2) - k (near resonance), the photon -> axion law."""
+    d = (1 / 32,) * 3
+    grid = axion_box((32, 1, 1), d, 0.95 * d[0], m=0.3 * W.K0)
+    og = oracle.OracleGrid(grid)
+    og.inject_axion(W.AxionSpec(amplitude=1e-2, k=(W.K0, 0.0, 0.0)))
+    g, B = grid.g, grid.B_ext[1]
+    dw = math.sqrt(W.K0 ** 2 + grid.m ** 2) - W.K0
+    ts, ps = [], []
+    for _ in range(520):
+        og.step(8)
+        dg = og.diagnostics()
+        ts.append(dg["t"])
+        ps.append(dg["P_a2g"])
+    ts, ps = np.array(ts), np.array(ps)
+    peak = (g * B / dw) ** 2
+    assert abs(ps.max() / peak - 1.0) < 0.10
+    minima = [ts[i] for i in range(1, len(ps) - 1) if ps[i] < ps[i - 1] and ps[i] < ps[i + 1]]
+    assert len(minima) >= 2
+    for j, tm in enumerate(minima[:2], start=1):
+        assert abs(tm / (2 * math.pi * j / dw) - 1.0) < 0.03
+    # near-zero at the minima: the photon is given back to the axion each beat
+    assert ps[[list(ts).index(t) for t in minima[:2]]].max() < 0.02 * peak
+
+
+# ---------------------------------------------------------------------------
+# Centroid of B1z (Sec. 3.4 measures the weak laser's group velocity from it)
+# ---------------------------------------------------------------------------
+
+def right_moving_packet(grid, k0, sigma, x0, amp):
+    """Exact right-moving discrete wave packet of order 1 in a periodic 1D box:
+    B1z at the x-faces lo + (i+1) dx sampled from amp exp(-(x-x0)^2/(2 sigma^2))
+    cos(k0 (x - x0)), and E1y at the cell centres from it mode by mode.  For a
+    Yee eigenmode moving towards +x with B1z^n = Re[b exp(i(k x_f - w t_n))], the
+    integer-time E1y^n = Re[b cos(th/2) exp(i(k x_c - w t_n))], th = w dt (the
+    free-mode case of the recurrence derived above), and x_c = x_f - dx/2."""
+    n, dx, dt = grid.n[0], grid.d[0], grid.dt
+    xf = grid.lo[0] + (np.arange(n) + 1.0) * dx
+    B = amp * np.exp(-((xf - x0) ** 2) / (2 * sigma ** 2)) * np.cos(k0 * (xf - x0))
+    k = 2 * np.pi * np.fft.fftfreq(n, d=dx)
+    th = 2 * np.arcsin(dt / dx * np.abs(np.sin(k * dx / 2)))
+    E = np.fft.ifft(np.fft.fft(B) * np.cos(th / 2) * np.exp(-1j * k * dx / 2)).real
+    shape = (1, 1, n)
+    st = {name: np.zeros(shape) for name in W.FIELD_NAMES}
+    st["phi_cur"], st["phi_old"] = np.zeros(shape), np.zeros(shape)
+    st["B1z"] = B.reshape(shape)
+    st["E1y"] = E.reshape(shape)
+    return st
+
+
+def test_b1z_centroid_moves_at_the_yee_group_velocity():
+    """The B1z^2-weighted centroid sum_xB1z2 / sum_B1z2 of a weak order-1 pulse in
+    vacuum (B_ext and the coupling on; with no axion and no laser nothing is
+    converted) sits at the pulse centre, with B1z at its face position, and
+    moves at the Yee group velocity v_g = dw/dk = cos(k dx/2) / cos(w dt/2).
+    A coarse grid (8 cells per wavelength, CFL 0.5) puts v_g = 0.941, far enough
+    from c that a position or velocity mistake shows."""
+    dx = 1 / 8
+    grid = W.GridSpec(n=(640, 1, 1), d=(dx,) * 3, dt=0.5 * dx, g=1e-3, B_ext=(0.0, 1.0, 0.0))
+    x0 = grid.lo[0] + 160 * dx  # a B1z face position: the samples are symmetric about it
+    st = right_moving_packet(grid, W.K0, 4.0, x0, 1e-3)
+    og = oracle.OracleGrid(grid)
+    og.load(st)
+    d0 = og.diagnostics()
+    assert abs(d0["sum_xB1z2"] / d0["sum_B1z2"] - x0) < 1e-9 * dx
+    th = yee_omega((W.K0, 0, 0), grid.d, grid.dt) * grid.dt
+    vg = math.cos(W.K0 * dx / 2) / math.cos(th / 2)
+    assert abs(vg - 0.941) < 1e-3
+    for _ in range(3):
+        og.step(240)
+        dg = og.diagnostics()
+        X = dg["sum_xB1z2"] / dg["sum_B1z2"]
+        assert abs((X - x0) / (vg * dg["t"]) - 1.0) < 1e-3, (X, x0 + vg * dg["t"])
+        assert dg["sum_B1z2"] == pytest.approx(d0["sum_B1z2"], rel=1e-2)  # B1z^2 keeps its share
+
+
 def test_cross_energy_conserved_1d():
     """W = H_phi + sum(E0.E1 + B0.B1) dV is conserved by the continuous FPS system
     (d/dt of the order-1 cross energy is -g phi_t E0.B0); it starts at 0."""

@@ -5,17 +5,20 @@ fields live in memory another allocator owns): its reduction scratch is a
 fixed array inside the library.  This file is collected last so that, if it
 fails, a run stopping at the first failure has already run every other test.
 """
+import os
+import subprocess
+import sys
+
 import numpy as np
 import pytest
 
 from paper_2406_16796_gb300 import workloads as W
 
-pytestmark = pytest.mark.gpu
-
 KEYS = ("H_phi", "H_g0", "H_g1", "P_g2a", "P_a2g", "W", "sum_xB1z2", "sum_B1z2", "gauss_l2")
 ORDER = ("E0x", "E0y", "E0z", "B0x", "B0y", "B0z", "E1x", "E1y", "E1z", "B1x", "B1y", "B1z", "phi_cur", "phi_old")
 
 
+@pytest.mark.gpu
 def test_noalloc_diagnostics_match_regular_entry_point_on_two_calls():
     import torch
 
@@ -47,11 +50,31 @@ def test_noalloc_diagnostics_match_regular_entry_point_on_two_calls():
     g.close()
 
 
+_REJECT = r"""
+import sys
+sys.path.insert(0, sys.argv[1])
+from paper_2406_16796_gb300 import axp
+from paper_2406_16796_gb300 import workloads as W
+big = W.pulse_2d(nx=4096, ny=2049).grid
+try:
+    axp.axp_diagnostics_noalloc(axp.desc_of(big), [1] * 14, big.B_ext, big.E_ext, 0, 0)
+except axp.AxpError as e:
+    print("status", e.status)
+else:
+    print("accepted")
+"""
+
+
 def test_noalloc_rejects_grids_beyond_its_scratch():
+    """A grid one row larger than the scratch allows is refused before any CUDA
+    call.  The pointers are placeholders, so the check runs in a child process
+    that sees no GPU at all: should the size check ever regress, the call fails
+    at device lookup (AXP_E_CUDA) instead of launching on bad addresses."""
     from paper_2406_16796_gb300 import axp
 
-    big = W.pulse_2d(nx=4096, ny=2049).grid
-    d = axp.desc_of(big)
-    with pytest.raises(axp.AxpError) as e:
-        axp.axp_diagnostics_noalloc(d, [1] * 14, big.B_ext, big.E_ext, 0, 0)
-    assert e.value.status == axp.AXP_E_INVAL
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, "-c", _REJECT, root], capture_output=True, text=True, env=env, timeout=300)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.split()[-2:] == ["status", str(axp.AXP_E_INVAL)], (r.stdout, r.stderr)
+    assert "exceed the maximum" in r.stderr
