@@ -276,9 +276,14 @@ axp_status axp_read_ghost(axp_grid *grid, int32_t axis, int32_t side, int32_t le
 axp_status axp_write_ghost(axp_grid *grid, int32_t axis, int32_t side, int32_t level, const double *host_src,
                            size_t bytes);
 
-/* Complete checkpoint: all arrays, ghosts, step count and background, as an
- * opaque byte image of axp_state_bytes() bytes.  Loading into a grid of the
- * same descriptor resumes bit for bit.  Both synchronise. */
+/* Complete checkpoint: the state, ghosts, step count, background and window,
+ * as an opaque byte image of axp_state_bytes() bytes.  The image holds only
+ * the arrays that can be non-zero: the order-0 components the injected laser
+ * couples to, all order-1 components and both axion levels; the cached axion
+ * current is recomputed after a load.  Its size therefore follows the grid's
+ * injected components at the time of the save.  Loading into a grid of the
+ * same descriptor resumes bit for bit (arrays outside the image are set to
+ * zero).  Both synchronise. */
 axp_status axp_state_bytes(const axp_grid *grid, size_t *bytes);
 axp_status axp_save_state(axp_grid *grid, void *host_dst, size_t bytes);
 axp_status axp_load_state(axp_grid *grid, const void *host_src, size_t bytes);

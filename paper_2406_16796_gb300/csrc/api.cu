@@ -17,7 +17,7 @@ using namespace axp;
 namespace {
 
 constexpr size_t kAlign = 256;
-constexpr uint64_t kStateMagic = 0x31505841u;  // "AXP1"
+constexpr uint64_t kStateMagic = 0x32505841u;  // "AXP2"
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
@@ -850,15 +850,25 @@ axp_status axp_write_ghost(axp_grid *g, int32_t axis, int32_t side, int32_t leve
 }
 
 // Checkpoint image: header, then the integer-time state packed by role -- the
-// 12 field arrays, phi^{n+1/2}, the second axion level, the cached current J
-// and the outflow ghost planes of levels n+1/2 and n-1/2.
-static void state_regions(axp_grid *g, std::vector<std::pair<char *, size_t>> *out)
+// field arrays that can be non-zero (the order-0 components in the closure of
+// the injected ones, every order-1 component), phi^{n+1/2}, the second axion
+// level and the outflow ghost planes of levels n+1/2 and n-1/2.  The other
+// order-0 arrays are zero by construction and the cached current J is a
+// function of the stored state, so neither is stored: a load zeroes the first
+// and marks J for recomputation.
+static uint32_t stored_fields(const axp_grid *g)
+{
+    const uint32_t c0 = order0_closure(g);
+    return (c0 & 7u) | (((c0 >> 3) & 7u) << kB0) | (0x3Fu << kE1);
+}
+
+static void state_regions(axp_grid *g, uint32_t fields, std::vector<std::pair<char *, size_t>> *out)
 {
     const size_t arr = (size_t)cells(g->desc) * g->layout.elem;
-    for (int f = 0; f < kFields; f++) out->push_back({g->ws + g->layout.off_fields[g->fset][f], arr});
+    for (int f = 0; f < kFields; f++)
+        if (fields >> f & 1u) out->push_back({g->ws + g->layout.off_fields[g->fset][f], arr});
     out->push_back({g->ws + g->layout.off_phi[g->phi_cur_slot], arr});
     out->push_back({g->ws + g->layout.off_phi[g->phi_b_slot], arr});
-    for (int a = 0; a < 3; a++) out->push_back({g->ws + g->layout.off_J[a], arr});
     for (int a = 0; a < 3; a++)
         for (int sd = 0; sd < 2; sd++)
             for (int l = 0; l < 2; l++) {
@@ -867,14 +877,20 @@ static void state_regions(axp_grid *g, std::vector<std::pair<char *, size_t>> *o
             }
 }
 
+static size_t image_bytes(axp_grid *g, uint32_t fields)
+{
+    std::vector<std::pair<char *, size_t>> r;
+    state_regions(g, fields, &r);
+    size_t total = sizeof(StateHeader);
+    for (auto &x : r) total += x.second;
+    return total;
+}
+
 axp_status axp_state_bytes(const axp_grid *g, size_t *bytes)
 {
     if (!g || !bytes) return AXP_E_INVAL;
-    std::vector<std::pair<char *, size_t>> r;
-    state_regions(const_cast<axp_grid *>(g), &r);
-    size_t total = sizeof(StateHeader);
-    for (auto &x : r) total += x.second;
-    *bytes = total;
+    axp_grid *gm = const_cast<axp_grid *>(g);
+    *bytes = image_bytes(gm, stored_fields(gm));
     return AXP_OK;
 }
 
@@ -896,7 +912,7 @@ axp_status axp_save_state(axp_grid *g, void *dst, size_t bytes)
         h.E_ext[a] = g->E_ext[a];
     }
     h.step = g->step;
-    h.J_valid = g->J_valid;
+    h.J_valid = 0;
     h.active = g->active;
     h.phi_active = g->phi_active;
     h.win_axis = g->win_axis;
@@ -907,7 +923,7 @@ axp_status axp_save_state(axp_grid *g, void *dst, size_t bytes)
     h.win_offset = g->win_offset;
     std::memcpy(dst, &h, sizeof(h));
     std::vector<std::pair<char *, size_t>> r;
-    state_regions(g, &r);
+    state_regions(g, stored_fields(g), &r);
     char *p = (char *)dst + sizeof(h);
     for (auto &x : r) {
         if (e == cudaSuccess) e = cudaMemcpyAsync(p, x.first, x.second, cudaMemcpyDeviceToHost, g->stream);
@@ -920,18 +936,30 @@ axp_status axp_save_state(axp_grid *g, void *dst, size_t bytes)
 axp_status axp_load_state(axp_grid *g, const void *src, size_t bytes)
 {
     axp::TraceRange trace_("axp_load_state");
-    size_t need;
-    if (!g || !src || axp_state_bytes(g, &need) != AXP_OK || bytes != need) return AXP_E_INVAL;
+    if (!g || !src || bytes < sizeof(StateHeader)) return AXP_E_INVAL;
     if (g->group) return AXP_E_STATE;
-    g->cfg_version++;
     StateHeader h;
     std::memcpy(&h, src, sizeof(h));
-    if (h.magic != kStateMagic || h.bytes != need || std::memcmp(&h.desc, &g->desc, sizeof(axp_grid_desc)) != 0)
+    if (h.magic != kStateMagic || h.bytes != bytes || std::memcmp(&h.desc, &g->desc, sizeof(axp_grid_desc)) != 0)
         return AXP_E_INVAL;
+    // the image's array set follows from its own record of the injected components
+    const uint32_t active_before = g->active;
+    g->active = h.active;
+    const uint32_t fields = stored_fields(g);
+    if (image_bytes(g, fields) != bytes) {
+        g->active = active_before;
+        return AXP_E_INVAL;
+    }
+    g->cfg_version++;
     cudaError_t e = cudaStreamSynchronize(g->stream);
     g->staggered = false;
+    // arrays outside the image are zero in both field sets (kernels never touch them)
+    const size_t arr = (size_t)cells(g->desc) * g->layout.elem;
+    for (int set = 0; set < 2 && e == cudaSuccess; set++)
+        for (int f = 0; f < kFields && e == cudaSuccess; f++)
+            if (!(fields >> f & 1u)) e = cudaMemsetAsync(g->ws + g->layout.off_fields[set][f], 0, arr, g->stream);
     std::vector<std::pair<char *, size_t>> r;
-    state_regions(g, &r);
+    state_regions(g, fields, &r);
     const char *p = (const char *)src + sizeof(h);
     for (auto &x : r) {
         if (e == cudaSuccess) e = cudaMemcpyAsync(x.first, p, x.second, cudaMemcpyHostToDevice, g->stream);
@@ -944,8 +972,7 @@ axp_status axp_load_state(axp_grid *g, const void *src, size_t bytes)
         g->E_ext[a] = h.E_ext[a];
     }
     g->step = h.step;
-    g->J_valid = h.J_valid != 0;
-    g->active = h.active;
+    g->J_valid = false;  // recomputed from the loaded state when a step needs it
     g->phi_active = h.phi_active != 0;
     g->win_axis = h.win_axis;
     g->win_cells = h.win_cells;

@@ -27,7 +27,12 @@ def oracle_reflectivity(bc, n, t_end=30.0):
     return og.diagnostics()["H_phi"] / H0, amp
 
 
-@pytest.mark.parametrize("bc,prec,tol", [("pml", "fp64", 1e-8), ("outflow", "fp64", 1e-8), ("pml", "fp32", 3e-2)])
+# FP32 split: the reflected energy and amplitude are what is left after the
+# layer absorbed all but 0.03% of the energy (2% of the amplitude), so they are
+# differences of FP32 fields of order 1; measured against the FP64 oracle they
+# differ by 3e-6 (energy) and 5e-6 (amplitude) on the 200 x 200 grid, held
+# here to 1e-4.
+@pytest.mark.parametrize("bc,prec,tol", [("pml", "fp64", 1e-8), ("outflow", "fp64", 1e-8), ("pml", "fp32", 1e-4)])
 def test_reflectivity_matches_oracle(bc, prec, tol):
     from paper_2406_16796_gb300 import bccheck
 
