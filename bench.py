@@ -54,7 +54,8 @@ def parse():
     ap.add_argument("--no-window", action="store_true")
     ap.add_argument("--scan-tiling", default=None,
                     help="block_steps,segment_cells,threads for the scan instead of the autotuner's choice")
-    ap.add_argument("--serve-requests", type=int, default=120)
+    ap.add_argument("--serve-requests", type=int, default=1000)
+    ap.add_argument("--serve-open-requests", type=int, default=200)
     ap.add_argument("--n3d", type=int, default=512, help="edge of the 3D axion box")
     return ap.parse_args()
 
@@ -373,70 +374,100 @@ def vacuum1d_measurement(world):
     return out
 
 
-def fp64_sequential_seconds(reqs, prefix=40, warm=4):
-    """Seconds the requests would take run one after another as single-grid FP64
-    runs: each request's grid is built and timed over a prefix of its steps
-    (after a few untimed ones), and its time is extrapolated by its step count
-    (every step of a run costs the same)."""
+def fp64_sequential_sample(reqs, served, sample=8, seed=20240628):
+    """The requests run one after another as single-grid FP64 runs, timed in full
+    (every step, device time) on a seeded sample, and extrapolated to the whole
+    set by cell-updates, per class (1D and 2D run at different rates).  The
+    same sample gives the served FP32-split conversion probabilities' error
+    against FP64."""
+    import numpy as np
     import torch
 
     from paper_2406_16796_gb300 import axp, workloads as W
 
-    total = 0.0
-    for r in reqs:
-        w = W.request_workload(r, precision="fp64")
-        g = axp.Grid(w.grid)
-        g.inject_laser(w.lasers[0])
-        g.step(warm)
-        g.synchronize()
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ev0.record(g.stream)
-        g.step(prefix)
-        ev1.record(g.stream)
-        ev1.synchronize()
-        total += ev0.elapsed_time(ev1) / 1e3 / prefix * r.steps
-        g.close()
-    return total
+    rng = np.random.default_rng(seed)
+    by_class = {nd: [i for i, r in enumerate(reqs) if r.ndim == nd] for nd in (1, 2)}
+    # the sample keeps the stream's class mix (at least one of each class present)
+    n2 = max(1 if by_class[2] else 0, round(sample * len(by_class[2]) / max(1, len(reqs))))
+    pick = {1: sorted(rng.choice(by_class[1], min(sample - n2, len(by_class[1])), replace=False).tolist()),
+            2: sorted(rng.choice(by_class[2], min(n2, len(by_class[2])), replace=False).tolist()) if n2 else []}
+    rate, errs, secs = {}, [], 0.0
+    for nd, idx in pick.items():
+        t_tot, cu_tot = 0.0, 0
+        for i in idx:
+            r = reqs[i]
+            w = W.request_workload(r, precision="fp64")
+            g = axp.Grid(w.grid)
+            g.inject_laser(w.lasers[0])
+            g.synchronize()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(g.stream)
+            g.step(r.steps)
+            ev1.record(g.stream)
+            ev1.synchronize()
+            t_tot += ev0.elapsed_time(ev1) / 1e3
+            cu_tot += r.n[0] * r.n[1] * r.steps
+            d = g.diagnostics()
+            g.close()
+            if served.get(i) is not None and d["P_g2a"] > 0:
+                errs.append(abs(served[i] - d["P_g2a"]) / d["P_g2a"])
+        secs += t_tot
+        if cu_tot:
+            rate[nd] = cu_tot / t_tot
+    total = sum(r.n[0] * r.n[1] * r.steps / rate[r.ndim] for r in reqs if r.ndim in rate)
+    return {"seconds_extrapolated": total, "sims_per_s": len(reqs) / total,
+            "sample": "%d seeded requests (%d 1D, %d 2D) run one after another in FP64, every step timed (%.1f s)"
+                      % (len(pick[1]) + len(pick[2]), len(pick[1]), len(pick[2]), secs),
+            "cell_updates_per_s_1d": rate.get(1), "cell_updates_per_s_2d": rate.get(2),
+            "max_rel_err_P_served_vs_fp64": max(errs) if errs else None}
 
 
-def serve_measurement(count, rank, world):
+def serve_measurement(count, rank, world, open_count=200):
     """The serving loop on the first `count` requests of the seeded stream (80%
     1D Nx log-uniform in [1024, 65536], 20% 2D Nx log-uniform in [256, 2048]
     with Ny = Nx/2, scan parameters, 5000-40000 steps).  Capacity is measured
-    closed-loop (every request present at t = 0); then the same requests arrive
-    as a Poisson stream at 0.5, 0.9 and 1.2 x that capacity.  Each rank serves
-    its own share (replicas).  The comparator is the same requests run one
-    after another as single-grid FP64 runs (timed prefix, extrapolated)."""
+    closed-loop (every request present at t = 0) on all of them; then the first
+    `open_count` arrive as a Poisson stream at 0.5, 0.9 and 1.2 x that
+    capacity.  Latency percentiles are reported overall and per class.  Each
+    rank serves its own share (replicas).  The comparator is the same requests
+    run one after another as single-grid FP64 runs, timed in full on a seeded
+    sample."""
     from paper_2406_16796_gb300 import serve, workloads as W
 
-    base = W.shard(W.serve_requests(count=count), rank, world)
+    stream = W.serve_requests(count=count)
+    base = W.shard(stream, rank, world)
     fields = ("ndim", "n", "m", "g", "B0", "steps")
     closed = [W.Request(0.0, *[getattr(r, f) for f in fields]) for r in base]
-    def job_rate(summary, n_local):
+
+    def job_rate(summary, n_local, n_all):
         # all ranks' requests over the slowest rank's span (latencies are rank 0's)
-        return count / max_over_ranks(n_local / summary["sims_per_s"], world)
+        return n_all / max_over_ranks(n_local / summary["sims_per_s"], world)
 
     srv = serve.Server()
-    cap = srv.serve(closed).summary()
-    cap["sims_per_s"] = job_rate(cap, len(base))
+    cstats = srv.serve(closed)
+    cap = cstats.summary()
+    cap["sims_per_s"] = job_rate(cap, len(base), count)
+    served = {k: rec.P_g2a for k, rec in enumerate(cstats.records)}
     levels = []
+    n_open = min(open_count, count)
     for f in (0.5, 0.9, 1.2):
         rate = f * cap["sims_per_s"]
-        reqs = W.shard(W.serve_requests(count=count, rate_per_s=rate), rank, world)
+        reqs = W.shard(W.serve_requests(count=n_open, rate_per_s=rate), rank, world)
         s = srv.serve(reqs).summary()
-        s["sims_per_s"] = job_rate(s, len(reqs))
+        s["sims_per_s"] = job_rate(s, len(reqs), n_open)
         s["offered_load"] = f
         s["offered_rate_per_s"] = rate
         levels.append(s)
     srv.close()
-    seq = max_over_ranks(fp64_sequential_seconds(base), world)
-    cu = sum(r.n[0] * r.n[1] * r.steps for r in W.serve_requests(count=count))
+    seq = fp64_sequential_sample(base, served)
+    seq_s = max_over_ranks(seq["seconds_extrapolated"], world)
+    cu = sum(r.n[0] * r.n[1] * r.steps for r in stream)
     return {"workload": "serve_%d_requests" % count, "requests": count, "cell_updates": cu,
-            "sample": "the first %d of the 10000-request seeded stream" % count,
+            "sample": "closed loop: the first %d of the 10000-request seeded stream; open loop: its first %d"
+                      % (count, n_open),
             "capacity": cap, "load": levels,
-            "fp64_sequential": {"sims_per_s": count / seq, "seconds": seq,
-                                "how": "each request's FP64 grid timed over 40 steps, extrapolated by its steps"},
-            "speedup_vs_fp64_sequential": cap["sims_per_s"] / (count / seq)}
+            "fp64_sequential": dict(seq, sims_per_s=count / seq_s),
+            "speedup_vs_fp64_sequential": cap["sims_per_s"] / (count / seq_s)}
 
 
 def boundary_measurement():
@@ -678,7 +709,7 @@ def gpu_arm(args):
         scan = scan_measurement(rank, world, tiling=tl)
     srv = None
     if not args.no_serve:
-        srv = serve_measurement(args.serve_requests, rank, world)
+        srv = serve_measurement(args.serve_requests, rank, world, open_count=args.serve_open_requests)
     bcm = None
     if not args.no_bc and rank == 0:
         bcm = boundary_measurement()

@@ -288,6 +288,38 @@ axp_status axp_state_bytes(const axp_grid *grid, size_t *bytes);
 axp_status axp_save_state(axp_grid *grid, void *host_dst, size_t bytes);
 axp_status axp_load_state(axp_grid *grid, const void *host_src, size_t bytes);
 
+/* Slab decomposition of one grid across devices (the rows exchange that a
+ * domain decomposition of the explicit scheme of Sec. 2.3 needs; the paper
+ * itself runs inside EPOCH's own decomposition).  Rows are the cells with one
+ * index along the grid's slowest axis with more than one cell (z in 3D, y in
+ * 2D, x in 1D); row r is the contiguous range of n0*n1 (3D), n0 (2D) or 1
+ * (1D) elements at offset r times that.  A slab grid holds its owned rows
+ * plus halo rows on each side; k steps on their own leave the owned rows
+ * exact while the halo is at least k + 2 rows wide (one step's dependency
+ * cone is one cell wide, the axion current's stencil widens it once), wider
+ * by the absorbing layer where a slab's cut side carries one.
+ *
+ * axp_pack_rows copies rows [row0, row0 + nrows) of the 14 arrays of the
+ * present state (the 12 fields, phi^{n+1/2}, then the second axion level, in
+ * the grid's storage precision and present representation) into the device
+ * buffer dev_dst, array after array; axp_unpack_rows writes such a buffer
+ * into rows of this grid.  Both are asynchronous on the grid's stream and
+ * allocate nothing; bytes must equal axp_rows_bytes(nrows).  The state's
+ * representation (integer time, or the staggered state of the single-pass
+ * kernels) must be the same on both sides: slabs that exchange rows take the
+ * same kernel path and the same steps.  AXP_E_INVAL for rows outside the
+ * grid.
+ *
+ * axp_compute_diagnostics_rows: the record of axp_compute_diagnostics
+ * restricted to the cells whose row lies in [row0, row1) (and in the physical
+ * region).  Its energies and sums (H_phi, H_g0, H_g1, W, sum_xB1z2, sum_B1z2,
+ * gauss_l2) add up across slabs; the ratios are formed from the sums.
+ * Synchronises. */
+axp_status axp_rows_bytes(const axp_grid *grid, int64_t nrows, size_t *bytes);
+axp_status axp_pack_rows(axp_grid *grid, int64_t row0, int64_t nrows, void *dev_dst, size_t bytes);
+axp_status axp_unpack_rows(axp_grid *grid, int64_t row0, int64_t nrows, const void *dev_src, size_t bytes);
+axp_status axp_compute_diagnostics_rows(axp_grid *grid, int64_t row0, int64_t row1, axp_diag *out);
+
 /* Current step index n, and a wait for all queued work of the handle. */
 axp_status axp_get_step(const axp_grid *grid, int64_t *step);
 axp_status axp_synchronize(axp_grid *grid);
@@ -323,19 +355,34 @@ axp_status axp_get_window_offset(const axp_grid *grid, int64_t *cells);
  * AXP_KERNEL_TM2D forces the single-pass kernel specialised for 2D grids with
  * an (E0z; B0x, B0y) laser and periodic or PML edges (at most 2^32 cells);
  * AXP_KERNEL_AX3D forces the single-pass kernel specialised for periodic 3D
- * grids with no laser fields and no uniform E (an axion wave in a uniform B).
- * Forcing a kernel that does not support the grid makes axp_step return
- * AXP_E_STATE. */
+ * grids with no laser fields and no uniform E (an axion wave in a uniform B);
+ * AXP_KERNEL_BLOCK1D forces the time-blocked kernel for FP64 1D grids that
+ * are periodic along x (at least 256 cells, no soft source): the general
+ * kernels' stages, bit for bit, over windows held in shared memory for blocks
+ * of steps, in one cooperative launch per run of steps.  Should one of its
+ * bounded grid-wide waits give up, the next synchronising call on the handle
+ * (axp_synchronize, diagnostics, reads, axp_save_state) returns
+ * AXP_E_TIMEOUT.  Forcing a kernel that does not support the grid makes
+ * axp_step return AXP_E_STATE. */
 typedef enum {
     AXP_KERNEL_AUTO = 0,
     AXP_KERNEL_GENERAL = 1,
     AXP_KERNEL_FUSED = 2,
     AXP_KERNEL_TM2D = 3,
-    AXP_KERNEL_AX3D = 4
+    AXP_KERNEL_AX3D = 4,
+    AXP_KERNEL_BLOCK1D = 5
 } axp_kernel;
 axp_status axp_set_kernel(axp_grid *grid, int32_t kernel);
-/* Which path the next axp_step will take (AXP_KERNEL_GENERAL, _FUSED, _TM2D or _AX3D). */
+/* Which path the next axp_step will take (an axp_kernel value other than AUTO). */
 axp_status axp_get_kernel_path(axp_grid *grid, int32_t *path);
+
+/* Failure detection test for the time-blocked 1D kernel (no counterpart in
+ * the paper): in the next launch of that kernel on this grid, block `block`
+ * leaves before its first grid-wide wait, as a participant that never
+ * arrives.  The other blocks' bounded waits give up after about a second, the
+ * launch ends, the state is left partly advanced, and the next synchronising
+ * call returns AXP_E_TIMEOUT.  -1 cancels.  Nothing faults or hangs. */
+axp_status axp_test_block1d_absent(axp_grid *grid, int32_t block);
 
 /* Number of kernel launches issued by this handle since creation (for
  * launch accounting in benchmarks). */

@@ -18,7 +18,7 @@ from .workloads import BC_CODE, AxionSpec, GridSpec, LaserSpec, SourceSpec
 
 AXP_OK, AXP_E_INVAL, AXP_E_UNSTABLE, AXP_E_NOMEM, AXP_E_CUDA, AXP_E_TIMEOUT, AXP_E_NONFINITE, AXP_E_STATE = range(8)
 AXP_FP64, AXP_FP32_SPLIT = 0, 1
-AXP_KERNEL_AUTO, AXP_KERNEL_GENERAL, AXP_KERNEL_FUSED, AXP_KERNEL_TM2D, AXP_KERNEL_AX3D = 0, 1, 2, 3, 4
+AXP_KERNEL_AUTO, AXP_KERNEL_GENERAL, AXP_KERNEL_FUSED, AXP_KERNEL_TM2D, AXP_KERNEL_AX3D, AXP_KERNEL_BLOCK1D = 0, 1, 2, 3, 4, 5
 FIELD_IDS = {n: i for i, n in enumerate(("E0x", "E0y", "E0z", "B0x", "B0y", "B0z",
                                           "E1x", "E1y", "E1z", "B1x", "B1y", "B1z"))}
 FIELD_IDS["phi_cur"] = 12
@@ -105,6 +105,11 @@ def lib():
             "axp_get_window_offset": ([_P, C.POINTER(C.c_int64)], C.c_int),
             "axp_get_kernel_path": ([_P, C.POINTER(C.c_int32)], C.c_int),
             "axp_get_launch_count": ([_P, C.POINTER(C.c_int64)], C.c_int),
+            "axp_test_block1d_absent": ([_P, C.c_int32], C.c_int),
+            "axp_rows_bytes": ([_P, C.c_int64, C.POINTER(C.c_size_t)], C.c_int),
+            "axp_pack_rows": ([_P, C.c_int64, C.c_int64, _P, C.c_size_t], C.c_int),
+            "axp_unpack_rows": ([_P, C.c_int64, C.c_int64, _P, C.c_size_t], C.c_int),
+            "axp_compute_diagnostics_rows": ([_P, C.c_int64, C.c_int64, C.POINTER(axp_diag)], C.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -273,6 +278,30 @@ def axp_get_launch_count(h):
     n = C.c_int64()
     _check(lib().axp_get_launch_count(h, C.byref(n)), "axp_get_launch_count")
     return n.value
+
+
+def axp_rows_bytes(h, nrows):
+    n = C.c_size_t()
+    _check(lib().axp_rows_bytes(h, int(nrows), C.byref(n)), "axp_rows_bytes")
+    return n.value
+
+
+def axp_pack_rows(h, row0, nrows, dev_ptr, nbytes):
+    _check(lib().axp_pack_rows(h, int(row0), int(nrows), _P(dev_ptr), nbytes), "axp_pack_rows")
+
+
+def axp_unpack_rows(h, row0, nrows, dev_ptr, nbytes):
+    _check(lib().axp_unpack_rows(h, int(row0), int(nrows), _P(dev_ptr), nbytes), "axp_unpack_rows")
+
+
+def axp_compute_diagnostics_rows(h, row0, row1):
+    d = axp_diag()
+    _check(lib().axp_compute_diagnostics_rows(h, int(row0), int(row1), C.byref(d)), "axp_compute_diagnostics_rows")
+    return d.as_dict()
+
+
+def axp_test_block1d_absent(h, block):
+    _check(lib().axp_test_block1d_absent(h, int(block)), "axp_test_block1d_absent")
 
 
 # ---- descriptors from the workload specs ----

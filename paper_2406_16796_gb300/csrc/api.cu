@@ -150,6 +150,21 @@ bool finite_diag(const axp_diag &d)
 
 bool is_fp32(const axp_grid *g) { return g->desc.precision == AXP_FP32_SPLIT; }
 
+// A grid-wide wait of the time-blocked 1D kernel that gave up leaves a word in
+// the workspace; synchronising calls report it once (AXP_E_TIMEOUT) and clear it.
+axp_status latched_status(axp_grid *g)
+{
+    if (!g->coop_used) return AXP_OK;
+    int *flag = (int *)(g->ws + g->layout.off_flag) + 1;
+    int v = 0;
+    cudaError_t e = cudaStreamSynchronize(g->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(&v, flag, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (!v) return AXP_OK;
+    e = cudaMemset(flag, 0, sizeof(int));
+    return e == cudaSuccess ? AXP_E_TIMEOUT : cuda_status(e);
+}
+
 struct StateHeader {
     uint64_t magic;
     uint64_t bytes;
@@ -185,7 +200,10 @@ bool compute_layout(const axp_grid_desc &d, Workspace *w)
             w->off_fields[set][f] = off;
             off += arr;
         }
-    const int nphi = d.precision == AXP_FP32_SPLIT ? 4 : 3;
+    // FP64 keeps two levels and one spare; 1D grids get a second spare, which the
+    // time-blocked 1D kernel uses to double-buffer both levels
+    const bool line = d.n[1] == 1 && d.n[2] == 1;
+    const int nphi = d.precision == AXP_FP32_SPLIT || line ? 4 : 3;
     for (int p = 0; p < 4; p++) {
         if (p < nphi) {
             w->off_phi[p] = off;
@@ -453,6 +471,7 @@ axp_status axp_create_grid(const axp_grid_desc *desc, void *dev_workspace, size_
     g->J_valid = false;
     g->kernel_choice = AXP_KERNEL_AUTO;
     g->win_axis = -1;
+    g->coop_absent = -1;
     cudaError_t e = cudaMemsetAsync(g->ws, 0, w.total, g->stream);
     if (e == cudaSuccess) {
         // absorbing-layer profiles and coefficients, computed once on the host
@@ -697,7 +716,8 @@ axp_status axp_get_window_offset(const axp_grid *g, int64_t *cells)
 axp_status axp_synchronize(axp_grid *g)
 {
     if (!g) return AXP_E_INVAL;
-    return cuda_status(cudaStreamSynchronize(g->stream));
+    const axp_status st = cuda_status(cudaStreamSynchronize(g->stream));
+    return st != AXP_OK ? st : latched_status(g);
 }
 
 axp_status axp_read_diagnostics(axp_grid *g, axp_diag *out, int64_t max, int64_t *n)
@@ -708,6 +728,8 @@ axp_status axp_read_diagnostics(axp_grid *g, axp_diag *out, int64_t max, int64_t
     *n = 0;
     cudaError_t e = cudaStreamSynchronize(g->stream);
     if (e != cudaSuccess) return cuda_status(e);
+    const axp_status lat = latched_status(g);
+    if (lat != AXP_OK) return lat;
     const int64_t cap = g->desc.diag_capacity;
     if (cap <= 0) return AXP_OK;
     if (g->ring_written - g->ring_read > cap) g->ring_read = g->ring_written - cap;
@@ -734,6 +756,8 @@ axp_status axp_compute_diagnostics(axp_grid *g, axp_diag *out)
     if (e == cudaSuccess) e = cudaMemcpyAsync(out, dst, sizeof(axp_diag), cudaMemcpyDeviceToHost, g->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
     if (e != cudaSuccess) return cuda_status(e);
+    const axp_status lat = latched_status(g);
+    if (lat != AXP_OK) return lat;
     return finite_diag(*out) ? AXP_OK : AXP_E_NONFINITE;
 }
 
@@ -753,6 +777,8 @@ axp_status axp_read_field(axp_grid *g, int32_t which, double *dst, size_t bytes)
     cudaError_t e = ensure_integer(g);
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
     if (e != cudaSuccess) return cuda_status(e);
+    const axp_status lat = latched_status(g);
+    if (lat != AXP_OK) return lat;
     if (!is_fp32(g)) return cuda_status(cudaMemcpy(dst, field_ptr(g, which), bytes, cudaMemcpyDeviceToHost));
     std::vector<float> tmp(N), inc;
     e = cudaMemcpy(tmp.data(), field_ptr(g, which == AXP_PHI_OLD ? AXP_PHI_CUR : which), N * 4,
@@ -930,7 +956,8 @@ axp_status axp_save_state(axp_grid *g, void *dst, size_t bytes)
         p += x.second;
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
-    return cuda_status(e);
+    if (e != cudaSuccess) return cuda_status(e);
+    return latched_status(g);
 }
 
 axp_status axp_load_state(axp_grid *g, const void *src, size_t bytes)
@@ -993,7 +1020,7 @@ axp_status axp_get_step(const axp_grid *g, int64_t *step)
 
 axp_status axp_set_kernel(axp_grid *g, int32_t kernel)
 {
-    if (!g || kernel < AXP_KERNEL_AUTO || kernel > AXP_KERNEL_AX3D) return AXP_E_INVAL;
+    if (!g || kernel < AXP_KERNEL_AUTO || kernel > AXP_KERNEL_BLOCK1D) return AXP_E_INVAL;
     if (g->group) return AXP_E_STATE;
     g->cfg_version++;
     g->kernel_choice = kernel;
@@ -1004,6 +1031,90 @@ axp_status axp_get_kernel_path(axp_grid *g, int32_t *path)
 {
     if (!g || !path) return AXP_E_INVAL;
     *path = is_fp32(g) ? fused_path<float>(g) : fused_path<double>(g);
+    return AXP_OK;
+}
+
+// ---- slab decomposition: rows of the present state along the slowest axis ----
+
+static int rows_axis(const axp_grid_desc &d) { return d.n[2] > 1 ? 2 : (d.n[1] > 1 ? 1 : 0); }
+
+static int64_t row_cells(const axp_grid_desc &d)
+{
+    const int a = rows_axis(d);
+    int64_t r = 1;
+    for (int b = 0; b < a; b++) r *= d.n[b];
+    return r;
+}
+
+// the 14 arrays of the present state in a fixed order: fields, phi^{n+1/2}, second level
+static void state_arrays(axp_grid *g, char *out[kFields + 2])
+{
+    for (int f = 0; f < kFields; f++) out[f] = g->ws + g->layout.off_fields[g->fset][f];
+    out[kFields] = g->ws + g->layout.off_phi[g->phi_cur_slot];
+    out[kFields + 1] = g->ws + g->layout.off_phi[g->phi_b_slot];
+}
+
+axp_status axp_rows_bytes(const axp_grid *g, int64_t nrows, size_t *bytes)
+{
+    if (!g || !bytes || nrows < 0) return AXP_E_INVAL;
+    *bytes = (size_t)(kFields + 2) * (size_t)nrows * (size_t)row_cells(g->desc) * g->layout.elem;
+    return AXP_OK;
+}
+
+static axp_status rows_copy(axp_grid *g, int64_t row0, int64_t nrows, char *dev, size_t bytes, bool pack)
+{
+    size_t need;
+    if (!g || !dev || axp_rows_bytes(g, nrows, &need) != AXP_OK || bytes != need) return AXP_E_INVAL;
+    if (g->group) return AXP_E_STATE;
+    const int a = rows_axis(g->desc);
+    if (row0 < 0 || row0 + nrows > g->desc.n[a]) return AXP_E_INVAL;
+    const size_t chunk = (size_t)nrows * (size_t)row_cells(g->desc) * g->layout.elem;
+    const size_t off = (size_t)row0 * (size_t)row_cells(g->desc) * g->layout.elem;
+    char *arr[kFields + 2];
+    state_arrays(g, arr);
+    cudaError_t e = cudaSuccess;
+    for (int q = 0; q < kFields + 2 && e == cudaSuccess; q++)
+        e = pack ? cudaMemcpyAsync(dev + q * chunk, arr[q] + off, chunk, cudaMemcpyDeviceToDevice, g->stream)
+                 : cudaMemcpyAsync(arr[q] + off, dev + q * chunk, chunk, cudaMemcpyDeviceToDevice, g->stream);
+    if (!pack) {
+        g->J_valid = false;
+        g->cfg_version++;
+    }
+    return cuda_status(e);
+}
+
+axp_status axp_pack_rows(axp_grid *g, int64_t row0, int64_t nrows, void *dev_dst, size_t bytes)
+{
+    return rows_copy(g, row0, nrows, (char *)dev_dst, bytes, true);
+}
+
+axp_status axp_unpack_rows(axp_grid *g, int64_t row0, int64_t nrows, const void *dev_src, size_t bytes)
+{
+    return rows_copy(g, row0, nrows, (char *)const_cast<void *>(dev_src), bytes, false);
+}
+
+axp_status axp_compute_diagnostics_rows(axp_grid *g, int64_t row0, int64_t row1, axp_diag *out)
+{
+    axp::TraceRange trace_("axp_compute_diagnostics_rows");
+    if (!g || !out || row0 < 0 || row1 < row0) return AXP_E_INVAL;
+    if (g->group) return AXP_E_STATE;
+    const int a = rows_axis(g->desc);
+    if (row1 > g->desc.n[a]) return AXP_E_INVAL;
+    axp_diag *dst = scratch_slot(g);
+    cudaError_t e = is_fp32(g) ? diag_compute_rows<float>(g, dst, a, row0, row1)
+                               : diag_compute_rows<double>(g, dst, a, row0, row1);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, dst, sizeof(axp_diag), cudaMemcpyDeviceToHost, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    const axp_status lat = latched_status(g);
+    if (lat != AXP_OK) return lat;
+    return finite_diag(*out) ? AXP_OK : AXP_E_NONFINITE;
+}
+
+axp_status axp_test_block1d_absent(axp_grid *g, int32_t block)
+{
+    if (!g || block < -1) return AXP_E_INVAL;
+    g->coop_absent = block;
     return AXP_OK;
 }
 

@@ -145,6 +145,10 @@ struct axp_grid {
     // soft source (axp_set_soft_source); its sheet weights sit in off_src
     bool src_on;
     axp_source_desc src;
+    // the time-blocked 1D kernel has run: its barrier-timeout word (off_flag + 4)
+    // is checked by the next synchronising call
+    bool coop_used;
+    int32_t coop_absent;  // failure-detection test: block that skips the next launch's barriers (-1: none)
 };
 
 namespace axp {
@@ -166,11 +170,16 @@ cudaError_t general_current(axp_grid *g);  // J^n of the present state
 template <typename T>
 cudaError_t diag_compute(axp_grid *g, axp_diag *dev_dst);
 template <typename T>
+cudaError_t diag_compute_rows(axp_grid *g, axp_diag *dev_dst, int axis, int64_t lo, int64_t hi);
+template <typename T>
 cudaError_t inject_laser(axp_grid *g, const axp_laser_desc &L);
 template <typename T>
 cudaError_t inject_axion(axp_grid *g, const axp_axion_desc &A);
 template <typename T>
 cudaError_t fused_step(axp_grid *g, int64_t nsteps, bool *handled);
+// time-blocked 1D kernel (FP64, periodic): eligibility and steps on the integer-time state
+bool block1d_supported(const axp_grid *g);
+cudaError_t block1d_step(axp_grid *g, int64_t nsteps);
 template <typename T>
 bool fused_supported(const axp_grid *g);
 // the path axp_step will take under the handle's kernel choice (an axp_kernel value)

@@ -138,6 +138,15 @@ static Ghosts<T> ghosts_lvl(axp_grid *g, int level)
 template <typename T>
 cudaError_t diag_compute(axp_grid *g, axp_diag *dev_dst)
 {
+    return diag_compute_rows<T>(g, dev_dst, -1, 0, 0);
+}
+
+// The sums over the cells whose index along `axis` lies in [lo, hi) as well as in
+// the physical region (axis < 0: no restriction).  A slab of a decomposed grid
+// sums its owned rows this way; the records' sums add up across slabs.
+template <typename T>
+cudaError_t diag_compute_rows(axp_grid *g, axp_diag *dev_dst, int axis, int64_t lo, int64_t hi)
+{
     // staggered (fused-path) state: reconstruct E^n into the spare field set first
     View<T> v;
     if (g->staggered) {
@@ -146,6 +155,10 @@ cudaError_t diag_compute(axp_grid *g, axp_diag *dev_dst)
         v = make_view_eset<T>(g, 1 - g->fset);
     } else {
         v = make_view<T>(g);
+    }
+    if (axis >= 0) {
+        if (lo > v.region_lo[axis]) v.region_lo[axis] = (int)lo;
+        if (hi < v.region_hi[axis]) v.region_hi[axis] = (int)hi;
     }
     double *partials = (double *)(g->ws + g->layout.off_partials);
     const int nb = g->layout.diag_blocks;
@@ -163,6 +176,8 @@ cudaError_t diag_compute(axp_grid *g, axp_diag *dev_dst)
 
 template cudaError_t diag_compute<double>(axp_grid *, axp_diag *);
 template cudaError_t diag_compute<float>(axp_grid *, axp_diag *);
+template cudaError_t diag_compute_rows<double>(axp_grid *, axp_diag *, int, int64_t, int64_t);
+template cudaError_t diag_compute_rows<float>(axp_grid *, axp_diag *, int, int64_t, int64_t);
 
 // ---------------------------------------------------------------------------
 // Diagnostics for callers that cannot allocate device memory.

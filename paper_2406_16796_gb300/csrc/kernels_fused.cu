@@ -1,11 +1,13 @@
 // kernels_fused.cu -- host side of the fused single-pass step: eligibility,
 // parameter setup, launch geometry and the per-step buffer rotation.
 #include <algorithm>
+#include <cstring>
 #include <cmath>
 #include <utility>
 
 #include "kernels_fused.cuh"
 #include "kernels_ax3d.cuh"
+#include "kernels_line1d.cuh"
 #include "kernels_tm2d.cuh"
 
 namespace axp {
@@ -220,11 +222,116 @@ bool fused_supported(const axp_grid *g)
     return true;
 }
 
+// steps per block of the time-blocked 1D kernel (halo tblock + 3 on each side):
+// with 4096 cells over 152 SMs a window of 27 + 2 x 15 cells fills two warps
+#ifndef AXP_LINE_BLOCK
+#define AXP_LINE_BLOCK 12
+#endif
+constexpr int kLineBlock = AXP_LINE_BLOCK;
+
+// Which grids take the time-blocked 1D kernel: FP64, 1D and periodic along x,
+// no soft source and no uniform E (as the other single-pass kernels), a window
+// that fits shared memory, a spare pair of axion buffers and a device that
+// supports cooperative launches.
+bool block1d_supported(const axp_grid *g)
+{
+    const axp_grid_desc &d = g->desc;
+    if (d.precision != AXP_FP64 || d.n[1] != 1 || d.n[2] != 1 || d.n[0] < 256 || g->src_on) return false;
+    if (d.em_bc[0][0] != AXP_BC_PERIODIC || d.axion_bc[0][0] != AXP_BC_PERIODIC) return false;
+    for (int a = 0; a < 3; a++)
+        if (g->E_ext[a] != 0.0) return false;
+    if (g->layout.off_phi[3] == 0) return false;
+    int coop = 0, sms = 0;
+    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, g->device) != cudaSuccess || !coop) return false;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device) != cudaSuccess || sms < 1) return false;
+    const int64_t seg = (d.n[0] + sms - 1) / sms;
+    return seg + 2 * (kLineBlock + 3) <= line1d::kMaxWindow;
+}
+
+// Runs of steps of the time-blocked 1D kernel on the staggered state: one
+// cooperative launch per run, split at diagnostic steps.
+cudaError_t block1d_step(axp_grid *g, int64_t nsteps)
+{
+    const axp_grid_desc &d = g->desc;
+    int sms = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
+    if (e != cudaSuccess) return e;
+    g->coop_used = true;
+    line1d::Args A;
+    std::memset(&A, 0, sizeof(A));
+    A.n = d.n[0];
+    A.tblock = kLineBlock;
+    A.halo = kLineBlock + 3;
+    A.seg = (int)((d.n[0] + sms - 1) / sms);
+    const int blocks = (int)((d.n[0] + A.seg - 1) / A.seg);
+    const size_t smem = (size_t)line1d::kArrays * (A.seg + 2 * A.halo) * sizeof(double);
+    e = cudaFuncSetAttribute(line1d::k_line1d, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(line1d::kArrays * line1d::kMaxWindow * sizeof(double)));
+    if (e != cudaSuccess) return e;
+    const double dx = d.d[0], dt = d.dt;
+    A.cB = dt / 2.0 / dx;
+    A.c2B = dt / dx;
+    A.h2g = dt * d.g;
+    A.lap_0 = 2.0 - dt * dt * (d.m * d.m + 2.0 / (dx * dx));
+    A.lap_c = dt * dt / (dx * dx);
+    A.dt2g = dt * dt * d.g;
+    A.inv_dt = 1.0 / dt;
+    A.q4dx = 1.0 / (4.0 * dx);
+    for (int a = 0; a < 3; a++) A.Bext[a] = g->B_ext[a];
+    const Workspace &w = g->layout;
+    A.ctr = (unsigned *)(g->ws + w.off_flag);
+    A.err = (int *)(g->ws + w.off_flag) + 1;  // read (and cleared) by the next synchronising call
+    A.absent = g->coop_absent;
+    g->coop_absent = -1;
+    int64_t left = nsteps;
+    while (left > 0) {
+        int64_t k = left;
+        if (d.diag_every > 0) k = std::min<int64_t>(k, d.diag_every - g->step % d.diag_every);
+        const int sets[2] = {g->fset, 1 - g->fset};
+        const int ph[2][2] = {{g->phi_cur_slot, g->phi_b_slot}, {g->phi_next_slot, g->phi_next_b_slot}};
+        for (int p = 0; p < 2; p++) {
+            for (int q = 0; q < 6; q++) {
+                const int fe = q < 3 ? kE0 + q : kE1 + (q - 3), fb = q < 3 ? kB0 + q : kB1 + (q - 3);
+                A.Ew[p][q] = (double *)(g->ws + w.off_fields[sets[p]][fe]);
+                A.Bw[p][q] = (double *)(g->ws + w.off_fields[sets[p]][fb]);
+                A.E[p][q] = A.Ew[p][q];
+                A.B[p][q] = A.Bw[p][q];
+            }
+            A.phi[p][0] = (double *)(g->ws + w.off_phi[ph[p][0]]);
+            A.phi[p][1] = (double *)(g->ws + w.off_phi[ph[p][1]]);
+        }
+        A.nsteps = k;
+        if ((e = cudaMemsetAsync(A.ctr, 0, sizeof(unsigned), g->stream)) != cudaSuccess) return e;
+        void *args[] = {&A};
+        e = cudaLaunchCooperativeKernel((const void *)line1d::k_line1d, dim3(blocks), dim3(line1d::kThreads), args,
+                                        smem, g->stream);
+        if (e != cudaSuccess) return e;
+        g->launches++;
+        A.absent = -1;
+        if (((k + A.tblock - 1) / A.tblock) & 1) {  // the state ended in the other buffer set
+            g->fset = 1 - g->fset;
+            std::swap(g->phi_cur_slot, g->phi_next_slot);
+            std::swap(g->phi_b_slot, g->phi_next_b_slot);
+        }
+        g->step += k;
+        left -= k;
+        if (d.diag_every > 0 && g->step % d.diag_every == 0) {
+            axp_diag *dst = ring_slot(g, g->ring_written);
+            if ((e = diag_compute<double>(g, dst)) != cudaSuccess) return e;
+            g->ring_written++;
+        }
+    }
+    return cudaGetLastError();
+}
+
 template <typename T>
 int32_t fused_path(const axp_grid *g)
 {
     const int32_t k = g->kernel_choice;
     if (k == AXP_KERNEL_GENERAL) return AXP_KERNEL_GENERAL;
+    const bool b1 = block1d_supported(g);
+    if (k == AXP_KERNEL_BLOCK1D) return b1 ? AXP_KERNEL_BLOCK1D : AXP_KERNEL_GENERAL;
+    if (k == AXP_KERNEL_AUTO && b1) return AXP_KERNEL_BLOCK1D;
     const bool tm = tm2d_supported(g), ax = ax3d_supported(g), fu = fused_supported<T>(g);
     if (k == AXP_KERNEL_TM2D) return tm ? AXP_KERNEL_TM2D : AXP_KERNEL_GENERAL;
     if (k == AXP_KERNEL_AX3D) return ax ? AXP_KERNEL_AX3D : AXP_KERNEL_GENERAL;
@@ -294,6 +401,10 @@ cudaError_t fused_step(axp_grid *g, int64_t nsteps, bool *handled)
     const int32_t path = fused_path<T>(g);
     if (path == AXP_KERNEL_GENERAL) return cudaSuccess;
     *handled = true;
+    if (path == AXP_KERNEL_BLOCK1D) {
+        cudaError_t e = enter_staggered<T>(g);
+        return e != cudaSuccess ? e : block1d_step(g, nsteps);
+    }
     const bool tm = path == AXP_KERNEL_TM2D, ax = path == AXP_KERNEL_AX3D;
     const int mode = grid_mode(g);
     const int set = pick_set(g);

@@ -87,13 +87,22 @@ Sheet<T> b_sheet(const axp_grid *g, double t)
 }
 
 // P at every cell centre, into scratch (one evaluation per cell and component).
+// Each stage's work at one cell is a device function; the general kernels loop
+// it over the grid, and the time-blocked 1D kernel over a window in shared memory.
+template <typename T, bool INCR>
+__device__ __forceinline__ void pcell_at(const View<T> &v, const PhiPair<T, INCR> &q, const PBuf<T> &P, int64_t c,
+                                         int64_t i, int64_t j, int64_t k)
+{
+    for (int a = 0; a < 3; a++) P.p[a][c] = p_comp<T, INCR>(v, q, a, i, j, k);
+}
+
 template <typename T, bool INCR>
 __global__ void __launch_bounds__(kThreads) k_pcell(View<T> v, PhiPair<T, INCR> q, PBuf<T> P)
 {
     for (int64_t qv = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; qv < v.Nv; qv += (int64_t)gridDim.x * blockDim.x) {
         int64_t i, j, k;
         const int64_t c = visit(v, qv, &i, &j, &k);
-        for (int a = 0; a < 3; a++) P.p[a][c] = p_comp<T, INCR>(v, q, a, i, j, k);
+        pcell_at<T, INCR>(v, q, P, c, i, j, k);
     }
 }
 
@@ -101,28 +110,35 @@ __global__ void __launch_bounds__(kThreads) k_pcell(View<T> v, PhiPair<T, INCR> 
 // from the scratch where c + a is a grid cell (its periodic image included) and
 // is evaluated in place beyond a non-periodic edge (ghost rules).
 template <typename T, bool INCR>
+__device__ __forceinline__ void current_at(const View<T> &v, const PhiPair<T, INCR> &q, const PBuf<T> &P, int64_t c,
+                                           int64_t i, int64_t j, int64_t k)
+{
+    for (int a = 0; a < 3; a++) {
+        int64_t u[3];
+        unit(a, u);
+        const T p0 = P.p[a][c];
+        int64_t w[3] = {i + u[0], j + u[1], k + u[2]};
+        bool in = true;
+        if (w[a] >= v.n[a]) {
+            // the periodic image is the same evaluation only when both the fields
+            // and the axion wrap along a
+            if (v.periodic[a] && v.axbc[a][0] == AXP_BC_PERIODIC && v.axbc[a][1] == AXP_BC_PERIODIC)
+                w[a] -= v.n[a];
+            else
+                in = false;
+        }
+        const T p1 = in ? P.p[a][lin3(v.n, w[0], w[1], w[2])] : p_comp<T, INCR>(v, q, a, w[0], w[1], w[2]);
+        v.J[a][c] = T(0.5) * (p0 + p1);
+    }
+}
+
+template <typename T, bool INCR>
 __global__ void __launch_bounds__(kThreads) k_current(View<T> v, PhiPair<T, INCR> q, PBuf<T> P)
 {
     for (int64_t qv = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; qv < v.Nv; qv += (int64_t)gridDim.x * blockDim.x) {
         int64_t i, j, k;
         const int64_t c = visit(v, qv, &i, &j, &k);
-        for (int a = 0; a < 3; a++) {
-            int64_t u[3];
-            unit(a, u);
-            const T p0 = P.p[a][c];
-            int64_t w[3] = {i + u[0], j + u[1], k + u[2]};
-            bool in = true;
-            if (w[a] >= v.n[a]) {
-                // the periodic image is the same evaluation only when both the fields
-                // and the axion wrap along a
-                if (v.periodic[a] && v.axbc[a][0] == AXP_BC_PERIODIC && v.axbc[a][1] == AXP_BC_PERIODIC)
-                    w[a] -= v.n[a];
-                else
-                    in = false;
-            }
-            const T p1 = in ? P.p[a][lin3(v.n, w[0], w[1], w[2])] : p_comp<T, INCR>(v, q, a, w[0], w[1], w[2]);
-            v.J[a][c] = T(0.5) * (p0 + p1);
-        }
+        current_at<T, INCR>(v, q, P, c, i, j, k);
     }
 }
 
@@ -159,51 +175,65 @@ __device__ __forceinline__ T curl_e(const View<T> &v, T *const E[3], int a, int6
 // Order 0 may carry the electric sheet: E_y, E_z of the cells at the plane add
 // w tau to their curl.
 template <typename T>
+__device__ __forceinline__ void e_half_at(const View<T> &v, int orders, const Sheet<T> &s, int64_t c, int64_t i,
+                                          int64_t j, int64_t k)
+{
+    const T sig = sigma_of<T>(v.sig_em, i, j, k);
+    if (orders & 1) {
+        T *const B[3] = {v.f[kB0], v.f[kB0 + 1], v.f[kB0 + 2]};
+        for (int a = 0; a < 3; a++) {
+            T X = curl_b(v, B, a, i, j, k);
+            if (i == s.plane && a > 0) X = X + s.w[a - 1][j + v.n[1] * k] * s.tau;
+            v.f[kE0 + a][c] = half_update(v.f[kE0 + a][c], X, sig, v.h);
+        }
+    }
+    if (orders & 2) {
+        T *const B[3] = {v.f[kB1], v.f[kB1 + 1], v.f[kB1 + 2]};
+        for (int a = 0; a < 3; a++) {
+            T X = curl_b(v, B, a, i, j, k);
+            X = X - v.g * v.J[a][c];
+            v.f[kE1 + a][c] = half_update(v.f[kE1 + a][c], X, sig, v.h);
+        }
+    }
+}
+
+template <typename T>
 __global__ void __launch_bounds__(kThreads) k_e_half(View<T> v, int orders, Sheet<T> s)
 {
     for (int64_t qv = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; qv < v.Nv; qv += (int64_t)gridDim.x * blockDim.x) {
         int64_t i, j, k;
         const int64_t c = visit(v, qv, &i, &j, &k);
-        const T sig = sigma_of<T>(v.sig_em, i, j, k);
-        if (orders & 1) {
-            T *const B[3] = {v.f[kB0], v.f[kB0 + 1], v.f[kB0 + 2]};
-            for (int a = 0; a < 3; a++) {
-                T X = curl_b(v, B, a, i, j, k);
-                if (i == s.plane && a > 0) X = X + s.w[a - 1][j + v.n[1] * k] * s.tau;
-                v.f[kE0 + a][c] = half_update(v.f[kE0 + a][c], X, sig, v.h);
-            }
-        }
-        if (orders & 2) {
-            T *const B[3] = {v.f[kB1], v.f[kB1 + 1], v.f[kB1 + 2]};
-            for (int a = 0; a < 3; a++) {
-                T X = curl_b(v, B, a, i, j, k);
-                X = X - v.g * v.J[a][c];
-                v.f[kE1 + a][c] = half_update(v.f[kE1 + a][c], X, sig, v.h);
-            }
-        }
+        e_half_at<T>(v, orders, s, c, i, j, k);
     }
 }
 
 // B half-step of both orders: B <- B - h curl E.  Order 0 may carry the magnetic
 // sheet on the faces at the plane (index plane - 1): B_y adds -w_z tau, B_z +w_y tau.
 template <typename T>
+__device__ __forceinline__ void b_half_at(const View<T> &v, const Sheet<T> &s, int64_t c, int64_t i, int64_t j,
+                                          int64_t k)
+{
+    const T sig = sigma_of<T>(v.sig_em, i, j, k);
+    T *const E0[3] = {v.f[kE0], v.f[kE0 + 1], v.f[kE0 + 2]};
+    T *const E1[3] = {v.f[kE1], v.f[kE1 + 1], v.f[kE1 + 2]};
+    for (int a = 0; a < 3; a++) {
+        T X = -curl_e(v, E0, a, i, j, k);
+        if (i == s.plane - 1 && a > 0) {
+            const int64_t jk = j + v.n[1] * k;
+            X = X + (a == 1 ? -(s.w[1][jk] * s.tau) : s.w[0][jk] * s.tau);
+        }
+        v.f[kB0 + a][c] = half_update(v.f[kB0 + a][c], X, sig, v.h);
+    }
+    for (int a = 0; a < 3; a++) v.f[kB1 + a][c] = half_update(v.f[kB1 + a][c], -curl_e(v, E1, a, i, j, k), sig, v.h);
+}
+
+template <typename T>
 __global__ void __launch_bounds__(kThreads) k_b_half(View<T> v, Sheet<T> s)
 {
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < v.N; c += (int64_t)gridDim.x * blockDim.x) {
         int64_t i, j, k;
         cell_of(c, v.n, &i, &j, &k);
-        const T sig = sigma_of<T>(v.sig_em, i, j, k);
-        T *const E0[3] = {v.f[kE0], v.f[kE0 + 1], v.f[kE0 + 2]};
-        T *const E1[3] = {v.f[kE1], v.f[kE1 + 1], v.f[kE1 + 2]};
-        for (int a = 0; a < 3; a++) {
-            T X = -curl_e(v, E0, a, i, j, k);
-            if (i == s.plane - 1 && a > 0) {
-                const int64_t jk = j + v.n[1] * k;
-                X = X + (a == 1 ? -(s.w[1][jk] * s.tau) : s.w[0][jk] * s.tau);
-            }
-            v.f[kB0 + a][c] = half_update(v.f[kB0 + a][c], X, sig, v.h);
-        }
-        for (int a = 0; a < 3; a++) v.f[kB1 + a][c] = half_update(v.f[kB1 + a][c], -curl_e(v, E1, a, i, j, k), sig, v.h);
+        b_half_at<T>(v, s, c, i, j, k);
     }
 }
 
@@ -213,12 +243,10 @@ __global__ void __launch_bounds__(kThreads) k_b_half(View<T> v, Sheet<T> s)
 //   FP32 split: pi^{n+1} = phi^{n+3/2} - phi^{n+1/2} replaces pi^n in place and
 //   phi^{n+3/2} = phi^{n+1/2} + pi^{n+1} goes to phi_next.
 template <typename T, bool INCR>
-__global__ void __launch_bounds__(kThreads) k_axion(View<T> v, Ghosts<T> gcur)
+__device__ __forceinline__ void axion_at(const View<T> &v, const Ghosts<T> &gcur, T dt2, int64_t c, int64_t i,
+                                         int64_t j, int64_t k)
 {
-    const T dt2 = v.dt * v.dt;
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < v.N; c += (int64_t)gridDim.x * blockDim.x) {
-        int64_t i, j, k;
-        cell_of(c, v.n, &i, &j, &k);
+    {
         const T S = source_at(v, i, j, k);
         const T ph = v.phi_cur[c];
         T lap = T(0);
@@ -254,6 +282,17 @@ __global__ void __launch_bounds__(kThreads) k_axion(View<T> v, Ghosts<T> gcur)
             v.phi_b[c] = nin;
             v.phi_next[c] = ph + nin;
         }
+    }
+}
+
+template <typename T, bool INCR>
+__global__ void __launch_bounds__(kThreads) k_axion(View<T> v, Ghosts<T> gcur)
+{
+    const T dt2 = v.dt * v.dt;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < v.N; c += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i, j, k;
+        cell_of(c, v.n, &i, &j, &k);
+        axion_at<T, INCR>(v, gcur, dt2, c, i, j, k);
     }
 }
 

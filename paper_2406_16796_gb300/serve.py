@@ -59,10 +59,19 @@ class ServeStats:
         done = len(self.records)
         first = min(r.arrival for r in self.records)
         last = max(r.finished for r in self.records)
-        return {"requests": done, "sims_per_s": done / max(last - first, 1e-9), "wall_s": self.wall_s,
-                "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
-                "mean_latency_s": float(lat.mean()), "rounds": self.rounds, "gpu_launches": self.launches,
-                "max_live": self.max_live}
+        out = {"requests": done, "sims_per_s": done / max(last - first, 1e-9), "wall_s": self.wall_s,
+               "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+               "mean_latency_s": float(lat.mean()), "p99_tail_samples": int((lat >= np.percentile(lat, 99)).sum()),
+               "rounds": self.rounds, "gpu_launches": self.launches, "max_live": self.max_live}
+        # per class (1D and 2D requests)
+        for nd in (1, 2):
+            cl = np.array([r.latency for r in self.records if r.ndim == nd])
+            if len(cl):
+                out["class_%dd" % nd] = {"requests": int(len(cl)), "p50_latency_s": float(np.percentile(cl, 50)),
+                                         "p99_latency_s": float(np.percentile(cl, 99)),
+                                         "mean_latency_s": float(cl.mean()),
+                                         "p99_tail_samples": int((cl >= np.percentile(cl, 99)).sum())}
+        return out
 
 
 def batch_instance(r: W.Request):

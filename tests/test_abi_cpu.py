@@ -14,7 +14,7 @@ from paper_2406_16796_gb300 import workloads as W
 def header_functions():
     src = open(_build.INCLUDE + "/axp.h").read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_]+\s*\*?\s*(axp_[a-z_]+)\s*\(", src, flags=re.M)))
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_]+\s*\*?\s*(axp_[a-z0-9_]+)\s*\(", src, flags=re.M)))
 
 
 def test_library_exports_every_declared_function():
@@ -24,7 +24,7 @@ def test_library_exports_every_declared_function():
     for n in names:
         assert hasattr(L, n), n
     out = subprocess.run(["nm", "-D", "--defined-only", _build.LIB], capture_output=True, text=True).stdout
-    exported = set(re.findall(r"\bT (axp_[a-z_]+)\b", out))
+    exported = set(re.findall(r"\bT (axp_[a-z0-9_]+)\b", out))
     assert set(names) <= exported
 
 

@@ -256,9 +256,14 @@ def test_fused_vs_oracle(case, prec):
         expect = axp.AXP_KERNEL_AX3D  # periodic 3D without laser fields: the specialised kernel
     elif case.startswith("3d") and prec == "fp64":
         expect = axp.AXP_KERNEL_GENERAL
+    elif case.startswith("1d") and prec == "fp64":
+        expect = axp.AXP_KERNEL_BLOCK1D  # periodic FP64 line: the time-blocked kernel
     else:
         expect = axp.AXP_KERNEL_FUSED
     assert g.kernel_path() == expect
+    if case.startswith("1d"):
+        g.set_kernel(axp.AXP_KERNEL_FUSED)  # the single-pass kernel is what this test checks
+        assert g.kernel_path() == axp.AXP_KERNEL_FUSED
     og.step(12)
     g.step(12)
     ref, got = og.fields(), g.fields()
@@ -414,6 +419,7 @@ def test_1d_graph_replay_matches_single_launches(prec):
     st = W.random_state(grid, seed=606, active=["E0y", "B0z"] + [n for n in W.FIELD_NAMES if n[1] == "1"])
     a, b = axp.Grid(grid), axp.Grid(grid)
     for x in (a, b):
+        x.set_kernel(axp.AXP_KERNEL_FUSED)
         x.load(st)
     a.step(100)  # two graph replays and four single launches
     for _ in range(100):

@@ -8,7 +8,8 @@ the conversion and centroid diagnostics against the oracle on the GPU.
 * 3D axion box (dx = lambda/16, CFL 0.95, axion plane wave 1e-2 along x, B_ext
   along y, periodic): all 2000 steps on a 32^3 box (two wavelengths per axis,
   with a weak oblique second wave so that every axis varies), FP32 split on
-  the 3D axion-box kernel against the FP64 oracle: fields <= 1e-4, P_a2g <= 1e-3.
+  the 3D axion-box kernel against the FP64 oracle: order-1 fields (as a group)
+  and phi <= 1e-4, P_a2g <= 1e-3.
 * 2D pulse (dx = lambda/32, CFL 0.95/sqrt(2), E_z Gaussian pulse, B_ext along z,
   PML along y): 4000 steps on 320 x 160 cells, periodic along x so that the
   pulse stays in the box for the whole run, m in {0, pi}, FP32 split on the 2D
@@ -32,6 +33,15 @@ def rel(a, b):
     return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
 
 
+def rel_group(got, ref, names):
+    """Normwise relative error of a group of fields taken together (a component
+    that is zero in exact arithmetic holds only rounding noise of each side, so
+    it is measured against its group)."""
+    num = math.sqrt(sum(np.linalg.norm(got[k] - ref[k]) ** 2 for k in names))
+    den = math.sqrt(sum(np.linalg.norm(ref[k]) ** 2 for k in names))
+    return num / den
+
+
 def yee_theta(k, d, dt):
     """th = w dt of the Yee (and massless Klein-Gordon) dispersion
     sin(w dt/2)/dt = sqrt(sum_d sin^2(k_d d_d/2)/d_d^2)."""
@@ -40,11 +50,19 @@ def yee_theta(k, d, dt):
 
 
 def test_1d_conversion_full_run_matches_oracle_and_closed_form():
+    """All 20000 steps.  The fields are compared from the same initial bits (the
+    oracle's injected laser loaded into the grid): the run is sensitive enough
+    that the last-bit differences of the two sides' injections (checked to 1e-13
+    on their own) grow to about 1e-12 over it.  P is also compared for the
+    grid's own injection."""
     from paper_2406_16796_gb300 import axp
 
     w = W.vacuum_1d(nx=4096)
     assert w.steps == 20000
-    og = oracle.run_workload(w)
+    og = oracle.OracleGrid(w.grid)
+    og.inject_laser(w.lasers[0])
+    start = og.fields()
+    og.step(w.steps)
     ref = og.fields()
     dr = og.diagnostics()
     th = yee_theta(w.lasers[0].k, w.grid.d, w.grid.dt)
@@ -52,20 +70,35 @@ def test_1d_conversion_full_run_matches_oracle_and_closed_form():
     assert dr["t"] == pytest.approx(593.75)
     assert abs(dr["P_g2a"] / closed - 1.0) < 5e-3
     for prec in ("fp64", "fp32"):
-        g = axp.Grid(w.grid.replace(precision=prec))
-        g.inject_laser(w.lasers[0])
-        g.step(w.steps)
-        d = g.diagnostics()
-        assert d["step"] == 20000
-        if prec == "fp64":
-            got = g.fields()
-            for k in ("E0y", "B0z", "E1y", "E1z", "B1y", "B1z", "phi_cur", "phi_old"):
-                assert rel(got[k], ref[k]) < 1e-12, (k, rel(got[k], ref[k]))
-            assert abs(d["P_g2a"] / dr["P_g2a"] - 1.0) < 1e-12, (d["P_g2a"], dr["P_g2a"])
-        else:
-            assert abs(d["P_g2a"] / dr["P_g2a"] - 1.0) < 1e-3, (d["P_g2a"], dr["P_g2a"])
-        assert abs(d["P_g2a"] / closed - 1.0) < 5e-3
-        g.close()
+        for own_injection in (False, True):
+            g = axp.Grid(w.grid.replace(precision=prec))
+            if own_injection:
+                g.inject_laser(w.lasers[0])
+            else:
+                g.load(start)
+            # FP64: the time-blocked 1D kernel
+            assert g.kernel_path() == (axp.AXP_KERNEL_BLOCK1D if prec == "fp64" else axp.AXP_KERNEL_FUSED)
+            g.step(w.steps)
+            d = g.diagnostics()
+            assert d["step"] == 20000
+            if prec == "fp64" and not own_injection:
+                got = g.fields()
+                for k in ("E0y", "B0z", "E1y", "E1z", "B1y", "B1z", "phi_cur", "phi_old"):
+                    assert rel(got[k], ref[k]) < 1e-12, (k, rel(got[k], ref[k]))
+                # and the one-launch-per-step single-pass kernel over the same run
+                f = axp.Grid(w.grid)
+                f.set_kernel(axp.AXP_KERNEL_FUSED)
+                f.load(start)
+                f.step(w.steps)
+                gotf = f.fields()
+                f.close()
+                # (its differently ordered roundings drift to 1.3e-12 over the 20000 steps)
+                for k in ("E0y", "B0z", "E1y", "E1z", "B1y", "B1z", "phi_cur", "phi_old"):
+                    assert rel(gotf[k], ref[k]) < 2e-12, ("fused", k, rel(gotf[k], ref[k]))
+            tolP = 1e-10 if prec == "fp64" else 1e-3
+            assert abs(d["P_g2a"] / dr["P_g2a"] - 1.0) < tolP, (prec, own_injection, d["P_g2a"], dr["P_g2a"])
+            assert abs(d["P_g2a"] / closed - 1.0) < 5e-3
+            g.close()
 
 
 def axion_box_32():
@@ -92,8 +125,9 @@ def test_3d_axion_box_full_run_fp32_matches_oracle():
     g.step(w.steps)
     got, d = g.fields(), g.diagnostics()
     g.close()
-    for k in ("E1x", "E1y", "E1z", "B1x", "B1y", "B1z", "phi_cur"):
-        assert rel(got[k], ref[k]) < 1e-4, (k, rel(got[k], ref[k]))
+    order1 = ("E1x", "E1y", "E1z", "B1x", "B1y", "B1z")
+    assert rel_group(got, ref, order1) < 1e-4, rel_group(got, ref, order1)
+    assert rel(got["phi_cur"], ref["phi_cur"]) < 1e-4, rel(got["phi_cur"], ref["phi_cur"])
     assert abs(d["P_a2g"] / dr["P_a2g"] - 1.0) < 1e-3, (d["P_a2g"], dr["P_a2g"])
     assert dr["P_a2g"] > 0
 
