@@ -274,9 +274,10 @@ def bytes_per_cell(prec):
 # one-pass stencil grows with the cells); None until a capture of the kernel as
 # it stands exists.  Sources are summarised under profiles/.
 TRAFFIC = {
-    # k_tm2d, 2048 x 2048 captures: FP64 688.8 MB, FP32 split 344.2 MB per launch
+    # k_tm2d, 2048 x 2048 capture: FP64 688.8 MB per launch
     ("k_tm2d (one launch per step)", "fp64"): 688.8e6 * (4096 * 2048) / (2048 * 2048),
-    ("k_tm2d (one launch per step)", "fp32"): 344.2e6 * (4096 * 2048) / (2048 * 2048),
+    # k_tm2d_x2 (FP32 split, two columns per thread): no capture of it yet
+    ("k_tm2d_x2 (one launch per step)", "fp32"): None,
 }
 # k_ax3d (3D, no order-0 fields), 256^3 capture: 1076.3 MB per launch
 TRAFFIC_3D_PER_CELL = 1076.3e6 / 256 ** 3
@@ -695,11 +696,13 @@ def gpu_arm(args):
         el32, l32 = timed_run(g32, k32, args.warmup, g32.stream)
         per32 = el32 / max(1, l32)
         ach = bytes_per_cell("fp32") * cells / per32 / 1e9
+        # FP32 split on an even-width grid takes the two-column form of the 2D kernel
+        kern32 = "k_tm2d_x2 (one launch per step)" if (path == axp.AXP_KERNEL_TM2D and args.nx % 2 == 0) else kern
         other = {"precision": "fp32_split", "value": cells * k32 * world / el32, "unit": "cell-updates/s",
-                 "steps": k32, "ms_per_step": el32 / k32 * 1e3,
+                 "steps": k32, "ms_per_step": el32 / k32 * 1e3, "kernel": kern32,
                  "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
                               "frac": ach / hbm_peak, "peak_source": hbm_src,
-                              "traffic": TRAFFIC.get((kern, "fp32")) if args.nx * args.ny == NX * NY else None,
+                              "traffic": TRAFFIC.get((kern32, "fp32")) if args.nx * args.ny == NX * NY else None,
                               "algorithmic_bytes_per_cell": bytes_per_cell("fp32")}}
         g32.close()
 

@@ -9,6 +9,7 @@
 #include "kernels_ax3d.cuh"
 #include "kernels_line1d.cuh"
 #include "kernels_tm2d.cuh"
+#include "kernels_tm2d_x2.cuh"
 
 namespace axp {
 
@@ -18,6 +19,7 @@ cudaError_t fused_dispatch_f32(int mode, int set, const fused::Params<float> &P,
                                int *occ);
 cudaError_t tm2d_dispatch_f64(const fused::Params<double> &P, int nchunks, cudaStream_t s, int *occ, int tx);
 cudaError_t tm2d_dispatch_f32(const fused::Params<float> &P, int nchunks, cudaStream_t s, int *occ, int tx);
+cudaError_t tm2d_x2_dispatch_f32(const fused::Params<float> &P, int nchunks, cudaStream_t s, int *occ, int cols);
 cudaError_t ax3d_dispatch_f64(const fused::Params<double> &P, int nchunks, cudaStream_t s, int *occ);
 cudaError_t ax3d_dispatch_f32(const fused::Params<float> &P, int nchunks, cudaStream_t s, int *occ);
 
@@ -103,6 +105,20 @@ bool ax3d_supported(const axp_grid *g)
 // the axion, no uniform background E, at most 2^32 cells.  A soft source is
 // taken when it drives E0z only (its polarisation along z keeps the closure
 // inside the set).
+bool tm2d_supported(const axp_grid *g);
+
+// The two-column form of the 2D kernel: FP32 split, an even number of columns (a
+// pair never straddles the grid's edge and stays 8-byte aligned), no soft source.
+template <typename T>
+bool tm2d_x2_eligible(const axp_grid *g)
+{
+#ifdef AXP_TM2D_ONE_COLUMN
+    return false;
+#else
+    return sizeof(T) == 4 && !g->src_on && g->desc.n[0] % 2 == 0 && tm2d_supported(g);
+#endif
+}
+
 bool tm2d_supported(const axp_grid *g)
 {
     if (grid_mode(g) != 2) return false;
@@ -411,8 +427,16 @@ cudaError_t fused_step(axp_grid *g, int64_t nsteps, bool *handled)
     cudaError_t e = enter_staggered<T>(g);
     if (e != cudaSuccess) return e;
     int tm_tx = tm2d::TX;  // tile width of the 2D kernel (chosen below)
+    // FP32 split on an even-width grid without a soft source: the two-column form
+    const bool x2 = tm && tm2d_x2_eligible<T>(g);
+    auto dispatch_2d = [&](const fused::Params<T> &Pl, int nch, int *occp, int width) -> cudaError_t {
+        if constexpr (sizeof(T) == 4) {
+            if (x2) return tm2d_x2_dispatch_f32(Pl, nch, g->stream, occp, width);
+        }
+        return dispatch_tm2d<T>(Pl, nch, g->stream, occp, width);
+    };
     auto launch = [&](const fused::Params<T> &Pl, int nch, int *occp) {
-        if (tm) return dispatch_tm2d<T>(Pl, nch, g->stream, occp, tm_tx);
+        if (tm) return dispatch_2d(Pl, nch, occp, tm_tx);
         if (ax) return dispatch_ax3d<T>(Pl, nch, g->stream, occp);
         return dispatch<T>(mode, set, Pl, nch, g->stream, occp);
     };
@@ -481,10 +505,14 @@ cudaError_t fused_step(axp_grid *g, int64_t nsteps, bool *handled)
         };
         double best = -1.0;
         int best_ce = 0, best_rows = 0, best_cf = 0;
-        for (int tx = tm2d::TX; tx >= 128; tx -= 32) {
+        // tile widths in columns; the two-column form takes multiples of 64 (tx / 2 threads)
+        const int halo = x2 ? tm2d_x2::HL + tm2d_x2::HR : tm2d::HL + tm2d::HR;
+        for (int tx = tm2d::TX; tx >= 128; tx -= x2 ? 64 : 32) {
             int o = 0;
-            if ((e = dispatch_tm2d<T>(P, 0, g->stream, &o, tx)) != cudaSuccess) return e;
+            if ((e = dispatch_2d(P, 0, &o, tx)) != cudaSuccess) return e;
             o = o > 0 ? o : 1;
+            // warps of one-column threads holding as many columns (the two-column form
+            // runs half as many threads with twice the work each)
             const double warps = (double)o * tx / 32.0;
             double u = warps >= 8.0 ? 1.0 : std::sqrt(warps / 8.0);
             if (sizeof(T) == 4) {
@@ -495,10 +523,14 @@ cudaError_t fused_step(axp_grid *g, int64_t nsteps, bool *handled)
                 if (o > 2) u *= kManyBlocks;
             }
             if (o < 2) u *= kOneBlock;
-            const int64_t strips = (nx + (tx - tm2d::HL - tm2d::HR) - 1) / (tx - tm2d::HL - tm2d::HR);
+            const int64_t strips = (nx + (tx - halo) - 1) / (tx - halo);
             const int64_t slots = (int64_t)sms * o;
             const double r = xedge ? kEdgeCost : 1.0;
-            for (int64_t nc = 1; nc <= 64 && ny / nc >= 16; nc++) {  // the same chunks everywhere
+            // a grid too small to give every resident block a chunk of 16 planes takes
+            // chunks down to 4 planes: the pipeline's extra planes then cost less than
+            // the SMs they would leave idle (small grids are latency-bound)
+            const int64_t min_chunk = strips * (ny / 16) < slots ? 4 : 16;
+            for (int64_t nc = 1; nc <= 512 && ny / nc >= min_chunk; nc++) {  // the same chunks everywhere
                 const int64_t chunk = (ny + nc - 1) / nc, rows = (ny + chunk - 1) / chunk;
                 const int64_t waves = (strips * rows + slots - 1) / slots;
                 const double cost = (double)waves * (double)(chunk + 6 + D) * r * tx * o / u;

@@ -2,6 +2,7 @@
 #include "kernels_fused_inst.cuh"
 #include "kernels_tm2d.cuh"
 #include "kernels_ax3d.cuh"
+#include "kernels_tm2d_x2.cuh"
 
 namespace axp {
 cudaError_t fused_dispatch_f32(int mode, int set, const fused::Params<float> &P, int nchunks, cudaStream_t s,
@@ -13,6 +14,11 @@ cudaError_t fused_dispatch_f32(int mode, int set, const fused::Params<float> &P,
 cudaError_t tm2d_dispatch_f32(const fused::Params<float> &P, int nchunks, cudaStream_t s, int *occ, int tx)
 {
     return tm2d::launch<float, true>(P, nchunks, s, occ, tx);
+}
+
+cudaError_t tm2d_x2_dispatch_f32(const fused::Params<float> &P, int nchunks, cudaStream_t s, int *occ, int cols)
+{
+    return tm2d_x2::launch(P, nchunks, s, occ, cols);
 }
 
 cudaError_t ax3d_dispatch_f32(const fused::Params<float> &P, int nchunks, cudaStream_t s, int *occ)
