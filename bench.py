@@ -276,8 +276,8 @@ def bytes_per_cell(prec):
 TRAFFIC = {
     # k_tm2d, 2048 x 2048 capture: FP64 688.8 MB per launch
     ("k_tm2d (one launch per step)", "fp64"): 688.8e6 * (4096 * 2048) / (2048 * 2048),
-    # k_tm2d_x2 (FP32 split, two columns per thread): no capture of it yet
-    ("k_tm2d_x2 (one launch per step)", "fp32"): None,
+    # k_tm2d_x2 (FP32 split, two columns per thread), 2048 x 2048 capture: 345.0 MB per launch
+    ("k_tm2d_x2 (one launch per step)", "fp32"): 345.0e6 * (4096 * 2048) / (2048 * 2048),
 }
 # k_ax3d (3D, no order-0 fields), 256^3 capture: 1076.3 MB per launch
 TRAFFIC_3D_PER_CELL = 1076.3e6 / 256 ** 3
