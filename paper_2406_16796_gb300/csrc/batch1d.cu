@@ -83,6 +83,16 @@ __device__ __forceinline__ float pick(const float (&a)[kK], int j)
     return v;
 }
 
+// Packed FP32 pairs (the sm_100 pair pipe): one instruction for two cells, the
+// same IEEE operation on each lane as the scalar form, so a cell's bits do not
+// depend on which form advanced it.
+__device__ __forceinline__ float2 p2(float s) { return make_float2(s, s); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+// a - b as a + b (-1): one rounding, the subtraction's bits
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+
 // One launch: every work item advances min(budget, remaining) steps.
 //
 // Thread t holds cells [t K, t K + K) of the item (of n cells) in registers.
@@ -207,7 +217,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_batch_block(Dev D, int budget, 
                 const float midm = j > 0 ? MID[j - 1] : lmid;
                 const float Dt = PI[j] * inv_dt;
                 const float Py = Dt * By;
-                const float bz = 0.5f * (B0[j] + pB0) + Bz;
+                const float bz = fmaf(0.5f, B0[j] + pB0, Bz);
                 const float Pz = fmaf(E0[j], (midp - midm) * hidx, Dt * bz);
                 // E1^{n+3/2} = E1^{n+1/2} + 2h (curl B1 - g J), (curl B1)_y = -D_x B1z,
                 // (curl B1)_z = D_x B1y; E0y^{n+3/2} = E0y^{n+1} + h (curl B0)_y
@@ -228,20 +238,138 @@ __global__ void __launch_bounds__(kMaxThreads) k_batch_block(Dev D, int budget, 
         };
         // Threads past the item's last cell only keep the barriers: no thread that
         // holds cells has them as neighbours (the item's last thread clamps or wraps).
-        const bool full = cnt == kK, idle = cnt == 0;
-        using Full = std::integral_constant<bool, true>;
+        // The pair path runs a whole warp's threads or none of them: its barriers are
+        // other instructions than the scalar path's, and all threads of a warp must
+        // meet at the same barrier instruction.  (Threads holding K cells in a warp
+        // with a partial or idle thread take the scalar path, to the same bits.)
+#ifdef AXP_BATCH_SCALAR
+        const bool full = false, idle = cnt == 0;
+#else
+        const bool full = __all_sync(0xffffffffu, cnt == kK), idle = cnt == 0;
+#endif
         using Part = std::integral_constant<bool, false>;
-        for (int st = 0; st < T; st++) {
-            const int pb = st & 1;
-            if (full) stage1(Full{});
-            else if (!idle) stage1(Part{});
-            __syncthreads();
-            if (full) stage2(Full{}, pb);
-            else if (!idle) stage2(Part{}, pb);
-            __syncthreads();
-            if (full) stage3(Full{}, pb);
-            else if (!idle) stage3(Part{}, pb);
-            __syncthreads();
+        if (full) {
+            // A full run of K cells advances on the pair pipe.  Pair q holds cells
+            // (q, q + K/2), so the neighbour of pair q is pair q +- 1, and only the
+            // run's end pairs take one cell from a neighbouring thread.
+            constexpr int Q = kK / 2;
+            float2 pE0[Q], pB0[Q], pE1y[Q], pE1z[Q], pB1y[Q], pB1z[Q], pPH[Q], pPI[Q], pMID[Q];
+#pragma unroll
+            for (int q = 0; q < Q; q++) {
+                pE0[q] = make_float2(E0[q], E0[q + Q]);
+                pB0[q] = make_float2(B0[q], B0[q + Q]);
+                pE1y[q] = make_float2(E1y[q], E1y[q + Q]);
+                pE1z[q] = make_float2(E1z[q], E1z[q + Q]);
+                pB1y[q] = make_float2(B1y[q], B1y[q + Q]);
+                pB1z[q] = make_float2(B1z[q], B1z[q + Q]);
+                pPH[q] = make_float2(PH[q], PH[q + Q]);
+                pPI[q] = make_float2(PI[q], PI[q + Q]);
+                pMID[q] = make_float2(0.f, 0.f);
+            }
+            // cells i + 1 and i - 1 of pair q, given the neighbouring threads' end cells
+            auto right = [&](const float2 (&a)[Q], int q, float r) {
+                return q + 1 < Q ? a[q + 1] : make_float2(a[0].y, r);
+            };
+            auto left = [&](const float2 (&a)[Q], int q, float l) {
+                return q > 0 ? a[q - 1] : make_float2(l, a[Q - 1].x);
+            };
+            const float2 mh2x = p2(-h2x), ph2x = p2(h2x), mhx = p2(-hx), mh2g = p2(-h2g);
+            for (int st = 0; st < T; st++) {
+                const int pb = st & 1;
+                {  // stage 1: B^{n+1}
+                    const float rE0 = tr >= 0 ? fE0[tr] : pE0[Q - 1].y, rE1y = tr >= 0 ? fE1y[tr] : pE1y[Q - 1].y;
+                    const float rE1z = tr >= 0 ? fE1z[tr] : pE1z[Q - 1].y;
+                    float2 n0[Q], n1y[Q], n1z[Q];
+#pragma unroll
+                    for (int q = 0; q < Q; q++) {
+                        n0[q] = fma2(mh2x, sub2(right(pE0, q, rE0), pE0[q]), pB0[q]);
+                        n1y[q] = fma2(ph2x, sub2(right(pE1z, q, rE1z), pE1z[q]), pB1y[q]);
+                        n1z[q] = fma2(mh2x, sub2(right(pE1y, q, rE1y), pE1y[q]), pB1z[q]);
+                    }
+#pragma unroll
+                    for (int q = 0; q < Q; q++) {
+                        pB0[q] = n0[q];
+                        pB1y[q] = n1y[q];
+                        pB1z[q] = n1z[q];
+                    }
+                    lB0[t] = pB0[Q - 1].y;
+                    lB1y[t] = pB1y[Q - 1].y;
+                    lB1z[t] = pB1z[Q - 1].y;
+                }
+                __syncthreads();
+                {  // stage 2: axion; E0y^{n+1}
+                    const float lph = tl >= 0 ? lPH[pb][tl] : pPH[0].x, rph = tr >= 0 ? fPH[pb][tr] : pPH[Q - 1].y;
+                    const float lB = tl >= 0 ? lB0[tl] : pB0[0].x;
+                    float2 pin[Q], e0n[Q];
+#pragma unroll
+                    for (int q = 0; q < Q; q++) {
+                        const float2 ph = pPH[q];
+                        const float2 d2 = add2(sub2(right(pPH, q, rph), ph), sub2(left(pPH, q, lph), ph));
+                        pin[q] = fma2(p2(dt2g), mul2(pE0[q], p2(By)), fma2(p2(cx), d2, fma2(p2(c0m), ph, pPI[q])));
+                        e0n[q] = fma2(mhx, sub2(pB0[q], left(pB0, q, lB)), pE0[q]);
+                    }
+#pragma unroll
+                    for (int q = 0; q < Q; q++) {
+                        pPI[q] = pin[q];
+                        pMID[q] = fma2(p2(0.5f), pin[q], pPH[q]);
+                        pE0[q] = e0n[q];
+                    }
+                    fMID[t] = pMID[0].x;
+                    lMID[t] = pMID[Q - 1].y;
+                }
+                __syncthreads();
+                {  // stage 3: current, E updates
+                    const float lmid = tl >= 0 ? lMID[tl] : pMID[0].x, rmid = tr >= 0 ? fMID[tr] : pMID[Q - 1].y;
+                    const float lB = tl >= 0 ? lB0[tl] : pB0[0].x, lBz1 = tl >= 0 ? lB1z[tl] : pB1z[0].x;
+                    const float lBy1 = tl >= 0 ? lB1y[tl] : pB1y[0].x;
+                    float2 e1y[Q], e1z[Q], e0[Q];
+#pragma unroll
+                    for (int q = 0; q < Q; q++) {
+                        const float2 Dt = mul2(pPI[q], p2(inv_dt));
+                        const float2 Py = mul2(Dt, p2(By));
+                        const float2 bz = fma2(p2(0.5f), add2(pB0[q], left(pB0, q, lB)), p2(Bz));
+                        const float2 dm = mul2(sub2(right(pMID, q, rmid), left(pMID, q, lmid)), p2(hidx));
+                        const float2 Pz = fma2(pE0[q], dm, mul2(Dt, bz));
+                        e1y[q] = fma2(mh2x, sub2(pB1z[q], left(pB1z, q, lBz1)), fma2(mh2g, Py, pE1y[q]));
+                        e1z[q] = fma2(ph2x, sub2(pB1y[q], left(pB1y, q, lBy1)), fma2(mh2g, Pz, pE1z[q]));
+                        e0[q] = fma2(mhx, sub2(pB0[q], left(pB0, q, lB)), pE0[q]);
+                    }
+#pragma unroll
+                    for (int q = 0; q < Q; q++) {
+                        pE1y[q] = e1y[q];
+                        pE1z[q] = e1z[q];
+                        pE0[q] = e0[q];
+                        pPH[q] = add2(pPH[q], pPI[q]);
+                    }
+                    fE0[t] = pE0[0].x;
+                    fE1y[t] = pE1y[0].x;
+                    fE1z[t] = pE1z[0].x;
+                    fPH[pb ^ 1][t] = pPH[0].x;
+                    lPH[pb ^ 1][t] = pPH[Q - 1].y;
+                }
+                __syncthreads();
+            }
+#pragma unroll
+            for (int q = 0; q < Q; q++) {
+                E0[q] = pE0[q].x, E0[q + Q] = pE0[q].y;
+                B0[q] = pB0[q].x, B0[q + Q] = pB0[q].y;
+                E1y[q] = pE1y[q].x, E1y[q + Q] = pE1y[q].y;
+                E1z[q] = pE1z[q].x, E1z[q + Q] = pE1z[q].y;
+                B1y[q] = pB1y[q].x, B1y[q + Q] = pB1y[q].y;
+                B1z[q] = pB1z[q].x, B1z[q + Q] = pB1z[q].y;
+                PH[q] = pPH[q].x, PH[q + Q] = pPH[q].y;
+                PI[q] = pPI[q].x, PI[q + Q] = pPI[q].y;
+            }
+        } else {
+            for (int st = 0; st < T; st++) {
+                const int pb = st & 1;
+                if (!idle) stage1(Part{});
+                __syncthreads();
+                if (!idle) stage2(Part{}, pb);
+                __syncthreads();
+                if (!idle) stage3(Part{}, pb);
+                __syncthreads();
+            }
         }
         // write the valid core cells to the other buffer
 #pragma unroll

@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "kernels_tm2d.cuh"
+#include "kernels_tm2d_x2.cuh"
 
 namespace axp {
 
@@ -68,9 +69,23 @@ GLayout glayout(int32_t max_grids, int32_t max_tiles)
     return L;
 }
 
-__global__ void __launch_bounds__(tm2d::TX, 2) k_tm2d_group(GDev D)
+// Blocks of kGroupThreads threads.  A member of even width takes tiles of the
+// two-column form (2 kGroupThreads columns per tile); a member of odd width the
+// one-column tile body (kGroupThreads columns).
+constexpr int kGroupThreads = tm2d_x2::NTX;
+constexpr int kVxPair = 2 * kGroupThreads - tm2d_x2::HL - tm2d_x2::HR;  // written columns per tile
+constexpr int kVxOne = kGroupThreads - tm2d::HL - tm2d::HR;
+constexpr size_t kGroupStage = tm2d_x2::stage_bytes(kGroupThreads);
+static_assert(tm2d::stage_bytes<float>(kGroupThreads) <= kGroupStage, "one staging buffer serves both forms");
+
+__host__ __device__ inline int group_vx(int64_t nx) { return nx % 2 == 0 ? kVxPair : kVxOne; }
+
+__global__ void __launch_bounds__(kGroupThreads, 2) k_tm2d_group(GDev D)
 {
-    __shared__ float rows[2][tm2d::NROWS][tm2d::RS];
+    // the published rows of either form
+    constexpr size_t kRowsOne = sizeof(float) * 2 * tm2d::NROWS * tm2d::RS;
+    constexpr size_t kRowsPair = sizeof(float2) * 2 * tm2d_x2::NROWS * tm2d_x2::RS;
+    __shared__ __align__(16) unsigned char rows_raw[kRowsOne > kRowsPair ? kRowsOne : kRowsPair];
     extern __shared__ __align__(16) unsigned char group_dyn[];
     __shared__ fused::Params<float> sP;
     __shared__ int s_item;
@@ -91,9 +106,15 @@ __global__ void __launch_bounds__(tm2d::TX, 2) k_tm2d_group(GDev D)
         const int64_t done = s_done;
         if (done < __ldcg(D.steps + I.member)) {
             const int *src = (const int *)(D.params + 2 * (size_t)I.member + (done & 1));
-            for (int k = threadIdx.x; k < kWords; k += tm2d::TX) ((int *)&sP)[k] = src[k];
+            for (int k = threadIdx.x; k < kWords; k += kGroupThreads) ((int *)&sP)[k] = src[k];
             __syncthreads();
-            tm2d::tile<float, true>(sP, I.bx, I.by, rows, reinterpret_cast<float *>(group_dyn));
+            if (sP.n[0] % 2 == 0)
+                tm2d_x2::tile(sP, I.bx, I.by,
+                              *reinterpret_cast<float2(*)[2][tm2d_x2::NROWS][tm2d_x2::RS]>(rows_raw),
+                              reinterpret_cast<float2 *>(group_dyn));
+            else
+                tm2d::tile<float, true>(sP, I.bx, I.by, *reinterpret_cast<float(*)[2][tm2d::NROWS][tm2d::RS]>(rows_raw),
+                                        reinterpret_cast<float *>(group_dyn));
             __syncthreads();
             if (threadIdx.x == 0) {
                 __threadfence();  // this tile's stores before the count that publishes them
@@ -160,7 +181,8 @@ void drop_graph(axp_group *G)
 
 int32_t tiles_of(const axp_grid *g, int32_t chunk)
 {
-    const int64_t strips = (g->desc.n[0] + tm2d::VX - 1) / tm2d::VX;
+    const int vx = group_vx(g->desc.n[0]);
+    const int64_t strips = (g->desc.n[0] + vx - 1) / vx;
     const int64_t chunks = (g->desc.n[1] + chunk - 1) / chunk;
     return (int32_t)(strips * chunks);
 }
@@ -171,7 +193,8 @@ axp_status rebuild(axp_group *G)
     for (int m = 0; m < G->max_grids; m++) {
         const auto &M = G->members[m];
         if (!M.active) continue;
-        const int strips = (int)((M.g->desc.n[0] + tm2d::VX - 1) / tm2d::VX);
+        const int vx = group_vx(M.g->desc.n[0]);
+        const int strips = (int)((M.g->desc.n[0] + vx - 1) / vx);
         const int chunks = (int)((M.g->desc.n[1] + G->chunk - 1) / G->chunk);
         for (int by = 0; by < chunks; by++)
             for (int bx = 0; bx < strips; bx++) items.push_back({m, bx, by, 0});
@@ -192,7 +215,7 @@ cudaError_t enqueue(axp_group *G, int64_t nsteps)
 {
     const int grid = std::max(1, std::min(G->grid_blocks, G->D.nitems));
     for (int64_t s = 0; s < nsteps; s++) {
-        k_tm2d_group<<<grid, tm2d::TX, tm2d::stage_bytes<float>(), G->stream>>>(G->D);
+        k_tm2d_group<<<grid, kGroupThreads, kGroupStage, G->stream>>>(G->D);
         G->launches++;
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -246,10 +269,9 @@ axp_status axp_group_create(int32_t max_grids, int32_t max_tiles, void *dev_work
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_tm2d_group, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)tm2d::stage_bytes<float>());
+        e = cudaFuncSetAttribute(k_tm2d_group, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGroupStage);
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tm2d_group, tm2d::TX, tm2d::stage_bytes<float>());
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tm2d_group, kGroupThreads, kGroupStage);
     G->grid_blocks = sms * std::max(1, occ);
     if (e == cudaSuccess) e = cudaMemsetAsync(G->ws, 0, L.total, G->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(G->stream);

@@ -49,11 +49,15 @@ def axp_group_workspace_bytes(max_grids, max_tiles):
     return n.value
 
 
-VX = 251  # written columns per tile
+# written columns per tile of the group kernel: 250 for a member of even width
+# (two columns per thread), 123 for one of odd width; the library's own count
+# decides admission (axp_group_add refuses a member beyond max_tiles)
+VX_EVEN, VX_ODD = 250, 123
 
 
 def tiles_of(nx, ny, chunk=64):
-    return -(-nx // VX) * -(-ny // chunk)
+    vx = VX_EVEN if nx % 2 == 0 else VX_ODD
+    return -(-nx // vx) * -(-ny // chunk)
 
 
 class Group:
