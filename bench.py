@@ -279,8 +279,8 @@ TRAFFIC = {
     # k_tm2d_x2 (FP32 split, two columns per thread), 2048 x 2048 capture: 345.0 MB per launch
     ("k_tm2d_x2 (one launch per step)", "fp32"): 345.0e6 * (4096 * 2048) / (2048 * 2048),
 }
-# k_ax3d (3D, no order-0 fields), 256^3 capture: 1076.3 MB per launch
-TRAFFIC_3D_PER_CELL = 1076.3e6 / 256 ** 3
+# k_ax3d_x2 (3D, no order-0 fields, two x cells per thread): no capture of it yet
+TRAFFIC_3D_PER_CELL = None
 
 
 def load_peaks():
@@ -350,8 +350,11 @@ def axion3d_measurement(steps, warmup, hbm_peak, hbm_src, world, n=512):
            "kernel_path": g.kernel_path(), "gpu_launches": launches,
            "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
                         "peak_source": hbm_src, "algorithmic_bytes_per_cell": BYTES_3D_FP32,
-                        "traffic": TRAFFIC_3D_PER_CELL * cells if g.kernel_path() == axp.AXP_KERNEL_AX3D else None},
-           "kernel": {axp.AXP_KERNEL_AX3D: "k_ax3d", axp.AXP_KERNEL_FUSED: "k_fused"}.get(g.kernel_path(), "general")}
+                        "traffic": (TRAFFIC_3D_PER_CELL * cells if TRAFFIC_3D_PER_CELL is not None
+                                    and g.kernel_path() == axp.AXP_KERNEL_AX3D else None)},
+           # FP32 split on an even-width box takes the two-cell form of the axion-box kernel
+           "kernel": {axp.AXP_KERNEL_AX3D: "k_ax3d_x2" if n % 2 == 0 else "k_ax3d",
+                      axp.AXP_KERNEL_FUSED: "k_fused"}.get(g.kernel_path(), "general")}
     g.close()
     torch.cuda.synchronize()
     return out

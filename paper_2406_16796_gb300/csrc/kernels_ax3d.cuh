@@ -215,6 +215,200 @@ __global__ void __launch_bounds__(Geo<T>::NT, 1) k_ax3d(fused::Params<T> P)
     tm2d::cp_wait<0>();
 }
 
+// FP32 split with two adjacent x cells per thread: a block of 16 x 32 threads
+// owns a 32 x 32-cell tile (halo of 2 columns on each side along x, one row
+// below and two above along y), each thread the pair (2 tx, 2 tx + 1) of its
+// row.  The pair's history moves as float2: 8-byte staging copies, stores and
+// publishes, and the packed FP32 pipe for the arithmetic (one instruction for
+// two cells).  A warp holds two tile rows of 16 pairs; x neighbours of a pair
+// come from its own other cell and, across pairs, by 16-lane shuffles.  The
+// pair starts at an even x (written columns per tile: 28), so with an even nx
+// every pair lies inside the grid and is 8-byte aligned.
+namespace x2 {
+constexpr int TXP = 16;             // pairs per tile row (threads along x)
+constexpr int TY = 32;              // tile rows (threads along y)
+constexpr int NT = TXP * TY;        // 512 threads
+constexpr int HLX = 2, HRX = 2;     // halo columns along x (even: pairs stay aligned)
+constexpr int VXC = 2 * TXP - HLX - HRX;  // written columns per tile: 28
+constexpr int VYR = TY - HL - HR;   // written rows per tile: 29
+constexpr int PXP = TXP + 2;        // published row, in pairs, with a guard pair each side
+constexpr int PYR = TY + 2;
+constexpr int PLANE = PXP * PYR;
+constexpr size_t smem_bytes() { return ((size_t)2 * NPUB * PLANE + (size_t)NS * NIN * NT) * sizeof(float2); }
+
+__device__ __forceinline__ float2 f2(float s) { return make_float2(s, s); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+
+__device__ __forceinline__ void cp_pair(float2 *dst, const float *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+}  // namespace x2
+
+template <typename T>
+__global__ void __launch_bounds__(x2::NT, 1) k_ax3d_x2(fused::Params<T> P)
+{
+    static_assert(sizeof(T) == 4, "the pair form is the FP32-split kernel");
+    using namespace x2;
+    constexpr int PL = x2::PLANE;
+    extern __shared__ __align__(16) unsigned char ax3d_x2_dyn[];
+    float2 *pub = reinterpret_cast<float2 *>(ax3d_x2_dyn);  // [2][NPUB][PYR][PXP]
+    float2 *stage = pub + 2 * NPUB * PL;                     // [NS][NIN][NT]
+    const int tid = threadIdx.x, tx = tid % TXP, ty = tid / TXP;
+    for (int i = tid; i < 2 * NPUB * PL; i += NT) pub[i] = make_float2(0.f, 0.f);
+
+    const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
+    const int gx = (int)blockIdx.x * VXC - HLX + 2 * tx, gy = (int)blockIdx.y * VYR - HL + ty;
+    const int wx = ((gx % nx) + nx) % nx, wy = ((gy % ny) + ny) % ny;
+    const bool write_col = tx >= HLX / 2 && tx < TXP - HRX / 2 && ty >= HL && ty < TY - HR && gx < nx && gy < ny;
+    const int64_t col = (int64_t)wx + (int64_t)nx * wy, plane_stride = (int64_t)nx * ny;
+    const int m0 = (int)blockIdx.z * P.chunk, m1 = min(nz, m0 + P.chunk);
+    const int t0 = m0 - 1, t1 = m1 + 1;
+
+    const float inv_dt = P.inv_dt;
+    const float h = P.h, g = P.g, idx = P.idx[0], idy = P.idx[1], idz = P.idx[2];
+    const float2 cx = f2(P.lap_c[0]), cy = f2(P.lap_c[1]), cz = f2(P.lap_c[2]), c0 = f2(P.lap_0);
+    const float2 h2x = f2(2.f * h * idx), h2y = f2(2.f * h * idy), h2z = f2(2.f * h * idz);
+    const float2 mh2x = f2(-2.f * h * idx), mh2y = f2(-2.f * h * idy), mh2z = f2(-2.f * h * idz);
+    const float2 mhgx = f2(-h * g * P.Bext[0]), mhgy = f2(-h * g * P.Bext[1]), mhgz = f2(-h * g * P.Bext[2]);
+    const float2 idt = f2(inv_dt);
+
+    const float2 z = make_float2(0.f, 0.f);
+    float2 Ex0 = z, Ex1 = z, Ex2 = z, Ey0 = z, Ey1 = z, Ey2 = z, Ez0 = z, Ez1 = z, Ez2 = z;
+    float2 Bx0 = z, Bx1 = z, By0 = z, By1 = z, Bz0 = z, Bz1 = z;
+    float2 Nx1 = z, Nx2 = z, Nx3 = z, Ny1 = z, Ny2 = z, Ny3 = z, Nz1 = z, Nz2 = z;
+    float2 ph0 = z, ph1 = z, ph2 = z, pb0 = z, pb1 = z;
+    float2 D1 = z, D2 = z;
+
+    auto gidx = [&](int p) -> int64_t {
+        const int wp = p < 0 ? p + nz : (p >= nz ? p - nz : p);
+        return col + plane_stride * (int64_t)wp;
+    };
+    auto prefetch = [&](int p) {
+        const int64_t o = gidx(p);
+        float2 *st = stage + ((p - t0) & (NS - 1)) * (NIN * NT) + tid;
+        cp_pair(st + 0 * NT, P.Ein[3] + o);
+        cp_pair(st + 1 * NT, P.Ein[4] + o);
+        cp_pair(st + 2 * NT, P.Ein[5] + o);
+        cp_pair(st + 3 * NT, P.Bin[3] + o);
+        cp_pair(st + 4 * NT, P.Bin[4] + o);
+        cp_pair(st + 5 * NT, P.Bin[5] + o);
+        cp_pair(st + 6 * NT, P.phi + o);
+        cp_pair(st + 7 * NT, P.phib + o);
+    };
+    auto take = [&](int p) {
+        const float2 *st = stage + ((p - t0) & (NS - 1)) * (NIN * NT) + tid;
+        Ex0 = st[0 * NT];
+        Ey0 = st[1 * NT];
+        Ez0 = st[2 * NT];
+        Bx0 = st[3 * NT];
+        By0 = st[4 * NT];
+        Bz0 = st[5 * NT];
+        ph0 = st[6 * NT];
+        pb0 = st[7 * NT];
+    };
+    auto store = [](float *base, int64_t gi, float2 v) { *reinterpret_cast<float2 *>(base + gi) = v; };
+    const int me = (ty + 1) * PXP + (tx + 1);
+    const unsigned all = 0xffffffffu;
+    // the pair one cell along +x / -x: (own.y, next pair's x) and (previous pair's y, own.x)
+    auto xp = [&](float2 v) { return make_float2(v.y, __shfl_down_sync(all, v.x, 1, TXP)); };
+    auto xm = [&](float2 v) { return make_float2(__shfl_up_sync(all, v.y, 1, TXP), v.x); };
+
+    for (int j = 0; j < NS - 1; j++) {
+        if (t0 + j <= t1) prefetch(t0 + j);
+        tm2d::cp_commit();
+    }
+    tm2d::cp_wait<NS - 2>();
+    take(t0);
+    __syncthreads();
+    for (int t = t0; t <= t1; ++t) {
+        if (t + NS - 1 <= t1) prefetch(t + NS - 1);
+        tm2d::cp_commit();
+        float2 *Q = pub + (t & 1) * (NPUB * PL);
+        Q[P_EX * PL + me] = Ex1;
+        Q[P_EZ * PL + me] = Ez1;
+        Q[P_PHI * PL + me] = ph1;
+        Q[P_NX * PL + me] = Nx2;
+        Q[P_NZ * PL + me] = Nz2;
+        Q[P_DT * PL + me] = D2;
+        const float2 Ez_xp = xp(Ez1), Ey_xp = xp(Ey1), ph_xp = xp(ph1), ph_xm = xm(ph1), D_xp = xp(D2);
+        const float2 Nz_xm = xm(Nz2), Ny_xm = xm(Ny2);
+        __syncthreads();
+        const float2 *qEx = Q + P_EX * PL + me, *qEz = Q + P_EZ * PL + me;
+        const float2 *qph = Q + P_PHI * PL + me, *qNx = Q + P_NX * PL + me;
+        const float2 *qNz = Q + P_NZ * PL + me, *qDt = Q + P_DT * PL + me;
+        // ---- stage 1: B^{n+1} on plane t-1 ----
+        {
+            const int p = t - 1;
+            Nx1 = fma2(mh2y, sub2(qEz[PXP], Ez1), fma2(h2z, sub2(Ey0, Ey1), Bx1));
+            Ny1 = fma2(mh2z, sub2(Ex0, Ex1), fma2(h2x, sub2(Ez_xp, Ez1), By1));
+            Nz1 = fma2(mh2x, sub2(Ey_xp, Ey1), fma2(h2y, sub2(qEx[PXP], Ex1), Bz1));
+            if (write_col && p >= m0 && p < m1) {
+                const int64_t gi = col + plane_stride * (int64_t)p;
+                store(P.Bout[3], gi, Nx1);
+                store(P.Bout[4], gi, Ny1);
+                store(P.Bout[5], gi, Nz1);
+            }
+        }
+        // ---- stage 2: phi^{n+3/2} and D_t phi^{n+1} on plane t-1 ----
+        {
+            const int p = t - 1;
+            const float2 spx = add2(sub2(ph_xp, ph1), sub2(ph_xm, ph1));
+            const float2 spy = add2(sub2(qph[PXP], ph1), sub2(qph[-PXP], ph1));
+            const float2 spz = add2(sub2(ph0, ph1), sub2(ph2, ph1));
+            float2 acc = fma2(c0, ph1, pb1);
+            acc = fma2(cx, spx, acc);
+            acc = fma2(cy, spy, acc);
+            acc = fma2(cz, spz, acc);
+            const float2 pin = acc, nw = add2(ph1, pin);
+            D1 = mul2(pin, idt);
+            if (write_col && p >= m0 && p < m1) {
+                const int64_t gi = col + plane_stride * (int64_t)p;
+                store(P.phi_out, gi, nw);
+                store(P.phib_out, gi, pin);
+            }
+        }
+        // ---- stage 3: J^{n+1} and E^{n+3/2} on plane t-2 ----
+        {
+            const int p = t - 2;
+            if (write_col && p >= m0 && p < m1) {
+                const int64_t gi = col + plane_stride * (int64_t)p;
+                store(P.Eout[3], gi, fma2(h2y, sub2(Nz2, qNz[-PXP]), fma2(mh2z, sub2(Ny2, Ny3), fma2(mhgx, add2(D2, D_xp), Ex2))));
+                store(P.Eout[4], gi, fma2(h2z, sub2(Nx2, Nx3), fma2(mh2x, sub2(Nz2, Nz_xm), fma2(mhgy, add2(D2, qDt[PXP]), Ey2))));
+                store(P.Eout[5], gi, fma2(h2x, sub2(Ny2, Ny_xm), fma2(mh2y, sub2(Nx2, qNx[-PXP]), fma2(mhgz, add2(D2, D1), Ez2))));
+            }
+        }
+        Ex2 = Ex1; Ex1 = Ex0; Ey2 = Ey1; Ey1 = Ey0; Ez2 = Ez1; Ez1 = Ez0;
+        Bx1 = Bx0; By1 = By0; Bz1 = Bz0;
+        Nx3 = Nx2; Nx2 = Nx1; Ny3 = Ny2; Ny2 = Ny1; Nz2 = Nz1;
+        ph2 = ph1; ph1 = ph0; pb1 = pb0;
+        D2 = D1;
+        tm2d::cp_wait<NS - 2>();
+        if (t < t1) take(t + 1);
+    }
+    tm2d::cp_wait<0>();
+}
+
+inline cudaError_t launch_x2(const fused::Params<float> &P, int nchunks, cudaStream_t stream, int *occupancy)
+{
+    static int occ = 0;
+    const size_t dyn = x2::smem_bytes();
+    if (occ == 0) {
+        cudaError_t e = cudaFuncSetAttribute(k_ax3d_x2<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_ax3d_x2<float>, x2::NT, dyn);
+        if (e != cudaSuccess) return e;
+    }
+    if (occupancy) *occupancy = occ;
+    if (nchunks <= 0) return cudaSuccess;
+    dim3 grid((P.n[0] + x2::VXC - 1) / x2::VXC, (P.n[1] + x2::VYR - 1) / x2::VYR, nchunks);
+    k_ax3d_x2<float><<<grid, x2::NT, dyn, stream>>>(P);
+    return cudaGetLastError();
+}
+
 template <typename T, bool INCR>
 cudaError_t launch(const fused::Params<T> &P, int nchunks, cudaStream_t stream, int *occupancy)
 {

@@ -450,8 +450,9 @@ cudaError_t fused_step(axp_grid *g, int64_t nsteps, bool *handled)
         // z chunks: fewest waves of resident blocks for the (tile + pipeline) work
         int sms = 152;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
-        const int64_t vy = ax3d::Geo<T>::VY;
-        const int64_t tiles = ((g->desc.n[0] + ax3d::VX - 1) / ax3d::VX) * ((g->desc.n[1] + vy - 1) / vy);
+        const bool pairs = sizeof(T) == 4 && g->desc.n[0] % 2 == 0;  // the two-cell form's tiles
+        const int64_t vx = pairs ? ax3d::x2::VXC : ax3d::VX, vy = pairs ? ax3d::x2::VYR : ax3d::Geo<T>::VY;
+        const int64_t tiles = ((g->desc.n[0] + vx - 1) / vx) * ((g->desc.n[1] + vy - 1) / vy);
         const int64_t nz = g->desc.n[2], slots = (int64_t)sms * (occ > 0 ? occ : 1);
         double best = 0;
         for (int64_t nc = 1; nc <= 32 && nc <= nz; nc++) {
