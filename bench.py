@@ -279,8 +279,8 @@ TRAFFIC = {
     # k_tm2d_x2 (FP32 split, two columns per thread), 2048 x 2048 capture: 345.0 MB per launch
     ("k_tm2d_x2 (one launch per step)", "fp32"): 345.0e6 * (4096 * 2048) / (2048 * 2048),
 }
-# k_ax3d_x2 (3D, no order-0 fields, two x cells per thread): no capture of it yet
-TRAFFIC_3D_PER_CELL = None
+# k_ax3d_x2 (3D, no order-0 fields, two x cells per thread), 256^3 capture: 1064.9 MB per launch
+TRAFFIC_3D_PER_CELL = 1064.9e6 / 256 ** 3
 
 
 def load_peaks():
