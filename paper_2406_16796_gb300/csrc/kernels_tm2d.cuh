@@ -84,7 +84,11 @@ enum { R_E0Z, R_E1Y, R_E1Z, R_PHI, R_N0Y2, R_MID3, R_N0Y3, R_PX4, R_N1Z4, R_N1Y4
 // of the grid P describes.  `rows` is the block's shared staging; the caller
 // separates consecutive tiles of one block with a barrier.  SRC compiles in the
 // soft source's sheets (P.src_x >= 0); without it the body has no trace of them.
-template <typename T, bool INCR, bool SRC = false>
+// FOLDP: square cells (dx = dy) and no uniform background B along x or y, the
+// 2D pulse's case.  The axion current is then carried as P / (1/(2 dt)): the
+// factor meets the gradient's 1/(4 dx) in one constant and the current's
+// coefficient in the E updates, three operations fewer per cell.
+template <typename T, bool INCR, bool SRC = false, bool FOLDP = false>
 __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, const int by, T (&rows)[2][NROWS][RS],
                                      T *stage)
 {
@@ -130,6 +134,10 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
     const T qidx = T(0.5) * hidx, qidy = T(0.5) * hidy, hinv_dt = T(0.5) * inv_dt;
     const T Bxi = Bx * inv_dt, Byi = By * inv_dt, dt2gBz = dt2g * Bz, gBzi = g * Bz * inv_dt;
     const T h2gBzi = h2g * Bz * inv_dt;
+    // FOLDP: P_x, P_y carried divided by 1/(2 dt); the gradient's factor and the
+    // current's coefficients absorb it
+    const T qq = qidx / hinv_dt;
+    const T hgP = FOLDP ? hg * hinv_dt : hg, gP = FOLDP ? g * hinv_dt : g;
     // soft source: this column holds the sheet's E cells (electric sheet) or the
     // B faces on the plane (magnetic sheet)
     const bool src_e_col = SRC && wx == P.src_x;
@@ -372,12 +380,19 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
         // ---- stage 3: P^{n+1} on plane t-3 ----
         {
             const int p = t - 3;
+            if constexpr (FOLDP) {
+                // P / (1/(2 dt)) = DF (N + N') + (E0z q) dphi, q = (1/(4 dx)) / (1/(2 dt))
+                const T ENq = EN3 * qq;
+                PX3 = fma(ENq, SM2 - SM4, DF3 * (N0x3 + N0x4));
+                PY3 = fma(-ENq, R[R_MID3][tx + 2] - R[R_MID3][tx], DF3 * (N0y3 + R[R_N0Y3][tx]));
+            } else {
             const T bbx = fma(hinv_dt, N0x3 + N0x4, Bxi);  // Bbar_x / dt
             const T bby = fma(hinv_dt, N0y3 + R[R_N0Y3][tx], Byi);
             const T dpy = (SM2 - SM4) * qidy;
             const T dpx = (R[R_MID3][tx + 2] - R[R_MID3][tx]) * qidx;
             PX3 = fma(EN3, dpy, DF3 * bbx);   // Dt Bbar_x - (Ebar_y dphi_z - Ebar_z dphi_y)
             PY3 = fma(-EN3, dpx, DF3 * bby);  // Dt Bbar_y - (Ebar_z dphi_x - Ebar_x dphi_z)
+            }
             // P_z = Dt B_ext,z (no laser B0z, no Ebar_x, Ebar_y): DF B_ext,z/dt, folded into E1z
             if (EDGE && !inside(p)) PX3 = PY3 = T(0);
         }
@@ -396,8 +411,8 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
                 // E0z's two half-steps read the same curl of B0^{n+1}: E0z^{n+3/2} =
                 // 2 E0z^{n+1} - E0z^{n+1/2} (an electric sheet's term is in it twice, too)
                 auto plain = [&]() {
-                    ex = fma(h2y, e1zy, fma(-hg, sjx, E1x4));
-                    ey = fma(-h2x, e1zx, fma(-hg, sjy, E1y4));
+                    ex = fma(h2y, e1zy, fma(-hgP, sjx, E1x4));
+                    ey = fma(-h2x, e1zx, fma(-hgP, sjy, E1y4));
                     ez = fma(h2x, e1yx, fma(-h2y, e1xy, fma(-h2gBzi, DF4, E1z4)));
                     e0 = fma(T(2), EN4, -E0z4);
                 };
@@ -409,8 +424,8 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
                     if (a2 == T(1)) {
                         plain();
                     } else {
-                        const T xx = fma(-g, T(0.5) * sjx, e1zy * idy);
-                        const T xy = fma(-g, T(0.5) * sjy, -e1zx * idx);
+                        const T xx = fma(-gP, T(0.5) * sjx, e1zy * idy);
+                        const T xy = fma(-gP, T(0.5) * sjy, -e1zx * idx);
                         const T xz = fma(-gBzi, DF4, e1yx * idx - e1xy * idy);
                         const T e0yx = N0y4 - R[R_N0Y4][tx], e0xy = N0x4 - N0x5;
                         ex = fma(b2, xx, a2 * E1x4);
@@ -485,20 +500,20 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
     cp_wait<0>();
 }
 
-template <typename T, bool INCR, bool SRC>
+template <typename T, bool INCR, bool SRC, bool FOLDP = false>
 __global__ void __launch_bounds__(TX, sizeof(T) == 4 ? 2 : 1) k_tm2d(fused::Params<T> P)
 {
     __shared__ T rows[2][NROWS][RS];
     extern __shared__ __align__(16) unsigned char tm2d_dyn[];
-    tile<T, INCR, SRC>(P, (int)blockIdx.x, (int)blockIdx.y, rows, reinterpret_cast<T *>(tm2d_dyn));
+    tile<T, INCR, SRC, FOLDP>(P, (int)blockIdx.x, (int)blockIdx.y, rows, reinterpret_cast<T *>(tm2d_dyn));
 }
 
-template <typename T, bool INCR, bool SRC>
+template <typename T, bool INCR, bool SRC, bool FOLDP = false>
 cudaError_t launch_variant(const fused::Params<T> &P, int nchunks, cudaStream_t stream, int *occupancy, int tx)
 {
     // resident blocks per SM for each tile width (multiples of 32 up to TX)
     static int occ[TX / 32 + 1] = {};
-    auto kern = k_tm2d<T, INCR, SRC>;
+    auto kern = k_tm2d<T, INCR, SRC, FOLDP>;
     // the staging ring is sized for the launch's tile width
     const size_t dyn = stage_bytes<T>(tx);
     if (tx < 64 || tx > TX || tx % 32) return cudaErrorInvalidValue;
@@ -519,6 +534,11 @@ template <typename T, bool INCR>
 cudaError_t launch(const fused::Params<T> &P, int nchunks, cudaStream_t stream, int *occupancy, int tx = TX)
 {
     if (P.src_x >= 0) return launch_variant<T, INCR, true>(P, nchunks, stream, occupancy, tx);
+#ifndef AXP_TM2D_NO_FOLDP
+    // FP64 with square cells and no uniform B along x or y: the folded current
+    if (sizeof(T) == 8 && P.Bext[0] == T(0) && P.Bext[1] == T(0) && P.idx[0] == P.idx[1])
+        return launch_variant<T, INCR, false, true>(P, nchunks, stream, occupancy, tx);
+#endif
     return launch_variant<T, INCR, false>(P, nchunks, stream, occupancy, tx);
 }
 

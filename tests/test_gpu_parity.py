@@ -306,6 +306,10 @@ TM2D_CASES = {
                 em_bc=W._bcs("pml", "pml"), pml_cells=8),
     "periodic_x_pml_y": dict(n=(560, 100, 1), B_ext=(0.0, 0.0, 1.0), axion_bc=W._bcs("periodic", "pml"),
                              em_bc=W._bcs("periodic", "pml"), pml_cells=6),
+    # square cells and B_ext along z only: the FP64 kernel's folded form of the current
+    "pml_square_cells": dict(n=(520, 130, 1), d=(0.05, 0.05, 0.05), B_ext=(0.0, 0.0, 1.3),
+                             axion_bc=W._bcs("pml", "pml"), em_bc=W._bcs("pml", "pml"), pml_cells=8),
+    "periodic_square_cells": dict(n=(600, 90, 1), d=(0.04, 0.04, 0.04), B_ext=(0.0, 0.0, -0.8)),
 }
 
 
