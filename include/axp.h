@@ -353,7 +353,16 @@ axp_status axp_get_window_offset(const axp_grid *grid, int64_t *cells);
  * time scheme, in the oracle's operation order); AXP_KERNEL_FUSED forces the
  * generic single-pass kernel (1D/2D/3D, periodic, reflect and PML edges);
  * AXP_KERNEL_TM2D forces the single-pass kernel specialised for 2D grids with
- * an (E0z; B0x, B0y) laser and periodic or PML edges (at most 2^32 cells);
+ * an (E0z; B0x, B0y) laser and periodic or PML edges (at most 2^32 cells), on
+ * its uniform launch grid of x strips by march chunks;
+ * AXP_KERNEL_TM2D_LIST forces the same kernel on per-block work lists (FP64
+ * grids without a soft source): the host cuts each x strip into tiles of about
+ * equal cost and lets two short tiles share a block, so that every block, all
+ * resident at once, finishes at about the same time (the work list sits in the
+ * workspace and is copied there, host to device on the grid's stream, by the
+ * first axp_step after a change of kernel, soft source or background field;
+ * a grid too wide for the list's 2048 items makes axp_step return AXP_E_CUDA);
+ * AUTO takes whichever of the two forms the planner's cost model prefers;
  * AXP_KERNEL_AX3D forces the single-pass kernel specialised for periodic 3D
  * grids with no laser fields and no uniform E (an axion wave in a uniform B);
  * AXP_KERNEL_BLOCK1D forces the time-blocked kernel for FP64 1D grids that
@@ -370,7 +379,8 @@ typedef enum {
     AXP_KERNEL_FUSED = 2,
     AXP_KERNEL_TM2D = 3,
     AXP_KERNEL_AX3D = 4,
-    AXP_KERNEL_BLOCK1D = 5
+    AXP_KERNEL_BLOCK1D = 5,
+    AXP_KERNEL_TM2D_LIST = 6
 } axp_kernel;
 axp_status axp_set_kernel(axp_grid *grid, int32_t kernel);
 /* Which path the next axp_step will take (an axp_kernel value other than AUTO). */

@@ -19,6 +19,7 @@ from .workloads import BC_CODE, AxionSpec, GridSpec, LaserSpec, SourceSpec
 AXP_OK, AXP_E_INVAL, AXP_E_UNSTABLE, AXP_E_NOMEM, AXP_E_CUDA, AXP_E_TIMEOUT, AXP_E_NONFINITE, AXP_E_STATE = range(8)
 AXP_FP64, AXP_FP32_SPLIT = 0, 1
 AXP_KERNEL_AUTO, AXP_KERNEL_GENERAL, AXP_KERNEL_FUSED, AXP_KERNEL_TM2D, AXP_KERNEL_AX3D, AXP_KERNEL_BLOCK1D = 0, 1, 2, 3, 4, 5
+AXP_KERNEL_TM2D_LIST = 6
 FIELD_IDS = {n: i for i, n in enumerate(("E0x", "E0y", "E0z", "B0x", "B0y", "B0z",
                                           "E1x", "E1y", "E1z", "B1x", "B1y", "B1z"))}
 FIELD_IDS["phi_cur"] = 12

@@ -237,6 +237,10 @@ bool compute_layout(const axp_grid_desc &d, Workspace *w)
         w->off_src[c] = off;
         off += align_up((size_t)plane_size(d, 0) * e);
     }
+    if (d.n[1] > 1 && d.n[2] == 1) {  // work lists of the 2D kernel
+        w->off_sched = off;
+        off += align_up((size_t)kSchedItems * 16);
+    }
     int64_t nb = (cells(d) + 255) / 256;
     if (nb > 1024) nb = 1024;
     if (nb < 1) nb = 1;
@@ -472,6 +476,7 @@ axp_status axp_create_grid(const axp_grid_desc *desc, void *dev_workspace, size_
     g->kernel_choice = AXP_KERNEL_AUTO;
     g->win_axis = -1;
     g->coop_absent = -1;
+    g->tm_plan_key = -1;
     cudaError_t e = cudaMemsetAsync(g->ws, 0, w.total, g->stream);
     if (e == cudaSuccess) {
         // absorbing-layer profiles and coefficients, computed once on the host
@@ -1020,7 +1025,7 @@ axp_status axp_get_step(const axp_grid *g, int64_t *step)
 
 axp_status axp_set_kernel(axp_grid *g, int32_t kernel)
 {
-    if (!g || kernel < AXP_KERNEL_AUTO || kernel > AXP_KERNEL_BLOCK1D) return AXP_E_INVAL;
+    if (!g || kernel < AXP_KERNEL_AUTO || kernel > AXP_KERNEL_TM2D_LIST) return AXP_E_INVAL;
     if (g->group) return AXP_E_STATE;
     g->cfg_version++;
     g->kernel_choice = kernel;

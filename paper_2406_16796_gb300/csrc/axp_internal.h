@@ -9,6 +9,7 @@
 #include <stdint.h>
 
 #include <cmath>
+#include <vector>
 
 #include <nvtx3/nvToolsExt.h>
 
@@ -80,6 +81,8 @@ inline void set_reciprocals(View<T> &v)
     }
 }
 
+constexpr int kSchedItems = 2048;
+
 struct Workspace {
     size_t off_fields[2][kFields];  // two field sets: the fused step reads one and writes the other
     size_t off_phi[4];              // axion buffers; roles are tracked by the handle
@@ -94,6 +97,7 @@ struct Workspace {
     size_t off_pml_tab[3];
     // soft source: per (j, k) of the x-plane, A pol_a f / dx for a = y, z (zero in layers)
     size_t off_src[2];
+    size_t off_sched;  // 2D grids: kSchedItems work-list items (int4) of the 2D kernel
     size_t off_partials;
     size_t off_ring;
     size_t off_flag;
@@ -149,6 +153,14 @@ struct axp_grid {
     // is checked by the next synchronising call
     bool coop_used;
     int32_t coop_absent;  // failure-detection test: block that skips the next launch's barriers (-1: none)
+    // launch plan of the 2D single-pass kernel, made for configuration tm_plan_key
+    // (-1: none): tile width, and either the uniform grid (chunk sizes, chunk rows)
+    // or tm_list_blocks blocks of tm_list_per_block work-list items in off_sched
+    int64_t tm_plan_key;
+    int32_t tm_tx, tm_chunk, tm_chunk_first, tm_chunk_edge, tm_nchunks;
+    int32_t tm_list_blocks, tm_list_per_block;
+    std::vector<int4> tm_items;  // the work lists (host copy)
+    bool tm_items_uploaded;      // tm_items are in off_sched
 };
 
 namespace axp {
@@ -184,7 +196,7 @@ template <typename T>
 bool fused_supported(const axp_grid *g);
 // the path axp_step will take under the handle's kernel choice (an axp_kernel value)
 template <typename T>
-int32_t fused_path(const axp_grid *g);
+int32_t fused_path(axp_grid *g);
 // staggered <-> integer-time conversion of E (E^{n+1/2} = E^n + h (curl B^n - g J^n))
 template <typename T>
 cudaError_t enter_staggered(axp_grid *g);

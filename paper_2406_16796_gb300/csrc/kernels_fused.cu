@@ -20,6 +20,8 @@ cudaError_t fused_dispatch_f32(int mode, int set, const fused::Params<float> &P,
 cudaError_t tm2d_dispatch_f64(const fused::Params<double> &P, int nchunks, cudaStream_t s, int *occ, int tx);
 cudaError_t tm2d_dispatch_f32(const fused::Params<float> &P, int nchunks, cudaStream_t s, int *occ, int tx);
 cudaError_t tm2d_x2_dispatch_f32(const fused::Params<float> &P, int nchunks, cudaStream_t s, int *occ, int cols);
+cudaError_t tm2d_list_dispatch_f64(const fused::Params<double> &P, const int4 *items, int nblocks, int per_block,
+                                   cudaStream_t s, int *occ, int tx);
 cudaError_t ax3d_dispatch_f64(const fused::Params<double> &P, int nchunks, cudaStream_t s, int *occ);
 cudaError_t ax3d_dispatch_f32(const fused::Params<float> &P, int nchunks, cudaStream_t s, int *occ);
 
@@ -340,8 +342,405 @@ cudaError_t block1d_step(axp_grid *g, int64_t nsteps)
     return cudaGetLastError();
 }
 
+// Cost, in plane-times of one tile, of a tile over planes [m0, m1) of a strip
+// whose plain iteration costs r: the march runs m1 - m0 + 6 iterations (the
+// pipeline's planes), and each iteration that runs the edge body over a y layer
+// (or next to a non-periodic y side: t < ylo + 6 or t >= yhi) adds `layer`.
+struct SpanCost {
+    bool pery;
+    int64_t ylo, yhi;
+    double layer;
+    double operator()(double r, int64_t m0, int64_t m1) const
+    {
+        const int64_t t0 = m0 - 2, t1 = m1 + 3;
+        double c = r * (double)(t1 - t0 + 1);
+        if (!pery) {
+            auto len = [](int64_t a, int64_t b) { return b >= a ? b - a + 1 : (int64_t)0; };
+            const int64_t lo_end = std::min(t1, ylo + 5), hi_beg = std::max(t0, yhi);
+            c += layer * (double)(len(t0, lo_end) + len(hi_beg, t1) - len(hi_beg, lo_end));
+        }
+        return c;
+    }
+};
+
+// A block's work list: at most kListTiles tiles (x: strip, y and z: planes
+// [y, z); an empty tile has z <= y), and the sum of their costs.
+constexpr int kListTiles = 3;
+struct ListBlock {
+    int4 t[kListTiles];
+    int n;
+    double cost;
+};
+
+// Cuts the strips `ids` (a plain iteration of each costs r) into blocks whose
+// costs are at most T, for the smallest T found by bisection: every strip is cut
+// from y = 0 into the longest tiles of cost <= T, and the strips' last tiles (the
+// remainders) share blocks, up to kListTiles to a block, first fit in order of
+// decreasing cost, where their costs add up to <= T.  T is
+// feasible when that takes at most `limit` blocks and cuts no tile shorter than
+// kMinTile planes (where the strip has them: shorter ones would spend more on the
+// march's set-up than the balance gains).  Returns T, or -1 when no T is
+// feasible.
+double list_cut(const std::vector<int> &ids, double r, int64_t ny, const SpanCost &C, int64_t limit,
+                std::vector<ListBlock> *blocks)
+{
+    constexpr int64_t kMinTile = 8;
+    auto cut = [&](double T, std::vector<ListBlock> *outp) -> bool {
+        std::vector<ListBlock> rem, out;
+        for (const int s : ids) {
+            int64_t m0 = 0;
+            while (m0 < ny) {
+                if (C(r, m0, m0 + 1) > T) return false;
+                int64_t lo = m0 + 1, hi = ny;  // the largest m1 with cost <= T
+                while (lo < hi) {
+                    const int64_t mid = (lo + hi + 1) / 2;
+                    if (C(r, m0, mid) <= T) lo = mid;
+                    else hi = mid - 1;
+                }
+                ListBlock b{};
+                b.t[0] = make_int4(s, (int)m0, (int)lo, 0);
+                b.n = 1;
+                b.cost = C(r, m0, lo);
+                (lo == ny ? rem : out).push_back(b);
+                if ((int64_t)out.size() > limit) return false;
+                m0 = lo;
+            }
+        }
+        std::stable_sort(rem.begin(), rem.end(), [](const ListBlock &a, const ListBlock &b) { return a.cost > b.cost; });
+        const size_t first_bin = out.size();
+        for (const ListBlock &x : rem) {
+            size_t k = first_bin;
+            while (k < out.size() && (out[k].n == kListTiles || out[k].cost + x.cost > T)) k++;
+            if (k == out.size()) {
+                out.push_back(x);
+            } else {
+                out[k].t[out[k].n++] = x.t[0];
+                out[k].cost += x.cost;
+            }
+        }
+        if ((int64_t)out.size() > limit) return false;
+        if (outp) *outp = std::move(out);
+        return true;
+    };
+    if (ids.empty()) {
+        blocks->clear();
+        return 0.0;
+    }
+    double hi = C(r, 0, ny), lo = C(r, 0, std::min(ny, kMinTile));
+    if (!cut(hi, nullptr)) return -1.0;
+    if (cut(lo, nullptr)) hi = lo;
+    for (int it = 0; it < 48 && hi - lo > 0.25; it++) {
+        const double mid = 0.5 * (lo + hi);
+        if (cut(mid, nullptr)) hi = mid;
+        else lo = mid;
+    }
+    cut(hi, blocks);
+    return hi;
+}
+
+// Work lists of the 2D kernel for a launch of `per_sm` blocks per SM, laid out
+// for the order in which the block scheduler fills a GPU: with sms * per_sm
+// blocks, blocks j and j + sms share an SM (j < sms).  A strip at a non-periodic
+// x edge runs the edge body over its layer, and its block waits at each plane's
+// barrier for the layer's warp: next to a block of another strip it takes
+// kEdgeNextToInner plane-times per plane, next to another such block
+// kEdgePair.  So with two blocks per SM the x-edge strips get SMs of their own
+// (both blocks), as many as balance their cost against the other strips'; the
+// number of such SMs is found by bisection (the other strips' cost grows with
+// it, theirs falls).  Returns the costliest SM's cost in plane-times and fills
+// `items` (kListTiles per block, every block of the launch listed), or -1 when no
+// list fits one wave (`forced`: then one wave is not required).
+double list_schedule(int64_t strips, bool xedge, int64_t ny, const SpanCost &C, int sms, int per_sm, bool forced,
+                     std::vector<int4> *items)
+{
+    constexpr double kEdgePair = 1.6, kEdgeNextToInner = 1.82;
+    const int64_t slots = (int64_t)sms * per_sm;
+    std::vector<int> inner, edge, all;
+    for (int s = 0; s < (int)strips; s++) {
+        (xedge && (s == 0 || s == strips - 1) ? edge : inner).push_back(s);
+        all.push_back(s);
+    }
+    std::vector<ListBlock> bi, be;
+    double T = -1.0;
+    int E = 0;  // SMs that take the x-edge strips
+    if (!edge.empty() && per_sm == 2 && sms >= 2) {
+        auto costs = [&](int e, std::vector<ListBlock> *oi, std::vector<ListBlock> *oe, double *ti, double *te) {
+            *ti = list_cut(inner, 1.0, ny, C, 2 * (int64_t)(sms - e), oi);
+            *te = list_cut(edge, kEdgePair, ny, C, 2 * (int64_t)e, oe);
+        };
+        // the smallest e whose edge cost no longer exceeds the inner cost
+        int lo = 1, hi = sms - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi) / 2;
+            double ti, te;
+            std::vector<ListBlock> a, b;
+            costs(mid, &a, &b, &ti, &te);
+            if (te >= 0 && (ti < 0 || te <= ti)) hi = mid;
+            else lo = mid + 1;
+        }
+        for (int e = std::max(1, lo - 1); e <= std::min(sms - 1, lo); e++) {
+            double ti, te;
+            std::vector<ListBlock> a, b;
+            costs(e, &a, &b, &ti, &te);
+            if (ti < 0 || te < 0) continue;
+            if (T < 0 || std::max(ti, te) < T) {
+                T = std::max(ti, te);
+                E = e;
+                bi = std::move(a);
+                be = std::move(b);
+            }
+        }
+    } else if (edge.empty()) {
+        T = list_cut(inner, 1.0, ny, C, slots, &bi);
+    } else {  // one block per SM: an x-edge strip's block is next to nothing, or next to inner blocks
+        std::vector<ListBlock> a, b;
+        const double ti = list_cut(inner, 1.0, ny, C, slots, &a);
+        const double te = list_cut(edge, per_sm > 1 ? kEdgeNextToInner : kEdgePair, ny, C, slots, &b);
+        if (ti >= 0 && te >= 0 && (int64_t)(a.size() + b.size()) <= slots) {
+            T = std::max(ti, te);
+            bi = std::move(a);
+            be = std::move(b);
+            for (ListBlock &x : be) bi.push_back(x);
+            be.clear();
+        }
+    }
+    if (T < 0) {
+        if (!forced) return -1.0;
+        // a grid of more strips than one wave holds: every strip at the edge rate
+        T = list_cut(all, kEdgeNextToInner, ny, C, std::max(slots, strips), &bi);
+        be.clear();
+        E = 0;
+        if (T < 0) return -1.0;
+    }
+    // lay the blocks out: x-edge blocks at j and j + sms for j < E, the others in
+    // the remaining places, costliest first in the first wave and cheapest first in
+    // the second (so that an SM's two blocks roughly even out); empty blocks pad
+    // the launch to whole waves
+    auto by_cost = [](const ListBlock &a, const ListBlock &b) { return a.cost > b.cost; };
+    std::stable_sort(bi.begin(), bi.end(), by_cost);
+    const int64_t nb = std::max<int64_t>(slots, (int64_t)(bi.size() + be.size()));
+    const ListBlock none{};
+    std::vector<ListBlock> lay((size_t)nb, none);
+    std::vector<char> taken((size_t)nb, 0);
+    for (size_t k = 0; k < be.size(); k++) {
+        const int64_t pos = (int64_t)(k / 2) + (k % 2 ? sms : 0);
+        lay[(size_t)pos] = be[k];
+        taken[(size_t)pos] = 1;
+    }
+    for (int j = 0; j < E && per_sm == 2; j++) taken[(size_t)j] = taken[(size_t)(j + sms)] = 1;
+    std::vector<int64_t> first, second;
+    for (int64_t p = 0; p < nb; p++) {
+        if (taken[(size_t)p]) continue;
+        (p < sms ? first : second).push_back(p);
+    }
+    std::reverse(second.begin(), second.end());
+    size_t k = 0;
+    for (const int64_t p : first)
+        if (k < bi.size()) lay[(size_t)p] = bi[k++];
+    for (const int64_t p : second)
+        if (k < bi.size()) lay[(size_t)p] = bi[k++];
+    for (; k < bi.size(); k++) lay.push_back(bi[k]);  // (forced lists beyond one wave)
+    items->clear();
+    for (const ListBlock &b : lay)
+        for (int k = 0; k < kListTiles; k++) items->push_back(b.t[k]);
+    return T;
+}
+
+// The work-list form takes FP64 grids without a soft source.
 template <typename T>
-int32_t fused_path(const axp_grid *g)
+bool tm2d_list_eligible(const axp_grid *g)
+{
+    return sizeof(T) == 8 && !g->src_on && g->layout.off_sched != 0 && tm2d_supported(g);
+}
+
+// Launch plan of the 2D kernel, made once per configuration (kernel choice, soft
+// source, and whether the folded-current form applies) and kept in the handle.
+template <typename T>
+cudaError_t tm2d_plan(axp_grid *g)
+{
+    fused::Params<T> P = make_params<T>(g);
+    const bool foldp = P.Bext[0] == T(0) && P.Bext[1] == T(0) && P.idx[0] == P.idx[1];
+    const int64_t key = ((int64_t)g->kernel_choice * 2 + (g->src_on ? 1 : 0)) * 2 + (foldp ? 1 : 0);
+    if (g->tm_plan_key == key) return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+    const bool x2 = tm2d_x2_eligible<T>(g);
+    auto occ_of = [&](int width, int *o) -> cudaError_t {
+        if constexpr (sizeof(T) == 4) {
+            if (x2) return tm2d_x2_dispatch_f32(P, 0, g->stream, o, width);
+        }
+        return dispatch_tm2d<T>(P, 0, g->stream, o, width);
+    };
+    const bool want_list = g->kernel_choice == AXP_KERNEL_TM2D_LIST;
+    const bool list_ok = tm2d_list_eligible<T>(g) && (want_list || g->kernel_choice == AXP_KERNEL_AUTO);
+    double best_list = -1.0;
+    int list_tx = 0;
+    std::vector<int4> list_items;
+    int tm_tx = tm2d::TX;
+    // Tile width and march chunks: the fewest resident-block waves for the work
+    // a wave does, (planes + pipeline) x columns x blocks per SM, divided by the
+    // share of its issue rate an SM reaches with that many warps resident.  FP64:
+    // below 8 warps the FP64 pipe's and the loads' latencies are no longer
+    // hidden, sqrt(warps / 8); FP32: warps / 16, and kManyBlocks beyond two blocks
+    // per SM; kOneBlock for one block per SM (all from measured tile widths).
+    // Measured per-CTA times give the other two costs: a strip at a non-periodic x edge runs the edge body
+    // over the x layer and takes kEdgeCost times as long per plane (its warps
+    // wait at each plane's barrier for the layer's warp), and a chunk that
+    // crosses a y layer runs the edge body over the layer and the pipeline's
+    // planes next to it, kLayerCost plane-times each.  With one wave the x-edge
+    // strips may get more, shorter chunks from the blocks the other strips
+    // leave free, and the other strips' first and last chunks are shortened by
+    // the y layer's extra cost.
+    const double kEdgeCost = sizeof(T) == 8 ? 1.55 : 1.35;
+    // A lone block per SM has nothing else to issue while its warps wait at a
+    // plane's barrier: two blocks of half the width ran the 2D pulse 7% faster.
+    const double kOneBlock = 0.92;
+    const double kManyBlocks = 0.7;  // FP32 with more than two blocks per SM (the FP32 rule below)
+    const double kLayerCost = sizeof(T) == 8 ? 0.93 : 0.32;
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
+    const int64_t nx = g->desc.n[0], ny = g->desc.n[1];
+    const bool xedge = g->desc.em_bc[0][0] != AXP_BC_PERIODIC;
+    const bool ylay = g->desc.em_bc[1][0] != AXP_BC_PERIODIC && P.has_pml;
+    const int64_t D = ylay ? (int64_t)std::lround(kLayerCost * (P.lay[1][0] + 7)) : 0;
+    // the same costs tile by tile, for the work-list form
+    const SpanCost span{g->desc.em_bc[1][0] == AXP_BC_PERIODIC, (int64_t)P.lay[1][0], ny - 1 - (int64_t)P.lay[1][1],
+                        kLayerCost};
+    // `rows` chunks over y: returns the costliest chunk in plane-times, with the
+    // first and the middle chunk sizes (the last chunk is what remains, <= cf)
+    auto split = [&](int64_t rows, int64_t *cf, int64_t *cm) -> double {
+        const int64_t u0 = (ny + rows - 1) / rows;
+        *cf = *cm = u0;
+        if (D == 0 || rows < 3) return (double)(u0 + 6 + D);
+        const int64_t c = (ny + 2 * D + rows - 1) / rows, f = c - D;
+        const int64_t last = ny - f - (rows - 2) * c;
+        if (f < 16 || last < 1 || last > f) return (double)(u0 + 6 + D);
+        *cf = f;
+        *cm = c;
+        return (double)(c + 6);
+    };
+    double best = -1.0;
+    int best_ce = 0, best_rows = 0, best_cf = 0;
+    // tile widths in columns; the two-column form takes multiples of 64 (tx / 2 threads)
+    const int halo = x2 ? tm2d_x2::HL + tm2d_x2::HR : tm2d::HL + tm2d::HR;
+    for (int tx = tm2d::TX; tx >= 128; tx -= x2 ? 64 : 32) {
+        int o = 0;
+        if ((e = occ_of(tx, &o)) != cudaSuccess) return e;
+        o = o > 0 ? o : 1;
+        // warps of one-column threads holding as many columns (the two-column form
+        // runs half as many threads with twice the work each)
+        const double warps = (double)o * tx / 32.0;
+        double u = warps >= 8.0 ? 1.0 : std::sqrt(warps / 8.0);
+        if (sizeof(T) == 4) {
+            // FP32 waits on memory, and more warps hide more of it: two 256-wide blocks
+            // per SM (16 warps) beat 224 and 192 by 1-8% on 2048^2 to 8192 x 4096 grids,
+            // while three or four narrower blocks per SM ran 15-30% slower
+            u = std::min(warps, 16.0) / 16.0;
+            if (o > 2) u *= kManyBlocks;
+        }
+        if (o < 2) u *= kOneBlock;
+        const int64_t strips = (nx + (tx - halo) - 1) / (tx - halo);
+        const int64_t slots = (int64_t)sms * o;
+        const double r = xedge ? kEdgeCost : 1.0;
+        if constexpr (sizeof(T) == 8) {
+            int ol = 0;  // the work-list form at this tile width
+            if (list_ok && (e = tm2d_list_dispatch_f64(P, nullptr, 0, kListTiles, g->stream, &ol, tx)) != cudaSuccess)
+                return e;
+            ol = ol > 0 ? ol : 1;
+            // (grids too small for chunks of 16 planes on half the resident blocks are
+            // latency-bound: there the uniform grid's shorter chunks did better)
+            if (list_ok && (want_list || 2 * strips * (ny / 16) >= (int64_t)sms * ol)) {
+                std::vector<int4> it;
+                const double tl = list_schedule(strips, xedge, ny, span, sms, ol, want_list, &it);
+                const double wl = (double)ol * tx / 32.0;
+                const double ul = (wl >= 8.0 ? 1.0 : std::sqrt(wl / 8.0)) * (ol < 2 ? kOneBlock : 1.0);
+                const double cost = tl * tx * ol / ul;
+                if (tl > 0 && it.size() <= (size_t)kSchedItems && (best_list < 0 || cost < best_list)) {
+                    best_list = cost;
+                    list_tx = tx;
+                    list_items = std::move(it);
+                }
+            }
+        }
+        // a grid too small to give every resident block a chunk of 16 planes takes
+        // chunks down to 4 planes: the pipeline's extra planes then cost less than
+        // the SMs they would leave idle (small grids are latency-bound)
+        const int64_t min_chunk = strips * (ny / 16) < slots ? 4 : 16;
+        for (int64_t nc = 1; nc <= 512 && ny / nc >= min_chunk; nc++) {  // the same chunks everywhere
+            const int64_t chunk = (ny + nc - 1) / nc, rows = (ny + chunk - 1) / chunk;
+            const int64_t waves = (strips * rows + slots - 1) / slots;
+            const double cost = (double)waves * (double)(chunk + 6 + D) * r * tx * o / u;
+            if (best < 0 || cost < best) {
+                best = cost;
+                tm_tx = tx;
+                P.chunk = (int)chunk;
+                best_cf = (int)chunk;
+                best_ce = (int)chunk;
+                best_rows = (int)rows;
+            }
+        }
+        if (!xedge || strips < 3) continue;
+        for (int64_t ni = 1; ni <= 64 && ny / ni >= 16; ni++) {  // shorter chunks at the x edges
+            const int64_t ri = ni;
+            int64_t cf = 0, cm = 0;
+            const double ci_cost = split(ri, &cf, &cm);
+            const int64_t left = slots - (strips - 2) * ri;
+            if (left < 2) break;
+            int64_t ne = std::min<int64_t>(left / 2, std::max<int64_t>(1, ny / 16));
+            const int64_t ce = (ny + ne - 1) / ne, re = (ny + ce - 1) / ce;
+            const double cost = std::max(ci_cost, (double)(ce + 6) * r + D) * tx * o / u;
+            if (cost < best) {
+                best = cost;
+                tm_tx = tx;
+                P.chunk = (int)cm;
+                best_cf = (int)cf;
+                best_ce = (int)ce;
+                best_rows = (int)std::max(ri, re);
+            }
+        }
+    }
+    if (best < 0) {  // grids shorter than 16 planes: one chunk
+        tm_tx = tm2d::TX;
+        P.chunk = (int)ny;
+        best_cf = (int)ny;
+        best_ce = (int)ny;
+        best_rows = 1;
+    }
+    // the work-list form of the SpanCost model, beside the uniform grid's
+    g->tm_tx = tm_tx;
+    g->tm_chunk = P.chunk;
+    g->tm_chunk_first = best_cf;
+    g->tm_chunk_edge = best_ce;
+    g->tm_nchunks = best_rows;
+    g->tm_list_blocks = 0;
+    g->tm_list_per_block = kListTiles;
+    if (want_list && best_list < 0) return cudaErrorInvalidValue;  // (more than kSchedItems items)
+    // AUTO takes the lists where the model expects them 5% faster: measured on
+    // 512^2 to 8192 x 4096 pulses, a smaller expected gain did not hold
+    if (best_list >= 0 && (want_list || best_list < 0.95 * best)) {
+        g->tm_tx = list_tx;
+        g->tm_list_blocks = (int32_t)(list_items.size() / kListTiles);
+        g->tm_items = std::move(list_items);
+        g->tm_items_uploaded = false;
+    }
+    g->tm_plan_key = key;
+    return cudaSuccess;
+}
+
+// Copies the work lists into the workspace once per plan (on the grid's stream,
+// ordered before the launches that read them).
+cudaError_t tm2d_upload_list(axp_grid *g)
+{
+    if (g->tm_items_uploaded) return cudaSuccess;
+    const size_t bytes = g->tm_items.size() * sizeof(int4);
+    if (g->tm_items.size() > (size_t)kSchedItems) return cudaErrorInvalidValue;
+    cudaError_t e =
+        cudaMemcpyAsync(g->ws + g->layout.off_sched, g->tm_items.data(), bytes, cudaMemcpyHostToDevice, g->stream);
+    if (e == cudaSuccess) g->tm_items_uploaded = true;
+    return e;
+}
+
+template <typename T>
+int32_t fused_path(axp_grid *g)
 {
     const int32_t k = g->kernel_choice;
     if (k == AXP_KERNEL_GENERAL) return AXP_KERNEL_GENERAL;
@@ -350,9 +749,11 @@ int32_t fused_path(const axp_grid *g)
     if (k == AXP_KERNEL_AUTO && b1) return AXP_KERNEL_BLOCK1D;
     const bool tm = tm2d_supported(g), ax = ax3d_supported(g), fu = fused_supported<T>(g);
     if (k == AXP_KERNEL_TM2D) return tm ? AXP_KERNEL_TM2D : AXP_KERNEL_GENERAL;
+    if (k == AXP_KERNEL_TM2D_LIST) return tm && tm2d_list_eligible<T>(g) ? AXP_KERNEL_TM2D_LIST : AXP_KERNEL_GENERAL;
     if (k == AXP_KERNEL_AX3D) return ax ? AXP_KERNEL_AX3D : AXP_KERNEL_GENERAL;
     if (k == AXP_KERNEL_FUSED) return fu ? AXP_KERNEL_FUSED : AXP_KERNEL_GENERAL;
-    return tm ? AXP_KERNEL_TM2D : (ax ? AXP_KERNEL_AX3D : (fu ? AXP_KERNEL_FUSED : AXP_KERNEL_GENERAL));
+    if (tm) return tm2d_plan<T>(g) == cudaSuccess && g->tm_list_blocks > 0 ? AXP_KERNEL_TM2D_LIST : AXP_KERNEL_TM2D;
+    return ax ? AXP_KERNEL_AX3D : (fu ? AXP_KERNEL_FUSED : AXP_KERNEL_GENERAL);
 }
 
 // Fused 1D steps are short (microseconds), so runs of them replay from CUDA
@@ -421,7 +822,7 @@ cudaError_t fused_step(axp_grid *g, int64_t nsteps, bool *handled)
         cudaError_t e = enter_staggered<T>(g);
         return e != cudaSuccess ? e : block1d_step(g, nsteps);
     }
-    const bool tm = path == AXP_KERNEL_TM2D, ax = path == AXP_KERNEL_AX3D;
+    const bool tm = path == AXP_KERNEL_TM2D || path == AXP_KERNEL_TM2D_LIST, ax = path == AXP_KERNEL_AX3D;
     const int mode = grid_mode(g);
     const int set = pick_set(g);
     cudaError_t e = enter_staggered<T>(g);
@@ -436,6 +837,12 @@ cudaError_t fused_step(axp_grid *g, int64_t nsteps, bool *handled)
         return dispatch_tm2d<T>(Pl, nch, g->stream, occp, width);
     };
     auto launch = [&](const fused::Params<T> &Pl, int nch, int *occp) {
+        if constexpr (sizeof(T) == 8) {
+            if (tm && g->tm_plan_key >= 0 && g->tm_list_blocks > 0)
+                return tm2d_list_dispatch_f64(Pl, (const int4 *)(g->ws + g->layout.off_sched),
+                                              nch > 0 ? g->tm_list_blocks : 0, g->tm_list_per_block, g->stream, occp,
+                                              tm_tx);
+        }
         if (tm) return dispatch_2d(Pl, nch, occp, tm_tx);
         if (ax) return dispatch_ax3d<T>(Pl, nch, g->stream, occp);
         return dispatch<T>(mode, set, Pl, nch, g->stream, occp);
@@ -465,115 +872,13 @@ cudaError_t fused_step(axp_grid *g, int64_t nsteps, bool *handled)
             }
         }
     } else if (tm) {
-        // Tile width and march chunks: the fewest resident-block waves for the work
-        // a wave does, (planes + pipeline) x columns x blocks per SM, divided by the
-        // share of its issue rate an SM reaches with that many warps resident.  FP64:
-        // below 8 warps the FP64 pipe's and the loads' latencies are no longer
-        // hidden, sqrt(warps / 8); FP32: warps / 16, and kManyBlocks beyond two blocks
-        // per SM; kOneBlock for one block per SM (all from measured tile widths).
-        // Measured per-CTA times give the other two costs: a strip at a non-periodic x edge runs the edge body
-        // over the x layer and takes kEdgeCost times as long per plane (its warps
-        // wait at each plane's barrier for the layer's warp), and a chunk that
-        // crosses a y layer runs the edge body over the layer and the pipeline's
-        // planes next to it, kLayerCost plane-times each.  With one wave the x-edge
-        // strips may get more, shorter chunks from the blocks the other strips
-        // leave free, and the other strips' first and last chunks are shortened by
-        // the y layer's extra cost.
-        const double kEdgeCost = sizeof(T) == 8 ? 1.55 : 1.35;
-        // A lone block per SM has nothing else to issue while its warps wait at a
-        // plane's barrier: two blocks of half the width ran the 2D pulse 7% faster.
-        const double kOneBlock = 0.92;
-        const double kManyBlocks = 0.7;  // FP32 with more than two blocks per SM (the FP32 rule below)
-        const double kLayerCost = sizeof(T) == 8 ? 0.93 : 0.32;
-        int sms = 152;
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
-        const int64_t nx = g->desc.n[0], ny = g->desc.n[1];
-        const bool xedge = g->desc.em_bc[0][0] != AXP_BC_PERIODIC;
-        const bool ylay = g->desc.em_bc[1][0] != AXP_BC_PERIODIC && P.has_pml;
-        const int64_t D = ylay ? (int64_t)std::lround(kLayerCost * (P.lay[1][0] + 7)) : 0;
-        // `rows` chunks over y: returns the costliest chunk in plane-times, with the
-        // first and the middle chunk sizes (the last chunk is what remains, <= cf)
-        auto split = [&](int64_t rows, int64_t *cf, int64_t *cm) -> double {
-            const int64_t u0 = (ny + rows - 1) / rows;
-            *cf = *cm = u0;
-            if (D == 0 || rows < 3) return (double)(u0 + 6 + D);
-            const int64_t c = (ny + 2 * D + rows - 1) / rows, f = c - D;
-            const int64_t last = ny - f - (rows - 2) * c;
-            if (f < 16 || last < 1 || last > f) return (double)(u0 + 6 + D);
-            *cf = f;
-            *cm = c;
-            return (double)(c + 6);
-        };
-        double best = -1.0;
-        int best_ce = 0, best_rows = 0, best_cf = 0;
-        // tile widths in columns; the two-column form takes multiples of 64 (tx / 2 threads)
-        const int halo = x2 ? tm2d_x2::HL + tm2d_x2::HR : tm2d::HL + tm2d::HR;
-        for (int tx = tm2d::TX; tx >= 128; tx -= x2 ? 64 : 32) {
-            int o = 0;
-            if ((e = dispatch_2d(P, 0, &o, tx)) != cudaSuccess) return e;
-            o = o > 0 ? o : 1;
-            // warps of one-column threads holding as many columns (the two-column form
-            // runs half as many threads with twice the work each)
-            const double warps = (double)o * tx / 32.0;
-            double u = warps >= 8.0 ? 1.0 : std::sqrt(warps / 8.0);
-            if (sizeof(T) == 4) {
-                // FP32 waits on memory, and more warps hide more of it: two 256-wide blocks
-                // per SM (16 warps) beat 224 and 192 by 1-8% on 2048^2 to 8192 x 4096 grids,
-                // while three or four narrower blocks per SM ran 15-30% slower
-                u = std::min(warps, 16.0) / 16.0;
-                if (o > 2) u *= kManyBlocks;
-            }
-            if (o < 2) u *= kOneBlock;
-            const int64_t strips = (nx + (tx - halo) - 1) / (tx - halo);
-            const int64_t slots = (int64_t)sms * o;
-            const double r = xedge ? kEdgeCost : 1.0;
-            // a grid too small to give every resident block a chunk of 16 planes takes
-            // chunks down to 4 planes: the pipeline's extra planes then cost less than
-            // the SMs they would leave idle (small grids are latency-bound)
-            const int64_t min_chunk = strips * (ny / 16) < slots ? 4 : 16;
-            for (int64_t nc = 1; nc <= 512 && ny / nc >= min_chunk; nc++) {  // the same chunks everywhere
-                const int64_t chunk = (ny + nc - 1) / nc, rows = (ny + chunk - 1) / chunk;
-                const int64_t waves = (strips * rows + slots - 1) / slots;
-                const double cost = (double)waves * (double)(chunk + 6 + D) * r * tx * o / u;
-                if (best < 0 || cost < best) {
-                    best = cost;
-                    tm_tx = tx;
-                    P.chunk = (int)chunk;
-                    best_cf = (int)chunk;
-                    best_ce = (int)chunk;
-                    best_rows = (int)rows;
-                }
-            }
-            if (!xedge || strips < 3) continue;
-            for (int64_t ni = 1; ni <= 64 && ny / ni >= 16; ni++) {  // shorter chunks at the x edges
-                const int64_t ri = ni;
-                int64_t cf = 0, cm = 0;
-                const double ci_cost = split(ri, &cf, &cm);
-                const int64_t left = slots - (strips - 2) * ri;
-                if (left < 2) break;
-                int64_t ne = std::min<int64_t>(left / 2, std::max<int64_t>(1, ny / 16));
-                const int64_t ce = (ny + ne - 1) / ne, re = (ny + ce - 1) / ce;
-                const double cost = std::max(ci_cost, (double)(ce + 6) * r + D) * tx * o / u;
-                if (cost < best) {
-                    best = cost;
-                    tm_tx = tx;
-                    P.chunk = (int)cm;
-                    best_cf = (int)cf;
-                    best_ce = (int)ce;
-                    best_rows = (int)std::max(ri, re);
-                }
-            }
-        }
-        if (best < 0) {  // grids shorter than 16 planes: one chunk
-            tm_tx = tm2d::TX;
-            P.chunk = (int)ny;
-            best_cf = (int)ny;
-            best_ce = (int)ny;
-            best_rows = 1;
-        }
-        P.chunk_first = best_cf;
-        P.chunk_edge = best_ce;
-        nchunks = best_rows;
+        if ((e = tm2d_plan<T>(g)) != cudaSuccess) return e;
+        tm_tx = g->tm_tx;
+        P.chunk = g->tm_chunk;
+        P.chunk_first = g->tm_chunk_first;
+        P.chunk_edge = g->tm_chunk_edge;
+        nchunks = g->tm_nchunks;
+        if (g->tm_list_blocks > 0 && (e = tm2d_upload_list(g)) != cudaSuccess) return e;
     } else if (mode >= 2) {
         int sms = 152;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
@@ -665,8 +970,8 @@ fused::Params<T> tm2d_params(axp_grid *g, int chunk)
 }
 
 template fused::Params<float> tm2d_params<float>(axp_grid *, int);
-template int32_t fused_path<double>(const axp_grid *);
-template int32_t fused_path<float>(const axp_grid *);
+template int32_t fused_path<double>(axp_grid *);
+template int32_t fused_path<float>(axp_grid *);
 template bool fused_supported<double>(const axp_grid *);
 template bool fused_supported<float>(const axp_grid *);
 template cudaError_t fused_step<double>(axp_grid *, int64_t, bool *);

@@ -15,6 +15,12 @@ cudaError_t tm2d_dispatch_f64(const fused::Params<double> &P, int nchunks, cudaS
     return tm2d::launch<double, false>(P, nchunks, s, occ, tx);
 }
 
+cudaError_t tm2d_list_dispatch_f64(const fused::Params<double> &P, const int4 *items, int nblocks, int per_block,
+                                   cudaStream_t s, int *occ, int tx)
+{
+    return tm2d::launch_list<double, false>(P, items, nblocks, per_block, s, occ, tx);
+}
+
 cudaError_t ax3d_dispatch_f64(const fused::Params<double> &P, int nchunks, cudaStream_t s, int *occ)
 {
     return ax3d::launch<double, false>(P, nchunks, s, occ);

@@ -80,17 +80,17 @@ __device__ __forceinline__ void cp_wait()
 // rows published each iteration (all at x offset +1 in the row)
 enum { R_E0Z, R_E1Y, R_E1Z, R_PHI, R_N0Y2, R_MID3, R_N0Y3, R_PX4, R_N1Z4, R_N1Y4, R_N0Y4, NROWS };
 
-// One tile: x strip bx (VX written columns) and march chunk by (P.chunk planes)
-// of the grid P describes.  `rows` is the block's shared staging; the caller
-// separates consecutive tiles of one block with a barrier.  SRC compiles in the
-// soft source's sheets (P.src_x >= 0); without it the body has no trace of them.
+// One tile: x strip bx (VX written columns), planes [m0, m1) of the grid P
+// describes.  `rows` is the block's shared staging; the caller separates
+// consecutive tiles of one block with a barrier.  SRC compiles in the soft
+// source's sheets (P.src_x >= 0); without it the body has no trace of them.
 // FOLDP: square cells (dx = dy) and no uniform background B along x or y, the
 // 2D pulse's case.  The axion current is then carried as P / (1/(2 dt)): the
 // factor meets the gradient's 1/(4 dx) in one constant and the current's
 // coefficient in the E updates, three operations fewer per cell.
 template <typename T, bool INCR, bool SRC = false, bool FOLDP = false>
-__device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, const int by, T (&rows)[2][NROWS][RS],
-                                     T *stage)
+__device__ __forceinline__ void tile_span(const fused::Params<T> &P, const int bx, const int m0, const int m1,
+                                          T (&rows)[2][NROWS][RS], T *stage)
 {
     constexpr int NS = ns<T>();
     const int ntx = (int)blockDim.x, vx = ntx - HL - HR;  // this launch's tile width
@@ -103,23 +103,17 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
     int wx = gx;
     if (wx < 0 || wx >= nx) wx = perx ? ((wx % nx) + nx) % nx : -1;
     const bool write_col = tx >= HL && tx < ntx - HR && gx >= 0 && gx < nx;
-    // the strips at a non-periodic x edge (which carry the x layers and run the
-    // edge body) may march shorter chunks than the others; the others' first chunk
-    // (and, by the host's choice of sizes, about the last) may be shorter than the
-    // rest, since they run the edge body over the y layers
-    const int nstrips = (nx + vx - 1) / vx;
-    const bool xstrip = !perx && (bx == 0 || bx == nstrips - 1);
-    const int chunk = xstrip ? P.chunk_edge : P.chunk;
-    const int first = xstrip ? P.chunk_edge : P.chunk_first;
-    const int m0 = by == 0 ? 0 : first + (by - 1) * chunk;
-    if (m0 >= ny) return;  // (the whole block: more chunk rows than this strip uses)
-    const int m1 = min(ny, by == 0 ? first : m0 + chunk);
     const int gx0 = bx * vx - HL;
     // The plain body is exact for a column inside the grid with no x layer (the
     // edge body adds nothing there), so the choice is made per warp: in a tile
     // at an x edge only the warps over the layer take the edge body.
     const int wx0 = gx0 + (tx & ~31), wx1 = wx0 + 31;
     const bool tile_fast = perx || (wx0 - 1 >= P.lay[0][0] && wx1 + 1 <= nx - 1 - P.lay[0][1]);
+    // A warp whose columns all lie beyond the last column of a non-periodic grid
+    // would compute the closure's zeros (the edge body sets every value it keeps or
+    // publishes to zero outside the grid): it keeps the zeros of its registers and
+    // of the zeroed rows instead, and leaves the pipes to the other warps.
+    const bool dead = !perx && wx0 >= nx;
     const int ylo = P.lay[1][0], yhi = ny - 1 - P.lay[1][1];
 
     const T h = P.h, g = P.g, idx = P.idx[0], idy = P.idx[1], hidx = P.hidx[0], hidy = P.hidx[1];
@@ -449,11 +443,11 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
     // wait at the end of iteration t everything up to plane t+1 has landed
     for (int p = t0 - 4; p < t0; p++) fill_y(p);  // joins the first group (plane t0)
     for (int j = 0; j < NS - 1; j++) {
-        if (t0 + j <= t1) prefetch(t0 + j);
+        if (!dead && t0 + j <= t1) prefetch(t0 + j);
         cp_commit();
     }
     cp_wait<NS - 2>();
-    take(t0);
+    if (!dead) take(t0);
     __syncthreads();
     // FP32: unrolled by 4, so that the column history shifts become register
     // renaming and the row buffer and staging slot indices (taken relative to t0)
@@ -461,10 +455,12 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
     // (its registers are at the limit)
 #pragma unroll(sizeof(T) == 4 ? 4 : 1)
     for (int t = t0; t <= t1; ++t) {
-        if (t + NS - 1 <= t1) prefetch(t + NS - 1);
+        if (!dead && t + NS - 1 <= t1) prefetch(t + NS - 1);
         cp_commit();
         const int b = (t - t0) & 1;
-        // publish what the x neighbours read in this iteration
+        // publish what the x neighbours read in this iteration (a dead warp's slots
+        // keep their zeros; fill_y is warp 0's, which always holds a column of the grid)
+        if (!dead) {
         rows[b][R_E0Z][tx + 1] = E0z1;
         rows[b][R_E1Y][tx + 1] = E1y1;
         rows[b][R_E1Z][tx + 1] = E1z1;
@@ -476,10 +472,15 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
         rows[b][R_N1Z4][tx + 1] = N1z4;
         rows[b][R_N1Y4][tx + 1] = N1y4;
         rows[b][R_N0Y4][tx + 1] = N0y4;
+        }
         __syncthreads();
         const bool fast = tile_fast && (pery || (t - 6 >= ylo && t + 1 <= yhi));
-        if (fast) body(std::false_type{}, t, b);
-        else body(std::true_type{}, t, b);
+        if (dead) {
+        } else if (fast) {
+            body(std::false_type{}, t, b);
+        } else {
+            body(std::true_type{}, t, b);
+        }
         // advance the column history by one plane
         E0z4 = E0z3; E0z3 = E0z2; E0z2 = E0z1; E0z1 = E0z0;
         E1x4 = E1x3; E1x3 = E1x2; E1x2 = E1x1; E1x1 = E1x0;
@@ -495,9 +496,30 @@ __device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, co
         SM4 = SM3; SM3 = SM2; DF4 = DF3; DF3 = DF2; EN4 = EN3; EN3 = EN2;
         PX4 = PX3; PY4 = PY3;
         cp_wait<NS - 2>();
-        if (t < t1) take(t + 1);
+        if (!dead && t < t1) take(t + 1);
     }
     cp_wait<0>();
+}
+
+// The tile of strip bx and march chunk by of the uniform launch grid.  The strips
+// at a non-periodic x edge (which carry the x layers and run the edge body) may
+// march shorter chunks than the others; the others' first chunk (and, by the
+// host's choice of sizes, about the last) may be shorter than the rest, since they
+// run the edge body over the y layers.
+template <typename T, bool INCR, bool SRC = false, bool FOLDP = false>
+__device__ __forceinline__ void tile(const fused::Params<T> &P, const int bx, const int by, T (&rows)[2][NROWS][RS],
+                                     T *stage)
+{
+    const int ntx = (int)blockDim.x, vx = ntx - HL - HR;
+    const int nx = P.n[0], ny = P.n[1];
+    const int nstrips = (nx + vx - 1) / vx;
+    const bool xstrip = !P.per[0] && (bx == 0 || bx == nstrips - 1);
+    const int chunk = xstrip ? P.chunk_edge : P.chunk;
+    const int first = xstrip ? P.chunk_edge : P.chunk_first;
+    const int m0 = by == 0 ? 0 : first + (by - 1) * chunk;
+    if (m0 >= ny) return;  // (the whole block: more chunk rows than this strip uses)
+    const int m1 = min(ny, by == 0 ? first : m0 + chunk);
+    tile_span<T, INCR, SRC, FOLDP>(P, bx, m0, m1, rows, stage);
 }
 
 template <typename T, bool INCR, bool SRC, bool FOLDP = false>
@@ -528,6 +550,56 @@ cudaError_t launch_variant(const fused::Params<T> &P, int nchunks, cudaStream_t 
     dim3 grid((P.n[0] + vx - 1) / vx, nchunks, 1);
     kern<<<grid, tx, dyn, stream>>>(P);
     return cudaGetLastError();
+}
+
+// Work-list form: block b runs the tiles items[b * per_block + j], j < per_block,
+// one after the other (x: strip, y and z: planes [y, z); an item with z <= y is
+// empty).  The host balances the lists so that every block's tiles cost about
+// the same, with all blocks resident at once.
+template <typename T, bool INCR, bool FOLDP>
+__global__ void __launch_bounds__(TX, sizeof(T) == 4 ? 2 : 1)
+    k_tm2d_list(fused::Params<T> P, const int4 *__restrict__ items, int per_block)
+{
+    __shared__ T rows[2][NROWS][RS];
+    extern __shared__ __align__(16) unsigned char tm2d_dyn[];
+    for (int j = 0; j < per_block; j++) {
+        const int4 it = items[(size_t)blockIdx.x * per_block + j];
+        if (it.z <= it.y) continue;  // (the same item for the whole block)
+        if (j > 0) __syncthreads();  // the previous tile's last reads of rows and yring
+        tile_span<T, INCR, false, FOLDP>(P, it.x, it.y, it.z, rows, reinterpret_cast<T *>(tm2d_dyn));
+    }
+}
+
+template <typename T, bool INCR, bool FOLDP>
+cudaError_t launch_list_variant(const fused::Params<T> &P, const int4 *items, int nblocks, int per_block,
+                                cudaStream_t stream, int *occupancy, int tx)
+{
+    static int occ[TX / 32 + 1] = {};
+    auto kern = k_tm2d_list<T, INCR, FOLDP>;
+    const size_t dyn = stage_bytes<T>(tx);
+    if (tx < 64 || tx > TX || tx % 32) return cudaErrorInvalidValue;
+    if (occ[tx / 32] == 0) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stage_bytes<T>());
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[tx / 32], kern, tx, dyn);
+        if (e != cudaSuccess) return e;
+    }
+    if (occupancy) *occupancy = occ[tx / 32];
+    if (nblocks <= 0) return cudaSuccess;
+    kern<<<nblocks, tx, dyn, stream>>>(P, items, per_block);
+    return cudaGetLastError();
+}
+
+// The work-list form takes grids without a soft source.
+template <typename T, bool INCR>
+cudaError_t launch_list(const fused::Params<T> &P, const int4 *items, int nblocks, int per_block, cudaStream_t stream,
+                        int *occupancy, int tx)
+{
+    if (P.src_x >= 0) return cudaErrorInvalidValue;
+#ifndef AXP_TM2D_NO_FOLDP
+    if (sizeof(T) == 8 && P.Bext[0] == T(0) && P.Bext[1] == T(0) && P.idx[0] == P.idx[1])
+        return launch_list_variant<T, INCR, true>(P, items, nblocks, per_block, stream, occupancy, tx);
+#endif
+    return launch_list_variant<T, INCR, false>(P, items, nblocks, per_block, stream, occupancy, tx);
 }
 
 template <typename T, bool INCR>

@@ -41,7 +41,7 @@ def test_full_size_pulse_grid_matches_the_oracle_on_sub_boxes(prec):
     g.load(W.random_state(grid, seed=20240624 + 1, active=active))
     start = g.fields()
     g.step(N_STEPS)
-    assert g.kernel_path() == axp.AXP_KERNEL_TM2D
+    assert g.kernel_path() in (axp.AXP_KERNEL_TM2D, axp.AXP_KERNEL_TM2D_LIST)
     end = g.fields()
     g.close()
     margin = L + 3 * N_STEPS + 2
@@ -113,3 +113,25 @@ def test_full_size_axion_box_matches_the_oracle_on_sub_boxes():
             assert np.linalg.norm(a - r) <= 1e-4 * nr, (b, k, np.linalg.norm(a - r) / nr)
         # the axion wave drives E1 along B_ext (y) through J = (D_t phi) B_ext
         assert np.linalg.norm(ref["phi_cur"][inner]) > 0 and np.linalg.norm(ref["E1y"][inner]) > 0
+
+
+def test_full_size_pulse_work_lists_equal_the_uniform_grid():
+    """At the full 4096 x 2048 size the FP64 2D kernel's two launch forms, the
+    balanced work lists and the uniform grid of strips by chunks, give the same
+    fields bit for bit after a few steps from the same random state."""
+    from paper_2406_16796_gb300 import axp
+
+    grid = W.pulse_2d(precision="fp64").grid
+    active = ["E0z", "B0x", "B0y"] + [n for n in W.FIELD_NAMES if n[1] == "1"]
+    st = W.random_state(grid, seed=20240624 + 7, active=active)
+    out = {}
+    for kernel in (axp.AXP_KERNEL_TM2D_LIST, axp.AXP_KERNEL_TM2D):
+        g = axp.Grid(grid)
+        g.set_kernel(kernel)
+        g.load(st)
+        assert g.kernel_path() == kernel
+        g.step(3)
+        out[kernel] = g.fields()
+        g.close()
+    for k in NAMES:
+        assert np.array_equal(out[axp.AXP_KERNEL_TM2D_LIST][k], out[axp.AXP_KERNEL_TM2D][k]), k

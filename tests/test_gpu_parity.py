@@ -359,6 +359,76 @@ AX3D_CASES = {
 }
 
 
+@pytest.mark.parametrize("case", sorted(TM2D_CASES))
+def test_tm2d_work_lists_equal_the_uniform_grid_and_the_oracle(case):
+    """The 2D kernel's work-list form (tiles of about equal cost, two short ones
+    sharing a block) computes every cell with the same operations as the uniform
+    launch grid: the fields are bit for bit those of the grid form, and within
+    1e-12 of the oracle, after 12 steps."""
+    axp = axp_mod()
+    grid = periodic_grid(g=0.7, m=1.1, **TM2D_CASES[case])
+    active = ["E0z", "B0x", "B0y"] + [n for n in W.FIELD_NAMES if n[1] == "1"]
+    st = W.random_state(grid, seed=405, active=active)
+    out = {}
+    for kernel in (axp.AXP_KERNEL_TM2D, axp.AXP_KERNEL_TM2D_LIST):
+        g = axp.Grid(grid)
+        g.set_kernel(kernel)
+        g.load(st)
+        assert g.kernel_path() == kernel
+        g.step(5)
+        g.step(7)
+        out[kernel] = g.fields()
+        g.close()
+    og = oracle.OracleGrid(grid)
+    og.load(st)
+    og.step(12)
+    ref = og.fields()
+    for k in NAMES:
+        assert np.array_equal(out[axp.AXP_KERNEL_TM2D_LIST][k], out[axp.AXP_KERNEL_TM2D][k]), (case, k)
+        assert rel(out[axp.AXP_KERNEL_TM2D_LIST][k], ref[k]) < 1e-12, (case, k)
+
+
+@pytest.mark.parametrize("n", [(300, 40, 1), (1000, 17, 1), (130, 700, 1), (260, 3, 1)])
+def test_tm2d_work_lists_on_ragged_shapes(n):
+    """Work lists on shapes whose strips end in a few columns (the last strip's
+    warps beyond the grid keep the closure's zeros without computing them), whose
+    strips outnumber or are outnumbered by the resident blocks, and one only three
+    planes high: bit for bit the uniform grid's fields."""
+    axp = axp_mod()
+    grid = periodic_grid(g=0.9, m=0.7, n=n, d=(0.05, 0.05, 0.05), B_ext=(0.0, 0.0, 1.1),
+                         axion_bc=W._bcs("pml", "pml"), em_bc=W._bcs("pml", "pml"), pml_cells=min(6, n[1] // 2))
+    if n[1] < 8:
+        grid = grid.replace(axion_bc=W._bcs("pml", "periodic"), em_bc=W._bcs("pml", "periodic"))
+    active = ["E0z", "B0x", "B0y"] + [k for k in W.FIELD_NAMES if k[1] == "1"]
+    st = W.random_state(grid, seed=406, active=active)
+    out = {}
+    for kernel in (axp.AXP_KERNEL_TM2D, axp.AXP_KERNEL_TM2D_LIST, axp.AXP_KERNEL_GENERAL):
+        g = axp.Grid(grid)
+        g.set_kernel(kernel)
+        g.load(st)
+        g.step(9)
+        out[kernel] = g.fields()
+        g.close()
+    for k in NAMES:
+        assert np.array_equal(out[axp.AXP_KERNEL_TM2D_LIST][k], out[axp.AXP_KERNEL_TM2D][k]), (n, k)
+        assert rel(out[axp.AXP_KERNEL_TM2D_LIST][k], out[axp.AXP_KERNEL_GENERAL][k]) < 1e-12, (n, k)
+
+
+def test_tm2d_work_lists_refuse_fp32_and_soft_sources():
+    """The work-list form takes FP64 grids without a soft source; forcing it on
+    others is an error, not a fallback."""
+    axp = axp_mod()
+    kw = dict(n=(200, 60, 1), B_ext=(0.0, 0.0, 1.0), axion_bc=W._bcs("pml", "pml"), em_bc=W._bcs("pml", "pml"),
+              pml_cells=6)
+    g = axp.Grid(periodic_grid(g=0.7, m=1.1, precision="fp32", **kw))
+    g.set_kernel(axp.AXP_KERNEL_TM2D_LIST)
+    assert g.kernel_path() == axp.AXP_KERNEL_GENERAL
+    with pytest.raises(axp.AxpError) as e:
+        g.step(1)
+    assert e.value.status == axp.AXP_E_STATE
+    g.close()
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("case", sorted(AX3D_CASES))
 def test_ax3d_kernel_vs_oracle_and_generic(case, prec):
@@ -461,7 +531,7 @@ def test_fused_odd_step_counts_keep_inactive_arrays_zero(steps):
     g = axp.Grid(grid)
     g.load(st)
     g.step(steps)
-    assert g.kernel_path() == axp.AXP_KERNEL_TM2D
+    assert g.kernel_path() in (axp.AXP_KERNEL_TM2D, axp.AXP_KERNEL_TM2D_LIST)
     got, ref = g.fields(), og.fields()
     for k in ("E0x", "E0y", "B0z"):
         assert not got[k].any(), k
@@ -509,7 +579,10 @@ def test_tiny_grids_match_the_oracle(case, prec):
         og.step(5)
         if kernel == axp.AXP_KERNEL_AUTO:
             want = paths[0 if prec == "fp64" else 1]
-            assert g.kernel_path() == getattr(axp, "AXP_KERNEL_" + want), (case, g.kernel_path(), want)
+            ok = {getattr(axp, "AXP_KERNEL_" + want)}
+            if want == "TM2D" and prec == "fp64":
+                ok.add(axp.AXP_KERNEL_TM2D_LIST)  # (the 2D kernel's work-list form, where the planner prefers it)
+            assert g.kernel_path() in ok, (case, g.kernel_path(), want)
         got, ref = g.fields(), og.fields()
         for k in list(W.FIELD_NAMES) + ["phi_cur", "phi_old"]:
             assert rel(got[k], ref[k]) <= tol, (case, kernel, k, rel(got[k], ref[k]))

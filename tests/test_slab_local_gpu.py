@@ -43,7 +43,10 @@ def test_local_slabs_match_the_undivided_grid(case, prec):
     runs = [slab.SlabRun(glob, r, world, k, slab.LocalComm()) for r in range(world)]
     for r in runs:
         r.load_global(start)
-        assert r.engine.grid.kernel_path() == getattr(axp, "AXP_KERNEL_" + kern)
+        ok = {getattr(axp, "AXP_KERNEL_" + kern)}
+        if kern == "TM2D" and prec == "fp64":
+            ok.add(axp.AXP_KERNEL_TM2D_LIST)  # (the work-list form, where the planner prefers it)
+        assert r.engine.grid.kernel_path() in ok
     slab.run_local(runs, rounds)
     ax = 2 - slab.split_axis(glob)
     got = {name: np.concatenate([r.owned(r.engine.fields())[name] for r in runs], axis=ax) for name in NAMES}
