@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=1000)
     ap.add_argument("--serve-open-requests", type=int, default=200)
     ap.add_argument("--n3d", type=int, default=512, help="edge of the 3D axion box")
+    ap.add_argument("--tm2d-form", default="auto", choices=["auto", "grid", "list"],
+                    help="launch form of the 2D kernel on the headline grid: the planner's choice, the uniform "
+                         "grid of strips by chunks, or the balanced work lists (FP64)")
     return ap.parse_args()
 
 
@@ -274,8 +277,10 @@ def bytes_per_cell(prec):
 # one-pass stencil grows with the cells); None until a capture of the kernel as
 # it stands exists.  Sources are summarised under profiles/.
 TRAFFIC = {
-    # k_tm2d, 2048 x 2048 capture: FP64 688.8 MB per launch
-    ("k_tm2d (one launch per step)", "fp64"): 688.8e6 * (4096 * 2048) / (2048 * 2048),
+    # k_tm2d_list (FP64, work lists), 2048 x 2048 capture: 689.3 MB per launch
+    ("k_tm2d_list (one launch per step)", "fp64"): 689.3e6 * (4096 * 2048) / (2048 * 2048),
+    # k_tm2d (FP64, uniform grid), 2048 x 2048 capture: 689.2 MB per launch
+    ("k_tm2d (one launch per step)", "fp64"): 689.2e6 * (4096 * 2048) / (2048 * 2048),
     # k_tm2d_x2 (FP32 split, two columns per thread), 2048 x 2048 capture: 345.0 MB per launch
     ("k_tm2d_x2 (one launch per step)", "fp32"): 345.0e6 * (4096 * 2048) / (2048 * 2048),
 }
@@ -296,11 +301,13 @@ def load_peaks():
 # multiply or FMA) per cycle per SM; the SM count and the SM clock are read
 # live (device properties; nvidia-smi samples over the timed region).
 FP64_PIPE_WARP_INST_PER_CYCLE_PER_SM = 1.0 / 16.0
-# FP64-pipe warp instructions k_tm2d executes per cell-update (ncu,
-# sm__inst_executed_pipe_fp64.sum over one launch of the 2048 x 2048 pulse grid:
-# 7,899,910 for 4,194,304 cells; per cell the same at 4096 x 2048 to the share
-# of halo columns and layer cells), i.e. 60.3 thread-operation slots per cell
-FP64_PIPE_WARP_INST_PER_CELL = 7899910 / 4194304
+# FP64-pipe warp instructions the 2D kernel executes per cell-update, by launch
+# form (ncu, sm__inst_executed_pipe_fp64.sum over one launch of the 2048 x 2048
+# pulse grid, 4,194,304 cells; per cell the same at 4096 x 2048 to the share of
+# halo columns and layer cells): 7,348,298 on work lists (56.1 thread-operation
+# slots per cell), 7,468,742 on the uniform grid (57.0)
+FP64_PIPE_WARP_INST_PER_CELL = {"k_tm2d_list (one launch per step)": 7348298 / 4194304,
+                                "k_tm2d (one launch per step)": 7468742 / 4194304}
 
 
 def fp64_pipe_peak_gops(sm_count, sm_mhz):
@@ -591,6 +598,8 @@ def gpu_arm(args):
     prec = args.precision
     w = workload(args, prec)
     g = axp.Grid(w.grid)
+    if args.tm2d_form != "auto":
+        g.set_kernel(axp.AXP_KERNEL_TM2D if args.tm2d_form == "grid" else axp.AXP_KERNEL_TM2D_LIST)
     for L in w.lasers:
         g.inject_laser(L)
     cells = w.grid.cells
@@ -620,23 +629,25 @@ def gpu_arm(args):
     hbm_achieved = bpc * cells / per_launch / 1e9
     hbm = {"achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_achieved / hbm_peak,
            "peak_source": hbm_src, "algorithmic_bytes_per_cell": bpc}
-    kern = {axp.AXP_KERNEL_TM2D: "k_tm2d (one launch per step)", axp.AXP_KERNEL_FUSED: "k_fused (one launch per step)"}.get(
-        path, "general kernels (8 launches per step)")
+    kern = {axp.AXP_KERNEL_TM2D: "k_tm2d (one launch per step)",
+            axp.AXP_KERNEL_TM2D_LIST: "k_tm2d_list (one launch per step)",
+            axp.AXP_KERNEL_FUSED: "k_fused (one launch per step)"}.get(path, "general kernels (8 launches per step)")
     if prec == "fp64":
         sm_count = torch.cuda.get_device_properties(local).multi_processor_count
         sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
         peak = fp64_pipe_peak_gops(sm_count, sm_mhz)
         # executed: the kernel's FP64-pipe issue (ncu count per cell) at the live rate
-        executed = FP64_PIPE_WARP_INST_PER_CELL * 32 * cells / per_launch / 1e9
+        inst_per_cell = FP64_PIPE_WARP_INST_PER_CELL.get(kern)
+        executed = inst_per_cell * 32 * cells / per_launch / 1e9 if inst_per_cell else None
         # algorithmic: the scheme's 77 operations per cell-update at the same rate
         algorithmic = FP64_OPS_PER_CELL * cells / per_launch / 1e9
         flops = FLOPS_PER_CELL * cells / per_launch / 1e12
         roofline = {"bound": "alu", "achieved": executed, "peak": peak, "unit": "Gop/s (FP64 pipe)",
-                    "frac": executed / peak,
+                    "frac": executed / peak if executed else None,
                     "traffic": TRAFFIC.get((kern, prec)) if cells == NX * NY else None, "kernel": kern,
                     "peak_source": "measured: ncu sm__inst_executed_pipe_fp64 peak 1/16 warp instruction per cycle "
                                    "per SM (2 FP64 ops/cycle/SM) x %d SMs x %.0f MHz sampled" % (sm_count, sm_mhz),
-                    "executed_fp64_ops_per_cell": FP64_PIPE_WARP_INST_PER_CELL * 32,
+                    "executed_fp64_ops_per_cell": inst_per_cell * 32 if inst_per_cell else None,
                     "algorithmic_fp64_ops_per_cell": FP64_OPS_PER_CELL,
                     "algorithmic_equivalent": {"achieved": algorithmic, "frac": algorithmic / peak,
                                                "what": "the scheme's 77 operations per cell-update at the measured "
@@ -700,7 +711,11 @@ def gpu_arm(args):
         per32 = el32 / max(1, l32)
         ach = bytes_per_cell("fp32") * cells / per32 / 1e9
         # FP32 split on an even-width grid takes the two-column form of the 2D kernel
-        kern32 = "k_tm2d_x2 (one launch per step)" if (path == axp.AXP_KERNEL_TM2D and args.nx % 2 == 0) else kern
+        path32 = g32.kernel_path()
+        kern32 = ("k_tm2d_x2 (one launch per step)" if (path32 == axp.AXP_KERNEL_TM2D and args.nx % 2 == 0)
+                  else "k_tm2d (one launch per step)" if path32 == axp.AXP_KERNEL_TM2D
+                  else "k_fused (one launch per step)" if path32 == axp.AXP_KERNEL_FUSED
+                  else "general kernels (8 launches per step)")
         other = {"precision": "fp32_split", "value": cells * k32 * world / el32, "unit": "cell-updates/s",
                  "steps": k32, "ms_per_step": el32 / k32 * 1e3, "kernel": kern32,
                  "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
