@@ -246,6 +246,11 @@ bool fused_supported(const axp_grid *g)
 #define AXP_LINE_BLOCK 12
 #endif
 constexpr int kLineBlock = AXP_LINE_BLOCK;
+// blocks per SM of the time-blocked 1D kernel (each owns n / (SMs x this) cells)
+#ifndef AXP_LINE_BLOCKS_PER_SM
+#define AXP_LINE_BLOCKS_PER_SM 1
+#endif
+constexpr int kLineBlocksPerSM = AXP_LINE_BLOCKS_PER_SM;
 
 // Which grids take the time-blocked 1D kernel: FP64, 1D and periodic along x,
 // no soft source and no uniform E (as the other single-pass kernels), a window
@@ -262,7 +267,7 @@ bool block1d_supported(const axp_grid *g)
     int coop = 0, sms = 0;
     if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, g->device) != cudaSuccess || !coop) return false;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device) != cudaSuccess || sms < 1) return false;
-    const int64_t seg = (d.n[0] + sms - 1) / sms;
+    const int64_t slots = (int64_t)sms * kLineBlocksPerSM, seg = (d.n[0] + slots - 1) / slots;
     return seg + 2 * (kLineBlock + 3) <= line1d::kMaxWindow;
 }
 
@@ -280,7 +285,7 @@ cudaError_t block1d_step(axp_grid *g, int64_t nsteps)
     A.n = d.n[0];
     A.tblock = kLineBlock;
     A.halo = kLineBlock + 3;
-    A.seg = (int)((d.n[0] + sms - 1) / sms);
+    A.seg = (int)((d.n[0] + (int64_t)sms * kLineBlocksPerSM - 1) / ((int64_t)sms * kLineBlocksPerSM));
     const int blocks = (int)((d.n[0] + A.seg - 1) / A.seg);
     const size_t smem = (size_t)line1d::kArrays * (A.seg + 2 * A.halo) * sizeof(double);
     e = cudaFuncSetAttribute(line1d::k_line1d, cudaFuncAttributeMaxDynamicSharedMemorySize,
