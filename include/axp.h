@@ -251,8 +251,9 @@ axp_status axp_compute_diagnostics(axp_grid *grid, axp_diag *out);
  * limited to 8,388,608 cells (AXP_E_INVAL beyond, with a message on stderr).
  * The array lives on every GPU that loads the library until the process exits.
  * The first call on a device looks up the array's device address (with that
- * device current) and keeps it for the life of the process; make that first
- * call before any stream capture.  A cudaDeviceReset of the device discards
+ * device current) and keeps it for the life of the process.  Every call
+ * synchronises its stream, so the entry point cannot be used inside a stream
+ * capture.  A cudaDeviceReset of the device discards
  * the array and so the kept address: do not call this entry point on that
  * device again in the same process after a reset.  Every call shares the array and
  * rewrites what it uses, so results never depend on earlier calls, but calls
