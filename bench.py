@@ -661,10 +661,10 @@ def gpu_arm(args):
                     "kernel": kern,
                     "peak_source": hbm_src, "algorithmic_bytes_per_cell": bpc}
 
-    # e2e through the C ABI with pinned host buffers, the way a user runs the
-    # workload: upload the state, run the steps with the diagnostics recorded
-    # every 100 steps (the workload's cadence) into the grid's ring, read the
-    # records back, download the final state
+    # e2e through the C ABI with pinned host buffers, the way a user resumes the
+    # workload from a checkpoint: upload the state image, run the steps with the
+    # diagnostics recorded every 100 steps (the workload's cadence) into the
+    # grid's ring, read the records back, download the final image
     e2e = None
     if not args.no_e2e:
         ge = axp.Grid(w.grid, diag_every=100, diag_capacity=64)
@@ -694,8 +694,8 @@ def gpu_arm(args):
         diag_bytes = 88 * len(recs)
         e2e = {"value": cells * k * world / (t1 - t0), "unit": "cell-updates/s", "h2d_bytes_per_step": nbytes / k,
                "d2h_bytes_per_step": (nbytes + diag_bytes) / k, "steps": k, "diagnostics_records": len(recs),
-               "what": "state upload from pinned host, k steps with FP64 diagnostics every 100 steps, "
-                       "diagnostics read-back, state download"}
+               "what": "checkpoint image of the running simulation uploaded from pinned host, k steps with "
+                       "FP64 diagnostics every 100 steps, diagnostics read-back, checkpoint image downloaded"}
         ge.close()
     g.close()
 

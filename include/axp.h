@@ -282,9 +282,14 @@ axp_status axp_write_ghost(axp_grid *grid, int32_t axis, int32_t side, int32_t l
  * the arrays that can be non-zero: the order-0 components the injected laser
  * couples to, all order-1 components and both axion levels; the cached axion
  * current is recomputed after a load.  Its size therefore follows the grid's
- * injected components at the time of the save.  Loading into a grid of the
- * same descriptor resumes bit for bit (arrays outside the image are set to
- * zero).  Both synchronise. */
+ * injected components at the time of the save.  A grid that the single-pass
+ * kernels are stepping keeps E half a step ahead of B (leapfrog staggering);
+ * its image is taken in that form, without a conversion, unless the grid has
+ * a soft source (then E is converted to integer time first).  Loading into a
+ * grid of the same descriptor resumes bit for bit, a staggered image as the
+ * uninterrupted run would have continued (arrays outside the image are set to
+ * zero); a staggered image cannot be loaded into a grid with a soft source
+ * (AXP_E_STATE).  Both synchronise. */
 axp_status axp_state_bytes(const axp_grid *grid, size_t *bytes);
 axp_status axp_save_state(axp_grid *grid, void *host_dst, size_t bytes);
 axp_status axp_load_state(axp_grid *grid, const void *host_src, size_t bytes);

@@ -176,7 +176,7 @@ struct StateHeader {
     int32_t phi_active;
     int32_t win_axis;    // moving window (-1: none) and its state
     int32_t win_cells;
-    int32_t pad;
+    int32_t staggered;   // 1: E arrays hold E^{n+1/2} (the single-pass kernels' state)
     double win_velocity, win_travel;
     int64_t win_start, win_offset;
 };
@@ -880,13 +880,17 @@ axp_status axp_write_ghost(axp_grid *g, int32_t axis, int32_t side, int32_t leve
     return ghost_io(g, axis, side, level, nullptr, src, bytes);
 }
 
-// Checkpoint image: header, then the integer-time state packed by role -- the
-// field arrays that can be non-zero (the order-0 components in the closure of
-// the injected ones, every order-1 component), phi^{n+1/2}, the second axion
-// level and the outflow ghost planes of levels n+1/2 and n-1/2.  The other
-// order-0 arrays are zero by construction and the cached current J is a
-// function of the stored state, so neither is stored: a load zeroes the first
-// and marks J for recomputation.
+// Checkpoint image: header, then the state packed by role -- the field arrays
+// that can be non-zero (the order-0 components in the closure of the injected
+// ones, every order-1 component), phi^{n+1/2}, the second axion level and the
+// outflow ghost planes of levels n+1/2 and n-1/2.  The other order-0 arrays are
+// zero by construction and the cached current J is a function of the stored
+// state, so neither is stored: a load zeroes the first and marks J for
+// recomputation.  A grid that the single-pass kernels are stepping holds E at
+// n+1/2 (the leapfrog-staggered state); its image keeps that form (flagged in
+// the header), so a save and a load convert nothing and a resumed run is bit
+// for bit the uninterrupted one.  With a soft source the staggered E carries the
+// source's sheet terms, so such a grid saves its integer-time state instead.
 static uint32_t stored_fields(const axp_grid *g)
 {
     const uint32_t c0 = order0_closure(g);
@@ -931,11 +935,12 @@ axp_status axp_save_state(axp_grid *g, void *dst, size_t bytes)
     size_t need;
     if (!g || !dst || axp_state_bytes(g, &need) != AXP_OK || bytes != need) return AXP_E_INVAL;
     if (g->group) return AXP_E_STATE;
-    cudaError_t e = ensure_integer(g);
+    cudaError_t e = g->src_on ? ensure_integer(g) : cudaSuccess;
     if (e != cudaSuccess) return cuda_status(e);
     StateHeader h;
     std::memset(&h, 0, sizeof(h));
     h.magic = kStateMagic;
+    h.staggered = g->staggered ? 1 : 0;
     h.bytes = need;
     h.desc = g->desc;
     for (int a = 0; a < 3; a++) {
@@ -974,6 +979,7 @@ axp_status axp_load_state(axp_grid *g, const void *src, size_t bytes)
     std::memcpy(&h, src, sizeof(h));
     if (h.magic != kStateMagic || h.bytes != bytes || std::memcmp(&h.desc, &g->desc, sizeof(axp_grid_desc)) != 0)
         return AXP_E_INVAL;
+    if (h.staggered && g->src_on) return AXP_E_STATE;  // (its staggered E carries no sheet terms)
     // the image's array set follows from its own record of the injected components
     const uint32_t active_before = g->active;
     g->active = h.active;
@@ -984,7 +990,7 @@ axp_status axp_load_state(axp_grid *g, const void *src, size_t bytes)
     }
     g->cfg_version++;
     cudaError_t e = cudaStreamSynchronize(g->stream);
-    g->staggered = false;
+    g->staggered = h.staggered != 0;
     // arrays outside the image are zero in both field sets (kernels never touch them)
     const size_t arr = (size_t)cells(g->desc) * g->layout.elem;
     for (int set = 0; set < 2 && e == cudaSuccess; set++)

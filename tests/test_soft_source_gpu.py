@@ -185,3 +185,34 @@ def test_injected_pulse_converts_like_the_closed_form():
     want = (g_c * B0 * l / 2) ** 2 / math.cos(theta / 2) ** 2
     assert d["P_g2a"] == pytest.approx(want, rel=0.05)
     g.close()
+
+
+def test_checkpoints_with_a_soft_source_are_taken_at_integer_time():
+    """A grid with a soft source saves its integer-time state (its staggered E
+    carries the sheet terms), which a grid with the same source resumes bit for
+    bit; the staggered image of a grid without a source is refused by a grid
+    that has one."""
+    axp = axp_mod()
+    grid = grid2d(160, 64, "fp64")
+    src = beam(64)
+    a = axp.Grid(grid)
+    a.set_soft_source(src)
+    a.step(20)
+    img = a.save_state()
+    a.step(15)
+    ref = a.fields()
+    b = axp.Grid(grid)
+    b.set_soft_source(src)
+    b.load_state(img)
+    b.step(15)
+    got = b.fields()
+    for k in NAMES:
+        assert np.array_equal(got[k], ref[k]), k
+    plain = axp.Grid(grid)
+    plain.step(5)
+    staggered_img = plain.save_state()
+    with pytest.raises(axp.AxpError) as e:
+        b.load_state(staggered_img)
+    assert e.value.status == axp.AXP_E_STATE
+    for g in (a, b, plain):
+        g.close()
