@@ -96,13 +96,76 @@ __device__ __forceinline__ void pcell_at(const View<T> &v, const PhiPair<T, INCR
     for (int a = 0; a < 3; a++) P.p[a][c] = p_comp<T, INCR>(v, q, a, i, j, k);
 }
 
+// The same three components at a cell of a 2D grid (one cell along z,
+// periodic) whose x and y neighbours all lie inside the grid: every accessor of
+// p_comp then reads the array element itself (a z neighbour is the cell), so
+// the loads are taken directly and the expressions are p_comp's, in its order.
+template <typename T, bool INCR>
+__device__ __forceinline__ void pcell_interior_2d(const View<T> &v, const PhiPair<T, INCR> &q, const PBuf<T> &P,
+                                                  int64_t c)
+{
+    const int64_t sy = v.n[0];
+    auto mid_dt = [&](int64_t x, T *mid, T *dtv) {
+        const T hi = q.hi[x];
+        if (INCR) {
+            const T inc = q.b[x];
+            *mid = hi - T(0.5) * inc;
+            *dtv = inc / v.dt;
+            return;
+        }
+        const T lo = q.b[x];
+        *mid = T(0.5) * (hi + lo);
+        *dtv = (hi - lo) / v.dt;
+    };
+    auto mid_of = [&](int64_t x) {
+        T m, t;
+        mid_dt(x, &m, &t);
+        return m;
+    };
+    T mid, Dt;
+    mid_dt(c, &mid, &Dt);
+    // central differences of phi^n: along z the two neighbours are the cell itself
+    const T dx = over_2d(v, mid_of(c + 1) - mid_of(c - 1), 0);
+    const T dy = over_2d(v, mid_of(c + sy) - mid_of(c - sy), 1);
+    const T dz = over_2d(v, mid - mid, 2);
+    const T *E0x = v.f[kE0], *E0y = v.f[kE0 + 1], *E0z = v.f[kE0 + 2];
+    const T *B0x = v.f[kB0], *B0y = v.f[kB0 + 1], *B0z = v.f[kB0 + 2];
+    const T ex = T(0.5) * (E0x[c] + E0x[c - 1]) + v.Eext[0];
+    const T ey = T(0.5) * (E0y[c] + E0y[c - sy]) + v.Eext[1];
+    const T ez = T(0.5) * (E0z[c] + E0z[c]) + v.Eext[2];
+    T s;
+    s = B0x[c];
+    s = s + B0x[c];
+    s = s + B0x[c - sy];
+    s = s + B0x[c - sy];
+    const T bx = T(0.25) * s + v.Bext[0];
+    s = B0y[c];
+    s = s + B0y[c - 1];
+    s = s + B0y[c];
+    s = s + B0y[c - 1];
+    const T by = T(0.25) * s + v.Bext[1];
+    s = B0z[c];
+    s = s + B0z[c - sy];
+    s = s + B0z[c - 1];
+    s = s + B0z[c - 1 - sy];
+    const T bz = T(0.25) * s + v.Bext[2];
+    // P_a = Dt Bbar_a - (Ebar_b dphi_c - Ebar_c dphi_b), (a, b, c) cyclic
+    P.p[0][c] = Dt * bx - (ey * dz - ez * dy);
+    P.p[1][c] = Dt * by - (ez * dx - ex * dz);
+    P.p[2][c] = Dt * bz - (ex * dy - ey * dx);
+}
+
 template <typename T, bool INCR>
 __global__ void __launch_bounds__(kThreads) k_pcell(View<T> v, PhiPair<T, INCR> q, PBuf<T> P)
 {
+    const bool flat = v.n[2] == 1 && v.periodic[2] && v.n[0] >= 3 && v.n[1] >= 3;
     for (int64_t qv = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; qv < v.Nv; qv += (int64_t)gridDim.x * blockDim.x) {
         int64_t i, j, k;
         const int64_t c = visit(v, qv, &i, &j, &k);
-        pcell_at<T, INCR>(v, q, P, c, i, j, k);
+        if (flat && i >= 1 && i <= v.n[0] - 2 && j >= 1 && j <= v.n[1] - 2)
+            pcell_interior_2d<T, INCR>(v, q, P, c);
+        else
+            pcell_at<T, INCR>(v, q, P, c, i, j, k);
     }
 }
 
