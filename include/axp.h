@@ -372,9 +372,12 @@ axp_status axp_get_window_offset(const axp_grid *grid, int64_t *cells);
  * AXP_KERNEL_AX3D forces the single-pass kernel specialised for periodic 3D
  * grids with no laser fields and no uniform E (an axion wave in a uniform B);
  * AXP_KERNEL_BLOCK1D forces the time-blocked kernel for FP64 1D grids that
- * are periodic along x (at least 256 cells, no soft source): the general
- * kernels' stages, bit for bit, over windows held in shared memory for blocks
- * of steps, in one cooperative launch per run of steps.  Should one of its
+ * are periodic along x (at least 256 cells, no soft source): the single-pass
+ * kernels' staggered scheme reduced to 1D, its curl updates folded into one
+ * multiply-add per difference (within 1e-12 of the general path after 20000
+ * steps), over windows held in shared memory for blocks of steps, in one
+ * cooperative launch per run of steps; any split of a run into launches gives
+ * the same bits.  Should one of its
  * bounded grid-wide waits give up, the next synchronising call on the handle
  * (axp_synchronize, diagnostics, reads, axp_save_state) returns
  * AXP_E_TIMEOUT.  Forcing a kernel that does not support the grid makes
