@@ -241,9 +241,11 @@ bool fused_supported(const axp_grid *g)
 }
 
 // steps per block of the time-blocked 1D kernel (halo tblock + 3 on each side):
-// with 4096 cells over 152 SMs a window of 27 + 2 x 15 cells fills two warps
+// with 4096 cells over 152 SMs a window of 27 + 2 x 17 cells fits one pass of
+// the kernel's 64 cells (T = 10, 12, 14 measured 2.02, 1.98, 1.95 us/step; at
+// 16 the window takes two passes, 3.40)
 #ifndef AXP_LINE_BLOCK
-#define AXP_LINE_BLOCK 12
+#define AXP_LINE_BLOCK 14
 #endif
 constexpr int kLineBlock = AXP_LINE_BLOCK;
 // blocks per SM of the time-blocked 1D kernel (each owns n / (SMs x this) cells)

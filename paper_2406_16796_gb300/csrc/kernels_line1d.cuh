@@ -31,9 +31,15 @@
 namespace axp {
 namespace line1d {
 
-constexpr int kThreads = 64;
-constexpr int kArrays = 23;              // window arrays (listed in k_line1d)
-constexpr int kMaxWindow = 1100;         // cells: kArrays x 1100 x 8 B = 202 KB of shared memory
+// Four warps: each SM sub-partition has its own FP64 unit, which takes about 64
+// cycles per warp instruction, so a warp issues at most a quarter of the SM's
+// FP64 rate.  The window's cells are covered by two warps and each stage's work
+// on a cell is split into two halves of independent outputs: warps 0-1 take one
+// half and warps 2-3 (the other two sub-partitions) the other.
+constexpr int kThreads = 128;
+constexpr int kLanes = 64;               // cells a pass of one half covers
+constexpr int kArrays = 25;              // window arrays (listed in k_line1d)
+constexpr int kMaxWindow = 1100;         // cells: kArrays x 1100 x 8 B = 220 KB of shared memory
 constexpr unsigned kSpinLimit = 1u << 26;        // polls of a grid-wide wait before it gives up ...
 constexpr unsigned long long kWaitNs = 1000000000ull;  // ... or one second, whichever comes first
 
@@ -99,7 +105,7 @@ __global__ void __launch_bounds__(kThreads) k_line1d(Args A)
     const int H = A.halo, W = own + 2 * H, Wm = A.seg + 2 * A.halo;
     const int tid = threadIdx.x, nt = blockDim.x;
     // window arrays: E (6), B (6), phi^{n+1/2}, phi^{n-1/2}, B0^{n+1/2} y z, E0^{n+1} y z,
-    // 2 phi^{n+1}, dt D_t phi^{n+1}, P (3)
+    // 2 phi^{n+1}, dt D_t phi^{n+1}, P (3), Bbar0^{n+1} y z (with B_ext)
     double *E[6], *B[6];
     for (int q = 0; q < 6; q++) {
         E[q] = l1_sm + (size_t)q * Wm;
@@ -110,6 +116,8 @@ __global__ void __launch_bounds__(kThreads) k_line1d(Args A)
     double *Eny = l1_sm + (size_t)16 * Wm, *Enz = l1_sm + (size_t)17 * Wm;
     double *SM = l1_sm + (size_t)18 * Wm, *DF = l1_sm + (size_t)19 * Wm;
     double *Px = l1_sm + (size_t)20 * Wm, *PY = l1_sm + (size_t)21 * Wm, *PZ = l1_sm + (size_t)22 * Wm;
+    double *BY = l1_sm + (size_t)23 * Wm, *BZ = l1_sm + (size_t)24 * Wm;
+    const int half = tid / kLanes, lane = tid % kLanes;  // (a warp-uniform half)
     // values beyond the window's ends: the zero closure
     auto at = [&](const double *a, int w) { return (w >= 0 && w < W) ? a[w] : 0.0; };
     const double Bx = A.Bext[0], By = A.Bext[1], Bz = A.Bext[2];
@@ -132,57 +140,69 @@ __global__ void __launch_bounds__(kThreads) k_line1d(Args A)
         __syncthreads();
         for (int st = 0; st < steps; st++) {
             // 1. B^{n+1/2} and B^{n+1}: (curl E)_y = -D_x E_z, (curl E)_z = D_x E_y (forward)
-            for (int w = tid; w < W; w += nt) {
-                const double d0z = at(E[2], w + 1) - E[2][w], d0y = at(E[1], w + 1) - E[1][w];
-                const double d1z = at(E[5], w + 1) - E[5][w], d1y = at(E[4], w + 1) - E[4][w];
-                const double hy = fma(A.cB, d0z, B[1][w]), hz = fma(-A.cB, d0y, B[2][w]);
-                Bhy[w] = hy;
-                Bhz[w] = hz;
-                B[1][w] = fma(A.cB, d0z, hy);
-                B[2][w] = fma(-A.cB, d0y, hz);
-                B[4][w] = fma(A.c2B, d1z, B[4][w]);
-                B[5][w] = fma(-A.c2B, d1y, B[5][w]);
+            for (int w = lane; w < W; w += kLanes) {
+                if (half == 0) {
+                    const double d0z = at(E[2], w + 1) - E[2][w], d1z = at(E[5], w + 1) - E[5][w];
+                    const double hy = fma(A.cB, d0z, B[1][w]);
+                    Bhy[w] = hy;
+                    B[1][w] = fma(A.cB, d0z, hy);
+                    B[4][w] = fma(A.c2B, d1z, B[4][w]);
+                } else {
+                    const double d0y = at(E[1], w + 1) - E[1][w], d1y = at(E[4], w + 1) - E[4][w];
+                    const double hz = fma(-A.cB, d0y, B[2][w]);
+                    Bhz[w] = hz;
+                    B[2][w] = fma(-A.cB, d0y, hz);
+                    B[5][w] = fma(-A.c2B, d1y, B[5][w]);
+                }
             }
             __syncthreads();
-            // 2. source, phi^{n+3/2}, 2 phi^{n+1}, dt D_t phi^{n+1}, E0^{n+1}
-            for (int w = tid; w < W; w += nt) {
-                const double ex = 0.5 * (E[0][w] + at(E[0], w - 1));
-                const double bx = B[0][w] + Bx;
-                const double by = fma(0.5, Bhy[w] + at(Bhy, w - 1), By);
-                const double bz = fma(0.5, Bhz[w] + at(Bhz, w - 1), Bz);
-                const double S = fma(E[2][w], bz, fma(E[1][w], by, ex * bx));  // S/g
-                const double ph = cur[w];
-                double nw = fma(A.lap_0, ph, -old[w]);
-                nw = fma(A.lap_c, at(cur, w + 1) + at(cur, w - 1), nw);
-                nw = fma(A.dt2g, S, nw);
-                old[w] = nw;  // phi^{n+3/2} over phi^{n-1/2} (read by this cell only)
-                SM[w] = nw + ph;
-                DF[w] = nw - ph;
-                // (curl B0)_y = -D_x B0z, (curl B0)_z = D_x B0y (backward)
-                Eny[w] = fma(-A.cB, B[2][w] - at(B[2], w - 1), E[1][w]);
-                Enz[w] = fma(A.cB, B[1][w] - at(B[1], w - 1), E[2][w]);
+            // 2. source, phi^{n+3/2}, 2 phi^{n+1}, dt D_t phi^{n+1} | E0^{n+1}, Bbar0^{n+1} y z
+            for (int w = lane; w < W; w += kLanes) {
+                if (half == 0) {
+                    const double ex = 0.5 * (E[0][w] + at(E[0], w - 1));
+                    const double bx = B[0][w] + Bx;
+                    const double by = fma(0.5, Bhy[w] + at(Bhy, w - 1), By);
+                    const double bz = fma(0.5, Bhz[w] + at(Bhz, w - 1), Bz);
+                    const double S = fma(E[2][w], bz, fma(E[1][w], by, ex * bx));  // S/g
+                    const double ph = cur[w];
+                    double nw = fma(A.lap_0, ph, -old[w]);
+                    nw = fma(A.lap_c, at(cur, w + 1) + at(cur, w - 1), nw);
+                    nw = fma(A.dt2g, S, nw);
+                    old[w] = nw;  // phi^{n+3/2} over phi^{n-1/2} (read by this cell only)
+                    SM[w] = nw + ph;
+                    DF[w] = nw - ph;
+                } else {
+                    // (curl B0)_y = -D_x B0z, (curl B0)_z = D_x B0y (backward)
+                    Eny[w] = fma(-A.cB, B[2][w] - at(B[2], w - 1), E[1][w]);
+                    Enz[w] = fma(A.cB, B[1][w] - at(B[1], w - 1), E[2][w]);
+                    BY[w] = fma(0.5, B[1][w] + at(B[1], w - 1), By);
+                    BZ[w] = fma(0.5, B[2][w] + at(B[2], w - 1), Bz);
+                }
             }
             __syncthreads();
             // 3. P^{n+1} at the cell centres
-            for (int w = tid; w < W; w += nt) {
+            for (int w = lane; w < W; w += kLanes) {
                 const double Dt = DF[w] * A.inv_dt;
                 const double dphi = (at(SM, w + 1) - at(SM, w - 1)) * A.q4dx;
-                const double bx = B[0][w] + Bx;
-                const double by = fma(0.5, B[1][w] + at(B[1], w - 1), By);
-                const double bz = fma(0.5, B[2][w] + at(B[2], w - 1), Bz);
-                Px[w] = Dt * bx;
-                PY[w] = fma(-Enz[w], dphi, Dt * by);
-                PZ[w] = fma(Eny[w], dphi, Dt * bz);
+                if (half == 0) {
+                    PY[w] = fma(-Enz[w], dphi, Dt * BY[w]);
+                } else {
+                    Px[w] = Dt * (B[0][w] + Bx);
+                    PZ[w] = fma(Eny[w], dphi, Dt * BZ[w]);
+                }
             }
             __syncthreads();
             // 4. J^{n+1}; E1^{n+3/2}; E0^{n+3/2}
-            for (int w = tid; w < W; w += nt) {
-                const double Jx = 0.5 * (Px[w] + at(Px, w + 1));
-                E[3][w] = fma(-A.h2g, Jx, E[3][w]);
-                E[4][w] = fma(-A.c2B, B[5][w] - at(B[5], w - 1), fma(-A.h2g, PY[w], E[4][w]));
-                E[5][w] = fma(A.c2B, B[4][w] - at(B[4], w - 1), fma(-A.h2g, PZ[w], E[5][w]));
-                E[1][w] = fma(2.0, Eny[w], -E[1][w]);
-                E[2][w] = fma(2.0, Enz[w], -E[2][w]);
+            for (int w = lane; w < W; w += kLanes) {
+                if (half == 0) {
+                    const double Jx = 0.5 * (Px[w] + at(Px, w + 1));
+                    E[3][w] = fma(-A.h2g, Jx, E[3][w]);
+                    E[4][w] = fma(-A.c2B, B[5][w] - at(B[5], w - 1), fma(-A.h2g, PY[w], E[4][w]));
+                } else {
+                    E[5][w] = fma(A.c2B, B[4][w] - at(B[4], w - 1), fma(-A.h2g, PZ[w], E[5][w]));
+                    E[1][w] = fma(2.0, Eny[w], -E[1][w]);
+                    E[2][w] = fma(2.0, Enz[w], -E[2][w]);
+                }
             }
             double *t = cur;
             cur = old;
