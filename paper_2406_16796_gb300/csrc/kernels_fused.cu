@@ -241,11 +241,11 @@ bool fused_supported(const axp_grid *g)
 }
 
 // steps per block of the time-blocked 1D kernel (halo tblock + 3 on each side):
-// with 4096 cells over 152 SMs a window of 27 + 2 x 17 cells fits one pass of
-// the kernel's 64 cells (T = 10, 12, 14 measured 2.02, 1.98, 1.95 us/step; at
-// 16 the window takes two passes, 3.40)
+// with 4096 cells over 152 SMs a window of 27 + 2 x 18 cells fits one pass of
+// the kernel's 64 cells (T = 12, 14, 15 measured 1.80, 1.77, 1.76 us/step; from
+// 16 the window takes two passes)
 #ifndef AXP_LINE_BLOCK
-#define AXP_LINE_BLOCK 14
+#define AXP_LINE_BLOCK 15
 #endif
 constexpr int kLineBlock = AXP_LINE_BLOCK;
 // blocks per SM of the time-blocked 1D kernel (each owns n / (SMs x this) cells)

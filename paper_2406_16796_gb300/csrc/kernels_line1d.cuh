@@ -38,8 +38,8 @@ namespace line1d {
 // half and warps 2-3 (the other two sub-partitions) the other.
 constexpr int kThreads = 128;
 constexpr int kLanes = 64;               // cells a pass of one half covers
-constexpr int kArrays = 25;              // window arrays (listed in k_line1d)
-constexpr int kMaxWindow = 1100;         // cells: kArrays x 1100 x 8 B = 220 KB of shared memory
+constexpr int kArrays = 27;              // window arrays (listed in k_line1d)
+constexpr int kMaxWindow = 1000;         // cells: kArrays x 1000 x 8 B = 216 KB of shared memory
 constexpr unsigned kSpinLimit = 1u << 26;        // polls of a grid-wide wait before it gives up ...
 constexpr unsigned long long kWaitNs = 1000000000ull;  // ... or one second, whichever comes first
 
@@ -105,7 +105,9 @@ __global__ void __launch_bounds__(kThreads) k_line1d(Args A)
     const int H = A.halo, W = own + 2 * H, Wm = A.seg + 2 * A.halo;
     const int tid = threadIdx.x, nt = blockDim.x;
     // window arrays: E (6), B (6), phi^{n+1/2}, phi^{n-1/2}, B0^{n+1/2} y z, E0^{n+1} y z,
-    // 2 phi^{n+1}, dt D_t phi^{n+1}, P (3), Bbar0^{n+1} y z (with B_ext)
+    // 2 phi^{n+1}, dt D_t phi^{n+1}, P (3), Bbar0^{n+1} y z (with B_ext), and two values that
+    // stay fixed over a window's steps: E0x and B0x do not change in 1D (no curl along x),
+    // so Bbar0_x = B0x + B_ext,x and the source's term Ebar0_x Bbar0_x are formed once
     double *E[6], *B[6];
     for (int q = 0; q < 6; q++) {
         E[q] = l1_sm + (size_t)q * Wm;
@@ -117,6 +119,7 @@ __global__ void __launch_bounds__(kThreads) k_line1d(Args A)
     double *SM = l1_sm + (size_t)18 * Wm, *DF = l1_sm + (size_t)19 * Wm;
     double *Px = l1_sm + (size_t)20 * Wm, *PY = l1_sm + (size_t)21 * Wm, *PZ = l1_sm + (size_t)22 * Wm;
     double *BY = l1_sm + (size_t)23 * Wm, *BZ = l1_sm + (size_t)24 * Wm;
+    double *BXT = l1_sm + (size_t)25 * Wm, *SX = l1_sm + (size_t)26 * Wm;
     const int half = tid / kLanes, lane = tid % kLanes;  // (a warp-uniform half)
     // values beyond the window's ends: the zero closure
     auto at = [&](const double *a, int w) { return (w >= 0 && w < W) ? a[w] : 0.0; };
@@ -136,6 +139,13 @@ __global__ void __launch_bounds__(kThreads) k_line1d(Args A)
             }
             cur[w] = A.phi[par][0][gi];
             old[w] = A.phi[par][1][gi];
+        }
+        __syncthreads();
+        for (int w = tid; w < W; w += nt) {
+            const double ex = 0.5 * (E[0][w] + at(E[0], w - 1));
+            const double bx = B[0][w] + Bx;
+            BXT[w] = bx;
+            SX[w] = ex * bx;
         }
         __syncthreads();
         for (int st = 0; st < steps; st++) {
@@ -159,11 +169,9 @@ __global__ void __launch_bounds__(kThreads) k_line1d(Args A)
             // 2. source, phi^{n+3/2}, 2 phi^{n+1}, dt D_t phi^{n+1} | E0^{n+1}, Bbar0^{n+1} y z
             for (int w = lane; w < W; w += kLanes) {
                 if (half == 0) {
-                    const double ex = 0.5 * (E[0][w] + at(E[0], w - 1));
-                    const double bx = B[0][w] + Bx;
                     const double by = fma(0.5, Bhy[w] + at(Bhy, w - 1), By);
                     const double bz = fma(0.5, Bhz[w] + at(Bhz, w - 1), Bz);
-                    const double S = fma(E[2][w], bz, fma(E[1][w], by, ex * bx));  // S/g
+                    const double S = fma(E[2][w], bz, fma(E[1][w], by, SX[w]));  // S/g
                     const double ph = cur[w];
                     double nw = fma(A.lap_0, ph, -old[w]);
                     nw = fma(A.lap_c, at(cur, w + 1) + at(cur, w - 1), nw);
@@ -187,7 +195,7 @@ __global__ void __launch_bounds__(kThreads) k_line1d(Args A)
                 if (half == 0) {
                     PY[w] = fma(-Enz[w], dphi, Dt * BY[w]);
                 } else {
-                    Px[w] = Dt * (B[0][w] + Bx);
+                    Px[w] = Dt * BXT[w];
                     PZ[w] = fma(Eny[w], dphi, Dt * BZ[w]);
                 }
             }
