@@ -991,6 +991,7 @@ axp_status axp_load_state(axp_grid *g, const void *src, size_t bytes)
     g->cfg_version++;
     cudaError_t e = cudaStreamSynchronize(g->stream);
     g->staggered = h.staggered != 0;
+    g->half_prev = false;
     // arrays outside the image are zero in both field sets (kernels never touch them)
     const size_t arr = (size_t)cells(g->desc) * g->layout.elem;
     for (int set = 0; set < 2 && e == cudaSuccess; set++)

@@ -161,6 +161,11 @@ struct axp_grid {
     int32_t tm_list_blocks, tm_list_per_block;
     std::vector<int4> tm_items;  // the work lists (host copy)
     bool tm_items_uploaded;      // tm_items are in off_sched
+    // the other field set holds E^{n-1/2} of the present staggered state E^{n+1/2}:
+    // the last change of state was a single-pass step (made at configuration
+    // half_prev_cfg), so E^n follows cell by cell from the two levels
+    bool half_prev;
+    int64_t half_prev_cfg;
 };
 
 namespace axp {

@@ -334,6 +334,7 @@ axp_status axp_group_add(axp_group *G, axp_grid *g, int64_t steps, int32_t *memb
     G->members[m] = axp_group::Member{g, steps, nblk, 1};
     g->group = G;
     g->J_valid = false;
+    g->half_prev = false;
     G->dirty = true;
     *member = m;
     return AXP_OK;
@@ -362,6 +363,10 @@ axp_status axp_group_remove(axp_group *G, int32_t member)
     g->step += done;
     g->launches += done;
     g->J_valid = false;
+    // each group step wrote the other field set from the present one, as a
+    // single-grid step does: after one, that set holds E^{n-1/2}
+    g->half_prev = done >= 1;
+    g->half_prev_cfg = g->cfg_version;
     g->group = nullptr;
     G->members[member] = axp_group::Member{nullptr, 0, 0, 0};
     G->dirty = true;

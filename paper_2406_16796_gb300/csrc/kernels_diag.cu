@@ -141,16 +141,86 @@ cudaError_t diag_compute(axp_grid *g, axp_diag *dev_dst)
     return diag_compute_rows<T>(g, dev_dst, -1, 0, 0);
 }
 
+// E^n from the two E levels a single-pass step leaves (Sec. 2.3): both E
+// half-steps of the step from n-1/2 read the same X = curl B^n - g J^n, so
+// E^n = a E^{n-1/2} + b X and E^{n+1/2} = a E^n + b X, where a, b are the
+// half-step's layer coefficients (a = 1, b = h outside the layers; the smallest
+// a of the axes at a corner).  Hence E^n = (E^{n+1/2} + a E^{n-1/2}) / (1 + a),
+// the mean of the two levels outside the layers.  Written over E^{n-1/2} (the
+// other field set); the active E arrays only (the others are zero in both sets).
+template <typename T>
+struct ELevels {
+    T *lo[6];        // E^{n-1/2}, overwritten with E^n (order 0 xyz, order 1 xyz)
+    const T *hi[6];  // E^{n+1/2}
+    const T *a1[3];  // per axis, the one-half-step layer coefficient a (null: no layer along the axis)
+    unsigned mask;   // arrays to form
+    int64_t n0, n1, n2;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kDiagThreads) k_e_level(ELevels<T> L)
+{
+    const int64_t rows = L.n1 * L.n2;
+    for (int64_t r = blockIdx.y; r < rows; r += gridDim.y) {
+        const int64_t j = r % L.n1, k = r / L.n1;
+        T ayz = T(1);
+        if (L.a1[1] && L.a1[1][j] < ayz) ayz = L.a1[1][j];
+        if (L.a1[2] && L.a1[2][k] < ayz) ayz = L.a1[2][k];
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < L.n0; i += (int64_t)gridDim.x * blockDim.x) {
+            T a = ayz;
+            if (L.a1[0] && L.a1[0][i] < a) a = L.a1[0][i];
+            const int64_t c = i + L.n0 * r;
+#pragma unroll
+            for (int f = 0; f < 6; f++) {
+                if (!(L.mask >> f & 1u)) continue;
+                L.lo[f][c] = a == T(1) ? T(0.5) * (L.hi[f][c] + L.lo[f][c]) : (L.hi[f][c] + a * L.lo[f][c]) / (T(1) + a);
+            }
+        }
+    }
+}
+
+template <typename T>
+cudaError_t e_level_from_halves(axp_grid *g)
+{
+    ELevels<T> L;
+    const Workspace &w = g->layout;
+    const int oset = 1 - g->fset;
+    const int fe[6] = {kE0, kE0 + 1, kE0 + 2, kE1, kE1 + 1, kE1 + 2};
+    L.mask = 0;
+    for (int f = 0; f < 6; f++) {
+        L.lo[f] = (T *)(g->ws + w.off_fields[oset][fe[f]]);
+        L.hi[f] = (const T *)(g->ws + w.off_fields[g->fset][fe[f]]);
+        if (f >= 3 || (g->active >> fe[f] & 1u)) L.mask |= 1u << f;
+    }
+    for (int a = 0; a < 3; a++) {
+        const bool lay = g->desc.em_bc[a][0] != AXP_BC_PERIODIC && g->desc.pml_cells > 0 && g->desc.pml_sigma_max_dt > 0;
+        L.a1[a] = lay ? (const T *)(g->ws + w.off_pml_tab[a]) : nullptr;
+    }
+    L.n0 = g->desc.n[0];
+    L.n1 = g->desc.n[1];
+    L.n2 = g->desc.n[2];
+    const int64_t rows = L.n1 * L.n2;
+    dim3 grid((unsigned)((L.n0 + kDiagThreads - 1) / kDiagThreads), (unsigned)(rows < 65535 ? rows : 65535), 1);
+    if (grid.x > 64) grid.x = 64;
+    k_e_level<T><<<grid, kDiagThreads, 0, g->stream>>>(L);
+    g->launches++;
+    g->half_prev = false;  // the other set now holds E^n
+    return cudaGetLastError();
+}
+
 // The sums over the cells whose index along `axis` lies in [lo, hi) as well as in
 // the physical region (axis < 0: no restriction).  A slab of a decomposed grid
 // sums its owned rows this way; the records' sums add up across slabs.
 template <typename T>
 cudaError_t diag_compute_rows(axp_grid *g, axp_diag *dev_dst, int axis, int64_t lo, int64_t hi)
 {
-    // staggered (fused-path) state: reconstruct E^n into the spare field set first
+    // staggered (fused-path) state: reconstruct E^n into the spare field set first,
+    // from the two levels of the last single-pass step where the other set holds
+    // them, else by the general kernels' inverse half-step
     View<T> v;
     if (g->staggered) {
-        const cudaError_t e = exit_staggered<T>(g, false);
+        const bool halves = g->half_prev && g->half_prev_cfg == g->cfg_version;
+        const cudaError_t e = halves ? e_level_from_halves<T>(g) : exit_staggered<T>(g, false);
         if (e != cudaSuccess) return e;
         v = make_view_eset<T>(g, 1 - g->fset);
     } else {

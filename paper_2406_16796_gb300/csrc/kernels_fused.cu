@@ -282,6 +282,7 @@ cudaError_t block1d_step(axp_grid *g, int64_t nsteps)
     cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
     if (e != cudaSuccess) return e;
     g->coop_used = true;
+    g->half_prev = false;  // (its windows double-buffer both field sets)
     line1d::Args A;
     std::memset(&A, 0, sizeof(A));
     A.n = d.n[0];
@@ -913,6 +914,8 @@ cudaError_t fused_step(axp_grid *g, int64_t nsteps, bool *handled)
             if ((e = cudaGraphLaunch(exec, g->stream)) != cudaSuccess) return e;
             g->launches += kGraphSteps;
             g->step += kGraphSteps;
+            g->half_prev = true;  // the other set holds the last step's E^{n-1/2}
+            g->half_prev_cfg = g->cfg_version;
         }
     }
     for (; it < nsteps; it++) {
@@ -928,6 +931,8 @@ cudaError_t fused_step(axp_grid *g, int64_t nsteps, bool *handled)
         g->launches++;
         rotate_roles(g);
         g->step++;
+        g->half_prev = true;  // the other set holds the last step's E^{n-1/2}
+        g->half_prev_cfg = g->cfg_version;
         if (g->desc.diag_every > 0 && g->step % g->desc.diag_every == 0) {
             axp_diag *dst = ring_slot(g, g->ring_written);
             if ((e = diag_compute<T>(g, dst)) != cudaSuccess) return e;

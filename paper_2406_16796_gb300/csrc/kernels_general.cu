@@ -552,6 +552,7 @@ template <typename T>
 cudaError_t enter_staggered(axp_grid *g)
 {
     if (g->staggered) return cudaSuccess;
+    g->half_prev = false;
     cudaError_t e = general_current<T>(g);
     if (e != cudaSuccess) return e;
     View<T> v = make_view<T>(g);
@@ -567,6 +568,7 @@ template <typename T>
 cudaError_t exit_staggered(axp_grid *g, bool in_place)
 {
     if (!g->staggered) return cudaSuccess;
+    g->half_prev = false;
     const int oset = in_place ? g->fset : 1 - g->fset;
     View<T> vin = make_view<T>(g);
     View<T> vout = make_view_eset<T>(g, oset);
