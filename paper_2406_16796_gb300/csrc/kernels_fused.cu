@@ -452,7 +452,10 @@ double list_cut(const std::vector<int> &ids, double r, int64_t ny, const SpanCos
 // x edge runs the edge body over its layer, and its block waits at each plane's
 // barrier for the layer's warp: next to a block of another strip it takes
 // kEdgeNextToInner plane-times per plane, next to another such block
-// kEdgePair.  So with two blocks per SM the x-edge strips get SMs of their own
+// kEdgePair (block timestamps gave about 1.6; as the model's weight, 1.7 to 1.9
+// ran the 4096 x 2048 pulse in 0.903-0.906 ms/step, 1.6 in 0.958, 1.4 in 1.11
+// and 2.0 in 0.919: a weight at or below the measured ratio leaves the x-edge
+// SMs the last to finish).  So with two blocks per SM the x-edge strips get SMs of their own
 // (both blocks), as many as balance their cost against the other strips'; the
 // number of such SMs is found by bisection (the other strips' cost grows with
 // it, theirs falls).  Returns the costliest SM's cost in plane-times and fills
@@ -461,7 +464,10 @@ double list_cut(const std::vector<int> &ids, double r, int64_t ny, const SpanCos
 double list_schedule(int64_t strips, bool xedge, int64_t ny, const SpanCost &C, int sms, int per_sm, bool forced,
                      std::vector<int4> *items)
 {
-    constexpr double kEdgePair = 1.6, kEdgeNextToInner = 1.82;
+#ifndef AXP_LIST_EDGE_PAIR
+#define AXP_LIST_EDGE_PAIR 1.8
+#endif
+    constexpr double kEdgePair = AXP_LIST_EDGE_PAIR, kEdgeNextToInner = 1.82;
     const int64_t slots = (int64_t)sms * per_sm;
     std::vector<int> inner, edge, all;
     for (int s = 0; s < (int)strips; s++) {
@@ -541,7 +547,9 @@ double list_schedule(int64_t strips, bool xedge, int64_t ny, const SpanCost &C, 
         if (taken[(size_t)p]) continue;
         (p < sms ? first : second).push_back(p);
     }
+#ifndef AXP_LIST_SAME_ORDER
     std::reverse(second.begin(), second.end());
+#endif
     size_t k = 0;
     for (const int64_t p : first)
         if (k < bi.size()) lay[(size_t)p] = bi[k++];
