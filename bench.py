@@ -277,8 +277,8 @@ def bytes_per_cell(prec):
 # one-pass stencil grows with the cells); None until a capture of the kernel as
 # it stands exists.  Sources are summarised under profiles/.
 TRAFFIC = {
-    # k_tm2d_list (FP64, work lists), captured at this size (one-pass metrics): 773.0 + 628.4 MB
-    ("k_tm2d_list (one launch per step)", "fp64"): 1401.4e6,
+    # k_tm2d_list (FP64, work lists), captured at this size (one-pass metrics): 773.5 + 628.6 MB
+    ("k_tm2d_list (one launch per step)", "fp64"): 1402.0e6,
     # k_tm2d (FP64, uniform grid), 2048 x 2048 capture: 689.2 MB per launch
     ("k_tm2d (one launch per step)", "fp64"): 689.2e6 * (4096 * 2048) / (2048 * 2048),
     # k_tm2d_x2 (FP32 split, two columns per thread), 2048 x 2048 capture: 345.0 MB per launch
@@ -303,10 +303,10 @@ def load_peaks():
 FP64_PIPE_WARP_INST_PER_CYCLE_PER_SM = 1.0 / 16.0
 # FP64-pipe warp instructions the 2D kernel executes per cell-update, by launch
 # form (ncu, sm__inst_executed_pipe_fp64.sum over one launch): on work lists
-# 13,972,295 on the 4096 x 2048 pulse grid itself (53.3 thread-operation slots
+# 13,976,291 on the 4096 x 2048 pulse grid itself (53.3 thread-operation slots
 # per cell); on the uniform grid 7,468,742 on the 2048 x 2048 grid (57.0; per
 # cell about the same at 4096 x 2048, to the share of halo columns and layer cells)
-FP64_PIPE_WARP_INST_PER_CELL = {"k_tm2d_list (one launch per step)": 13972295 / 8388608,
+FP64_PIPE_WARP_INST_PER_CELL = {"k_tm2d_list (one launch per step)": 13976291 / 8388608,
                                 "k_tm2d (one launch per step)": 7468742 / 4194304}
 
 
