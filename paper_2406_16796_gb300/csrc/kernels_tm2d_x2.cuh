@@ -75,6 +75,11 @@ __device__ __forceinline__ void tile(const fused::Params<float> &P, const int bx
     const int gx0 = bx * vx - HL;
     const int wx0 = gx0 + 2 * (tx & ~31), wx1 = wx0 + 63;  // columns of this warp
     const bool tile_fast = perx || (wx0 - 1 >= P.lay[0][0] && wx1 + 1 <= nx - 1 - P.lay[0][1]);
+    // A warp whose columns all lie beyond the last column of a non-periodic grid
+    // would compute the closure's zeros (the edge body sets every value it keeps or
+    // publishes to zero outside the grid): it keeps the zeros of its registers and
+    // of the zeroed rows instead, meeting every barrier with the other warps.
+    const bool dead = !perx && wx0 >= nx;
     const int ylo = P.lay[1][0], yhi = ny - 1 - P.lay[1][1];
 
     const float h = P.h, g = P.g, idx = P.idx[0], idy = P.idx[1], hidx = P.hidx[0], hidy = P.hidx[1];
@@ -330,17 +335,18 @@ __device__ __forceinline__ void tile(const fused::Params<float> &P, const int bx
 
     for (int p = t0 - 4; p < t0; p++) fill_y(p);
     for (int j = 0; j < NS - 1; j++) {
-        if (t0 + j <= t1) prefetch(t0 + j);
+        if (!dead && t0 + j <= t1) prefetch(t0 + j);
         tm2d::cp_commit();
     }
     tm2d::cp_wait<NS - 2>();
-    take(t0);
+    if (!dead) take(t0);
     __syncthreads();
 #pragma unroll 2
     for (int t = t0; t <= t1; ++t) {
-        if (t + NS - 1 <= t1) prefetch(t + NS - 1);
+        if (!dead && t + NS - 1 <= t1) prefetch(t + NS - 1);
         tm2d::cp_commit();
         const int b = (t - t0) & 1;
+        if (!dead) {
         rows[b][R_E0Z][tx + 1] = E0z1;
         rows[b][R_E1Y][tx + 1] = E1y1;
         rows[b][R_E1Z][tx + 1] = E1z1;
@@ -352,10 +358,15 @@ __device__ __forceinline__ void tile(const fused::Params<float> &P, const int bx
         rows[b][R_N1Z4][tx + 1] = N1z4;
         rows[b][R_N1Y4][tx + 1] = N1y4;
         rows[b][R_N0Y4][tx + 1] = N0y4;
+        }
         __syncthreads();
         const bool fast = tile_fast && (pery || (t - 6 >= ylo && t + 1 <= yhi));
-        if (fast) body(std::false_type{}, t, b);
-        else body(std::true_type{}, t, b);
+        if (dead) {
+        } else if (fast) {
+            body(std::false_type{}, t, b);
+        } else {
+            body(std::true_type{}, t, b);
+        }
         E0z4 = E0z3; E0z3 = E0z2; E0z2 = E0z1; E0z1 = E0z0;
         E1x4 = E1x3; E1x3 = E1x2; E1x2 = E1x1; E1x1 = E1x0;
         E1y4 = E1y3; E1y3 = E1y2; E1y2 = E1y1; E1y1 = E1y0;
@@ -370,7 +381,7 @@ __device__ __forceinline__ void tile(const fused::Params<float> &P, const int bx
         SM4 = SM3; SM3 = SM2; DF4 = DF3; DF3 = DF2; EN4 = EN3; EN3 = EN2;
         PX4 = PX3; PY4 = PY3;
         tm2d::cp_wait<NS - 2>();
-        if (t < t1) take(t + 1);
+        if (!dead && t < t1) take(t + 1);
     }
     tm2d::cp_wait<0>();
 }
