@@ -281,8 +281,9 @@ TRAFFIC = {
     ("k_tm2d_list (one launch per step)", "fp64"): 1402.0e6,
     # k_tm2d (FP64, uniform grid), 2048 x 2048 capture: 689.2 MB per launch
     ("k_tm2d (one launch per step)", "fp64"): 689.2e6 * (4096 * 2048) / (2048 * 2048),
-    # k_tm2d_x2 (FP32 split, two columns per thread), 2048 x 2048 capture: 345.0 MB per launch
-    ("k_tm2d_x2 (one launch per step)", "fp32"): 345.0e6 * (4096 * 2048) / (2048 * 2048),
+    # k_tm2d_x2 (FP32 split, two columns per thread), captured at this size (one-pass
+    # metrics): 395.6 + 322.0 MB per launch
+    ("k_tm2d_x2 (one launch per step)", "fp32"): 717.5e6,
 }
 # k_ax3d_x2 (3D, no order-0 fields, two x cells per thread), 256^3 capture: 1064.9 MB per launch
 TRAFFIC_3D_PER_CELL = 1064.9e6 / 256 ** 3
