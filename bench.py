@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-bc", action="store_true")
     ap.add_argument("--no-window", action="store_true")
+    ap.add_argument("--no-group", action="store_true")
+    ap.add_argument("--group-members", type=int, default=40,
+                    help="2D requests of the seeded serving stream in the group measurement")
     ap.add_argument("--scan-tiling", default=None,
                     help="block_steps,segment_cells,threads for the scan instead of the autotuner's choice")
     ap.add_argument("--serve-requests", type=int, default=1000)
@@ -434,6 +437,49 @@ def fp64_sequential_sample(reqs, served, sample=8, seed=20240628):
             "max_rel_err_P_served_vs_fp64": max(errs) if errs else None}
 
 
+# k_tm2d_group on the first 40 2D requests of the seeded stream (21,932,100 cells),
+# one-pass ncu capture of one launch: 1054.2 + 919.8 MB
+TRAFFIC_GROUP40 = 1974.2e6
+
+
+def group_measurement(members, steps, hbm_peak, hbm_src):
+    """The serving path's 2D kernel alone: the first `members` 2D requests of the
+    seeded stream (FP32 split, beam set-up) admitted into one group and advanced
+    together, one persistent launch per step, timed with CUDA events on the
+    group's stream."""
+    import torch
+    from paper_2406_16796_gb300 import axp, group as G, workloads as W
+
+    reqs = [r for r in W.serve_requests(count=20 * members) if r.ndim == 2][:members]
+    grp = G.Group(max(64, members), 65536)
+    grids, cells = [], 0
+    for r in reqs:
+        w = W.request_workload(r, precision="fp32")
+        g = axp.Grid(w.grid)
+        g.inject_laser(w.lasers[0])
+        grp.add(g, 10 ** 6)
+        grids.append(g)
+        cells += w.grid.cells
+    grp.run(5)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(grp.stream)
+    grp.run(steps)
+    e1.record(grp.stream)
+    e1.synchronize()
+    per = e0.elapsed_time(e1) / 1e3 / steps
+    ach = bytes_per_cell("fp32") * cells / per / 1e9
+    out = {"workload": "serve_2d_group_%d" % len(grids), "members": len(grids), "cells": cells, "steps": steps,
+           "ms_per_step": per * 1e3, "value": cells / per, "unit": "cell-updates/s", "kernel": "k_tm2d_group",
+           "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+                        "peak_source": hbm_src, "algorithmic_bytes_per_cell": bytes_per_cell("fp32"),
+                        "traffic": TRAFFIC_GROUP40 if len(grids) == 40 else None}}
+    grp.close()
+    for g in grids:
+        g.close()
+    return out
+
+
 def serve_measurement(count, rank, world, open_count=200):
     """The serving loop on the first `count` requests of the seeded stream (80%
     1D Nx log-uniform in [1024, 65536], 20% 2D Nx log-uniform in [256, 2048]
@@ -732,6 +778,9 @@ def gpu_arm(args):
     srv = None
     if not args.no_serve:
         srv = serve_measurement(args.serve_requests, rank, world, open_count=args.serve_open_requests)
+    grp = None
+    if not args.no_group:
+        grp = group_measurement(args.group_members, 50, hbm_peak, hbm_src)
     bcm = None
     if not args.no_bc and rank == 0:
         bcm = boundary_measurement()
@@ -766,6 +815,8 @@ def gpu_arm(args):
         line["scan"] = scan
     if srv:
         line["serve"] = srv
+    if grp:
+        line["serve_2d_group"] = grp
     if ax3:
         line["axion_3d"] = ax3
     if bcm:
