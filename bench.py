@@ -288,8 +288,9 @@ TRAFFIC = {
     # metrics): 395.6 + 322.0 MB per launch
     ("k_tm2d_x2 (one launch per step)", "fp32"): 717.5e6,
 }
-# k_ax3d_x2 (3D, no order-0 fields, two x cells per thread), 256^3 capture: 1064.9 MB per launch
-TRAFFIC_3D_PER_CELL = 1064.9e6 / 256 ** 3
+# k_ax3d_x2 (3D, no order-0 fields, two x cells per thread, evict-first stores),
+# 256^3 capture (one-pass metrics): 574.7 + 488.5 MB per launch
+TRAFFIC_3D_PER_CELL = 1063.2e6 / 256 ** 3
 
 
 def load_peaks():

@@ -311,7 +311,9 @@ __global__ void __launch_bounds__(x2::NT, 1) k_ax3d_x2(fused::Params<T> P)
         ph0 = st[6 * NT];
         pb0 = st[7 * NT];
     };
-    auto store = [](float *base, int64_t gi, float2 v) { *reinterpret_cast<float2 *>(base + gi) = v; };
+    // the new state is read again only in the next step, after the whole box has
+    // streamed through L2: stores are marked evict-first
+    auto store = [](float *base, int64_t gi, float2 v) { __stcs(reinterpret_cast<float2 *>(base + gi), v); };
     const int me = (ty + 1) * PXP + (tx + 1);
     const unsigned all = 0xffffffffu;
     // the pair one cell along +x / -x: (own.y, next pair's x) and (previous pair's y, own.x)
