@@ -20,6 +20,7 @@ from paper_2406_16796_gb300.workloads import BC_CODE, FIELD_NAMES, AxionSpec, Gr
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "axp_oracle.c")
+PSRC = os.path.join(HERE, "axp_oracle_particles.c")
 LIB = os.path.join(HERE, "liborc.so")
 _lock = threading.Lock()
 _lib = None
@@ -29,10 +30,10 @@ def build(force=False) -> str:
     """Compile liborc.so with gcc (-O2 -ffp-contract=off, OpenMP when available)."""
     with _lock:
         hdr = os.path.join(HERE, "axp_oracle.h")
-        fresh = os.path.exists(LIB) and os.path.getmtime(LIB) >= max(os.path.getmtime(SRC), os.path.getmtime(hdr))
+        fresh = os.path.exists(LIB) and os.path.getmtime(LIB) >= max(os.path.getmtime(f) for f in (SRC, PSRC, hdr))
         if fresh and not force:
             return LIB
-        base = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-std=c11", SRC, "-o",
+        base = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-std=c11", SRC, PSRC, "-o",
                 LIB + ".tmp", "-lm"]
         try:
             subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
@@ -74,6 +75,11 @@ class _Source(C.Structure):
                 ("plane", C.c_int64)]
 
 
+class _Particles(C.Structure):
+    _fields_ = [("count", C.c_int64), ("q", C.c_double), ("m", C.c_double), ("w", _DP), ("x0", _DP * 3),
+                ("u0", _DP * 3), ("x1", _DP * 3), ("u1", _DP * 3), ("j0", _DP * 3), ("j1", _DP * 3)]
+
+
 class _Diag(C.Structure):
     _fields_ = [(n, C.c_double) for n in ("t", "H_phi", "H_g0", "H_g1", "P_g2a", "P_a2g", "W", "sum_xB1z2",
                                           "sum_B1z2", "gauss_l2")]
@@ -96,6 +102,15 @@ def lib():
         L.orc_sigma_cell.argtypes = [C.POINTER(_Params), C.c_int64, C.c_int64, C.c_int64, C.c_int]
         L.orc_sigma_cell.restype = C.c_double
         L.orc_outflow_solve.argtypes = [C.c_double] * 7 + [_DP, _DP]
+        PP = C.POINTER(_Particles)
+        L.orc_particles_validate.argtypes = [C.POINTER(_Params), PP]
+        L.orc_particles_start.argtypes = [C.POINTER(_Params), PP]
+        L.orc_particles_positions_now.argtypes = [C.POINTER(_Params), PP, _DP * 3, _DP * 3]
+        L.orc_gather.argtypes = [C.POINTER(_Params), C.POINTER(_State), _DP, _DP, _DP, _DP, _DP, _DP]
+        L.orc_kick.argtypes = [C.c_double, C.c_double] + [_DP] * 8
+        L.orc_deposit.argtypes = [C.POINTER(_Params), C.c_double, _DP, _DP, _DP, _DP, _DP * 3, _DP * 3]
+        L.orc_push.argtypes = [C.POINTER(_Params), C.POINTER(_State), PP]
+        L.orc_step_plasma.argtypes = [C.POINTER(_Params), C.POINTER(_State), C.POINTER(_Source), PP, C.c_int64]
         _lib = L
     return _lib
 
@@ -149,6 +164,7 @@ class OracleGrid:
                     self.ghost[a][s] = [np.zeros(plane_shape(grid, a)), np.zeros(plane_shape(grid, a))]
         self.step_count = 0
         self.src = None  # soft source (_Source) or None
+        self.parts = None  # macroparticles (dict of arrays) or None
 
     # -- state marshalling --
     def _state(self) -> _State:
@@ -187,8 +203,67 @@ class OracleGrid:
     def step(self, n: int = 1):
         st = self._state()
         src = C.byref(self.src) if self.src is not None else None
-        lib().orc_step_src(C.byref(self.p), C.byref(st), src, int(n))
+        if self.parts is None:
+            lib().orc_step_src(C.byref(self.p), C.byref(st), src, int(n))
+        else:
+            pc = self._parts_struct()
+            lib().orc_step_plasma(C.byref(self.p), C.byref(st), src, C.byref(pc), int(n))
         self.step_count = st.step
+
+    # -- perturbed-particle current (Sec. 2.2) --
+    def attach_particles(self, q, m, w, x0, u0, x1=None, u1=None):
+        """One species of macroparticles: weights w (count,), positions x0, x1 and
+        momenta u0, u1 (3, count) at the present integer time.  Deposits j^n and
+        moves the positions to the next half-integer time."""
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        n = w.shape[0]
+        z = np.zeros((3, n))
+        cells = self.phi_cur.shape
+        self.parts = {"q": float(q), "m": float(m), "w": w.copy(),
+                      "x0": np.array(x0, dtype=np.float64).reshape(3, n).copy(),
+                      "u0": np.array(u0, dtype=np.float64).reshape(3, n).copy(),
+                      "x1": (z.copy() if x1 is None else np.array(x1, dtype=np.float64).reshape(3, n).copy()),
+                      "u1": (z.copy() if u1 is None else np.array(u1, dtype=np.float64).reshape(3, n).copy()),
+                      "j0": np.zeros((3,) + cells), "j1": np.zeros((3,) + cells)}
+        pc = self._parts_struct()
+        if lib().orc_particles_validate(C.byref(self.p), C.byref(pc)):
+            self.parts = None
+            raise ValueError("particles need a positive mass and periodic E/B along every active axis")
+        lib().orc_particles_start(C.byref(self.p), C.byref(pc))
+
+    def _parts_struct(self) -> _Particles:
+        P = self.parts
+        for k in ("x0", "u0", "x1", "u1", "j0", "j1"):
+            assert P[k].flags.c_contiguous
+        return _Particles(P["w"].shape[0], P["q"], P["m"], _ptr(P["w"]),
+                          *[(_DP * 3)(*[_ptr(P[k][a]) for a in range(3)]) for k in ("x0", "u0", "x1", "u1", "j0",
+                                                                                    "j1")])
+
+    def particles_now(self) -> dict:
+        """Positions at the present integer time, momenta, and the currents j^n."""
+        P = self.parts
+        n = P["w"].shape[0]
+        x0n, x1n = np.zeros((3, n)), np.zeros((3, n))
+        pc = self._parts_struct()
+        lib().orc_particles_positions_now(C.byref(self.p), C.byref(pc), (_DP * 3)(*[_ptr(x0n[a]) for a in range(3)]),
+                                          (_DP * 3)(*[_ptr(x1n[a]) for a in range(3)]))
+        return {"x0": x0n, "x1": x1n, "u0": P["u0"].copy(), "u1": P["u1"].copy(), "j0": P["j0"].copy(),
+                "j1": P["j1"].copy(), "x0_half": P["x0"].copy(), "x1_half": P["x1"].copy()}
+
+    def gather(self, x0, x1):
+        """Fields felt at x0 (+ x1) from the present arrays: (E_nop, B_nop, E_p, B_p)."""
+        out = [np.zeros(3) for _ in range(4)]
+        st = self._state()
+        lib().orc_gather(C.byref(self.p), C.byref(st), _ptr(np.array(x0, dtype=np.float64)),
+                         _ptr(np.array(x1, dtype=np.float64)), *[_ptr(o) for o in out])
+        return tuple(out)
+
+    def deposit(self, qw, x0, x1, u0, u1):
+        """Current of one particle alone: (j0, j1), each (3, nz, ny, nx)."""
+        j0, j1 = np.zeros((3,) + self.phi_cur.shape), np.zeros((3,) + self.phi_cur.shape)
+        lib().orc_deposit(C.byref(self.p), float(qw), *[_ptr(np.array(v, dtype=np.float64)) for v in (x0, x1, u0, u1)],
+                          (_DP * 3)(*[_ptr(j0[a]) for a in range(3)]), (_DP * 3)(*[_ptr(j1[a]) for a in range(3)]))
+        return j0, j1
 
     def set_soft_source(self, S: SourceSpec | None):
         """Laser entering through an x-plane for the following steps (None: off)."""
@@ -247,6 +322,14 @@ class OracleGrid:
         out["phi_cur"] = self.phi_cur.copy()
         out["phi_old"] = self.phi_old.copy()
         return out
+
+
+def kick(q_over_m, dt, u0, u1, Enop, Bnop, Ep, Bp):
+    """One Boris momentum update of order 0 and its first-order part: (u0', u1')."""
+    o0, o1 = np.zeros(3), np.zeros(3)
+    lib().orc_kick(float(q_over_m), float(dt), *[_ptr(np.array(v, dtype=np.float64)) for v in
+                                                 (u0, u1, Enop, Bnop, Ep, Bp)], _ptr(o0), _ptr(o1))
+    return o0, o1
 
 
 def outflow_solve(dt, dxa, m, g_cur, g_old, p0_cur, S_g):

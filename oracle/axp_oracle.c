@@ -373,8 +373,10 @@ static double src_b_term(const orc_params *p, const orc_source *q, int a, int64_
     return src_weight(p, q, 1, j, k) * tau;
 }
 
+/* jp: the particle current of this order (NULL without particles), Ampere's law
+ * curl B = dE/dt + j (natural units) */
 static void e_half(const orc_params *p, double *E[3], double *const B[3], double *const J[3], double coef_g,
-                   const orc_source *src, double t)
+                   const orc_source *src, double t, double *const jp[3])
 {
     const double h = p->dt / 2.0;
     for (int a = 0; a < 3; a++) {
@@ -383,6 +385,7 @@ static void e_half(const orc_params *p, double *E[3], double *const B[3], double
             CELL_IJK(c);
             double X = curlB(p, B, a, i, j, k);
             if (J) X = X - coef_g * J[a][c];
+            if (jp) X = X - jp[a][c];
             if (src && i == src->plane) X = X + src_e_term(p, src, a, i, j, k, t);
             E[a][c] = half_update(E[a][c], X, orc_sigma_cell(p, i, j, k, 0), h);
         }
@@ -420,9 +423,25 @@ void orc_outflow_solve(double dt, double dxa, double m, double g_cur, double g_o
     *U_out = U;
 }
 
-void orc_step(const orc_params *p, orc_state *s, int64_t nsteps) { orc_step_src(p, s, NULL, nsteps); }
+static void step_impl(const orc_params *p, orc_state *s, const orc_source *src, orc_particles *P, int64_t nsteps);
+
+void orc_step(const orc_params *p, orc_state *s, int64_t nsteps) { step_impl(p, s, NULL, NULL, nsteps); }
 
 void orc_step_src(const orc_params *p, orc_state *s, const orc_source *src, int64_t nsteps)
+{
+    step_impl(p, s, src, NULL, nsteps);
+}
+
+void orc_step_plasma(const orc_params *p, orc_state *s, const orc_source *src, orc_particles *P, int64_t nsteps)
+{
+    if (P && orc_particles_validate(p, P)) die("invalid particles");
+    step_impl(p, s, src, P, nsteps);
+}
+
+/* Sec. 2.3 time scheme; with particles, Sec. 2.3's step order puts the particle
+ * push between the axion update and the second field half-steps, and the
+ * current j^n (j^{n+1}) enters the first (second) E half-steps of its order. */
+static void step_impl(const orc_params *p, orc_state *s, const orc_source *src, orc_particles *P, int64_t nsteps)
 {
     if (orc_validate(p)) die("invalid parameters");
     if (src && (src->plane < 1 || src->plane > p->n[0] - 1 || src->pol[0] != 0.0)) die("invalid soft source");
@@ -455,8 +474,8 @@ void orc_step_src(const orc_params *p, orc_state *s, const orc_source *src, int6
         const double t_n1 = (double)(s->step + 1) * dt;
 
         /* 2.-5. first half-steps, order 0 before order 1 (Eq. update_E and the B1 half-step) */
-        e_half(p, s->E0, s->B0, NULL, 0.0, src, t_n);
-        e_half(p, s->E1, s->B1, J, p->g, NULL, 0.0);
+        e_half(p, s->E0, s->B0, NULL, 0.0, src, t_n, P ? P->j0 : NULL);
+        e_half(p, s->E1, s->B1, J, p->g, NULL, 0.0, P ? P->j1 : NULL);
         b_half(p, s->B0, s->E0, src, t_h);
         b_half(p, s->B1, s->E1, NULL, 0.0);
 
@@ -504,15 +523,18 @@ void orc_step_src(const orc_params *p, orc_state *s, const orc_source *src, int6
                     }
             }
 
+        /* particles pushed by the fields of both orders at t_{n+1/2}; j^{n+1} */
+        if (P) orc_push(p, s, P);
+
         /* 10.-12. second half-steps of B (both orders) and of E0 */
         b_half(p, s->B0, s->E0, src, t_h);
         b_half(p, s->B1, s->E1, NULL, 0.0);
-        e_half(p, s->E0, s->B0, NULL, 0.0, src, t_n1);
+        e_half(p, s->E0, s->B0, NULL, 0.0, src, t_n1, P ? P->j0 : NULL);
 
         /* 13.-14. J^{n+1} from phi^{n+3/2}, phi^{n+1/2}, E0^{n+1}, B0^{n+1}; second E1 half-step */
         phi_pair qn1 = make_pair(phi_new, s->phi_cur, Gnew, Gcur);
         current_into(p, &qn1, s->E0, s->B0, J);
-        e_half(p, s->E1, s->B1, J, p->g, NULL, 0.0);
+        e_half(p, s->E1, s->B1, J, p->g, NULL, 0.0, P ? P->j1 : NULL);
 
         /* 17. rotate the axion levels: old <- cur, cur <- new (copies keep the caller's buffers) */
         memcpy(s->phi_old, s->phi_cur, sizeof(double) * N);

@@ -109,6 +109,24 @@ typedef struct {
     int64_t plane;       /* first cell on the +x side of the sheet, 1 <= plane <= n[0]-1 */
 } orc_source;
 
+/* Macroparticles of one species for the perturbed-particle current of Sec. 2.2
+ * (FPS: p = p0 + p1, v = v0 + v1, j = j0 + j1).  Natural units (c = 1):
+ * u = gamma v is the normalised momentum, du/dt = (q/m)(E + v x B).
+ * Time levels inside a run: positions x0, x1 at t_{n+1/2}, momenta u0, u1 at
+ * t_n, currents j0, j1 at t_n on the E_a positions (arrays of the grid's
+ * layout).  orc_particles_start takes positions at t_n and moves them to
+ * t_{n+1/2}; orc_particles_positions_now gives them back at t_n.
+ * Every active axis (n > 1) must be periodic for E and B; positions wrap into
+ * [lo, lo + n d) along active axes, x1 (a displacement) does not wrap. */
+typedef struct {
+    int64_t count;
+    double q, m;            /* charge and mass of the species */
+    double *w;              /* physical particles per macroparticle */
+    double *x0[3], *u0[3];  /* order 0 */
+    double *x1[3], *u1[3];  /* order 1 */
+    double *j0[3], *j1[3];  /* current densities, ncells each */
+} orc_particles;
+
 int orc_validate(const orc_params *p);
 void orc_step(const orc_params *p, orc_state *s, int64_t nsteps);
 /* orc_step with a soft source (src may be NULL) */
@@ -122,6 +140,28 @@ void orc_inject_axion(const orc_params *p, orc_state *s, const orc_axion *A);
 double orc_sigma_cell(const orc_params *p, int64_t i, int64_t j, int64_t k, int axion);
 void orc_outflow_solve(double dt, double dxa, double m, double g_cur, double g_old,
                        double p0_cur, double S_g, double *V_out, double *U_out);
+
+/* ---- perturbed-particle current (axp_oracle_particles.c) ---- */
+int orc_particles_validate(const orc_params *p, const orc_particles *P);
+/* positions given at t_n: deposit j0^n, j1^n, then move the positions to t_{n+1/2} */
+void orc_particles_start(const orc_params *p, orc_particles *P);
+/* positions at t_n of the present state (x0n, x1n: count doubles per axis) */
+void orc_particles_positions_now(const orc_params *p, const orc_particles *P, double *x0n[3], double *x1n[3]);
+/* fields felt by a particle at x0 (+ x1), from the state's present arrays:
+ * F_nop = sum S F0 (+ background), F_p = sum (dS/dx . x1) F0 + sum S F1 */
+void orc_gather(const orc_params *p, const orc_state *s, const double x0[3], const double x1[3], double Enop[3],
+                double Bnop[3], double Ep[3], double Bp[3]);
+/* one momentum update of both orders (Boris rotation and its first-order part) */
+void orc_kick(double q_over_m, double dt, const double u0[3], const double u1[3], const double Enop[3],
+              const double Bnop[3], const double Ep[3], const double Bp[3], double u0_out[3], double u1_out[3]);
+/* adds one particle's current at positions x0 (+ x1) with momenta u0, u1 */
+void orc_deposit(const orc_params *p, double qw, const double x0[3], const double x1[3], const double u0[3],
+                 const double u1[3], double *j0[3], double *j1[3]);
+/* the particle step between the field half-steps: kick with the present fields
+ * (t_{n+1/2}), drift, deposit j^{n+1} */
+void orc_push(const orc_params *p, const orc_state *s, orc_particles *P);
+/* orc_step_src with particles (src may be NULL) */
+void orc_step_plasma(const orc_params *p, orc_state *s, const orc_source *src, orc_particles *P, int64_t nsteps);
 
 #ifdef __cplusplus
 }
