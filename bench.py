@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-bc", action="store_true")
     ap.add_argument("--no-window", action="store_true")
     ap.add_argument("--no-group", action="store_true")
+    ap.add_argument("--no-plasma", action="store_true",
+                    help="leave out the magnetised-plasma (perturbed-particle current) measurement")
     ap.add_argument("--group-members", type=int, default=40,
                     help="2D requests of the seeded serving stream in the group measurement")
     ap.add_argument("--scan-tiling", default=None,
@@ -481,6 +483,42 @@ def group_measurement(members, steps, hbm_peak, hbm_src):
     return out
 
 
+# one push of a macroparticle reads its weight, positions and momenta of both
+# orders (13 doubles) and writes the positions and momenta back (12 doubles)
+BYTES_PER_PARTICLE = (13 + 12) * 8
+
+
+def plasma_measurement(steps, warmup, hbm_peak, hbm_src, world):
+    """Weak laser in a magnetised plasma (perturbed-particle current): 12000 x
+    100 cells, 4 electrons per cell (4.8M), the laser in the first-order fields;
+    FP64, one grid per GPU.  Each step is the general field kernels plus one
+    particle push that gathers, kicks, drifts and deposits both orders."""
+    import torch
+
+    from paper_2406_16796_gb300 import axp, workloads as W
+
+    grid, plasma, fields = W.magnetised_plasma_2d()
+    g = axp.Grid(grid)
+    for k, v in fields.items():
+        g.write(k, v)
+    g.attach_particles(plasma.q, plasma.m, plasma.w, plasma.x0, plasma.u0, plasma.x1, plasma.u1)
+    el, launches = timed_run(g, steps, warmup, g.stream)
+    per = el / steps
+    ach = BYTES_PER_PARTICLE * plasma.count / per / 1e9
+    out = {"workload": "magnetised_plasma_2d_%dx%d_ppc4" % (grid.n[0], grid.n[1]), "cells": grid.cells,
+           "particles": plasma.count, "precision": "fp64", "steps": steps, "ms_per_step": per * 1e3,
+           "value": plasma.count * steps * world / el, "unit": "particle-steps/s",
+           "cell_updates_per_s": grid.cells * steps * world / el, "gpu_launches": launches,
+           "kernel": "k_particles_push and the general field kernels",
+           "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+                        "peak_source": hbm_src, "algorithmic_bytes_per_particle": BYTES_PER_PARTICLE,
+                        "what": "the particle arrays only, over the whole step (the field passes, gathers and "
+                                "the current deposit come on top)", "traffic": None}}
+    g.close()
+    torch.cuda.synchronize()
+    return out
+
+
 def serve_measurement(count, rank, world, open_count=200):
     """The serving loop on the first `count` requests of the seeded stream (80%
     1D Nx log-uniform in [1024, 65536], 20% 2D Nx log-uniform in [256, 2048]
@@ -779,6 +817,9 @@ def gpu_arm(args):
     srv = None
     if not args.no_serve:
         srv = serve_measurement(args.serve_requests, rank, world, open_count=args.serve_open_requests)
+    plasma = None
+    if not args.no_plasma:
+        plasma = plasma_measurement(20, 3, hbm_peak, hbm_src, world)
     grp = None
     if not args.no_group:
         grp = group_measurement(args.group_members, 50, hbm_peak, hbm_src)
@@ -818,6 +859,8 @@ def gpu_arm(args):
         line["serve"] = srv
     if grp:
         line["serve_2d_group"] = grp
+    if plasma:
+        line["magnetised_plasma"] = plasma
     if ax3:
         line["axion_3d"] = ax3
     if bcm:

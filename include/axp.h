@@ -268,6 +268,52 @@ axp_status axp_diagnostics_noalloc(const axp_grid_desc *desc, const double *cons
 axp_status axp_read_field(axp_grid *grid, int32_t which, double *host_dst, size_t bytes);
 axp_status axp_write_field(axp_grid *grid, int32_t which, const double *host_src, size_t bytes);
 
+/* Macroparticles and the perturbed-particle current of Sec. 2.2 (FPS: the
+ * particle momentum, velocity and current split into an order-0 part and its
+ * first-order perturbation, j = j0 + j1).  One species per grid, FP64 grids
+ * only, every active axis (n > 1) periodic for E and B.  Natural units
+ * (c = 1): u = gamma v is the normalised momentum, du/dt = (q/m)(E + v x B);
+ * a macroparticle of weight w stands for w physical particles in the cell
+ * volume dV = d0 d1 d2.
+ *
+ * Each step (Sec. 2.3 step order) pushes the particles between the axion
+ * update and the second field half-steps, with the fields of both orders at
+ * t_{n+1/2} felt at x0 + x1 (Sec. 2.2: F_nop = sum S(r - x0) F0 plus the
+ * uniform background, F_p = sum (dS/dx . x1) F0 + sum S F1), the order-0
+ * momentum by the relativistic Boris scheme and u1 by the first-order part of
+ * the same operations (continuum limit dp1/dt = q (E_p + v0 x B_p + v1 x
+ * B_nop)).  The current j^{n+1} = (q w/dV)[S v0] and (q w/dV)[(dS/dx . x1) v0 +
+ * S v1], deposited at x^{n+1} with v^{n+1}, enters the second E half-steps of
+ * its order and the next step's first ones (curl B = dE/dt + j).  S is the
+ * quadratic B-spline on each component's own staggered nodes.  A grid with
+ * particles always takes the general (multi-pass) kernels: AXP_KERNEL_AUTO
+ * chooses them, and forcing a single-pass kernel makes axp_step return
+ * AXP_E_STATE.  Checkpoint images (axp_save_state) hold the fields only.
+ *
+ * axp_particles_bytes: device workspace for `count` particles on this grid.
+ * axp_attach_particles: attach `count` particles of charge q and mass m > 0,
+ *   kept in the caller's device workspace (256-byte aligned, at least
+ *   axp_particles_bytes; owned by the caller, used until detach or destroy).
+ *   They start at rest at the origin with weight 0 until written.
+ *   AXP_E_INVAL: bad arguments, an FP32 grid or a non-periodic active axis;
+ *   AXP_E_NOMEM: workspace too small; AXP_E_STATE: particles already attached
+ *   or the grid is in a group.
+ * axp_write_particles / axp_read_particles: host arrays of 13 rows of `count`
+ *   doubles: w, x0 (x, y, z), u0 (x, y, z), x1 (x, y, z), u1 (x, y, z), positions
+ *   and momenta at the grid's present time step.  Writing deposits j^n (so the
+ *   next step's first E half-steps see it); non-finite values give
+ *   AXP_E_NONFINITE.  Both synchronise.
+ * axp_read_particle_current: j^n of order `order` (0 or 1) as 3 rows of cells
+ *   doubles (x, y, z components on the E_x, E_y, E_z locations).
+ * axp_detach_particles: the grid continues without particles. */
+axp_status axp_particles_bytes(const axp_grid *grid, int64_t count, size_t *bytes);
+axp_status axp_attach_particles(axp_grid *grid, int64_t count, double q, double m, void *dev_workspace,
+                                size_t bytes);
+axp_status axp_write_particles(axp_grid *grid, const double *host_src, size_t bytes);
+axp_status axp_read_particles(axp_grid *grid, double *host_dst, size_t bytes);
+axp_status axp_read_particle_current(axp_grid *grid, int32_t order, double *host_dst, size_t bytes);
+axp_status axp_detach_particles(axp_grid *grid);
+
 /* Outflow ghost planes of axis `axis`, side `side` (level 0 = phi^{n+1/2},
  * 1 = phi^{n-1/2}) as doubles; plane index: axis 0 -> j + n1 k,
  * axis 1 -> i + n0 k, axis 2 -> i + n0 j.  AXP_E_INVAL unless that face is

@@ -111,6 +111,12 @@ def lib():
             "axp_pack_rows": ([_P, C.c_int64, C.c_int64, _P, C.c_size_t], C.c_int),
             "axp_unpack_rows": ([_P, C.c_int64, C.c_int64, _P, C.c_size_t], C.c_int),
             "axp_compute_diagnostics_rows": ([_P, C.c_int64, C.c_int64, C.POINTER(axp_diag)], C.c_int),
+            "axp_particles_bytes": ([_P, C.c_int64, C.POINTER(C.c_size_t)], C.c_int),
+            "axp_attach_particles": ([_P, C.c_int64, C.c_double, C.c_double, _P, C.c_size_t], C.c_int),
+            "axp_write_particles": ([_P, C.POINTER(C.c_double), C.c_size_t], C.c_int),
+            "axp_read_particles": ([_P, C.POINTER(C.c_double), C.c_size_t], C.c_int),
+            "axp_read_particle_current": ([_P, C.c_int32, C.POINTER(C.c_double), C.c_size_t], C.c_int),
+            "axp_detach_particles": ([_P], C.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -307,6 +313,38 @@ def axp_test_block1d_absent(h, block):
 
 # ---- descriptors from the workload specs ----
 
+def axp_particles_bytes(h, count):
+    n = C.c_size_t()
+    _check(lib().axp_particles_bytes(h, int(count), C.byref(n)), "axp_particles_bytes")
+    return n.value
+
+
+def axp_attach_particles(h, count, q, m, dev_ptr, nbytes):
+    _check(lib().axp_attach_particles(h, int(count), float(q), float(m), dev_ptr, nbytes), "axp_attach_particles")
+
+
+def axp_write_particles(h, rows: np.ndarray):
+    a = np.ascontiguousarray(rows, dtype=np.float64)
+    _check(lib().axp_write_particles(h, a.ctypes.data_as(C.POINTER(C.c_double)), a.nbytes), "axp_write_particles")
+
+
+def axp_read_particles(h, count):
+    out = np.empty((13, int(count)), dtype=np.float64)
+    _check(lib().axp_read_particles(h, out.ctypes.data_as(C.POINTER(C.c_double)), out.nbytes), "axp_read_particles")
+    return out
+
+
+def axp_read_particle_current(h, order, ncells):
+    out = np.empty((3, int(ncells)), dtype=np.float64)
+    _check(lib().axp_read_particle_current(h, int(order), out.ctypes.data_as(C.POINTER(C.c_double)), out.nbytes),
+           "axp_read_particle_current")
+    return out
+
+
+def axp_detach_particles(h):
+    _check(lib().axp_detach_particles(h), "axp_detach_particles")
+
+
 def desc_of(grid: GridSpec, diag_every=0, diag_capacity=0) -> axp_grid_desc:
     d = axp_grid_desc()
     for a in range(3):
@@ -444,3 +482,39 @@ class Grid:
 
     def load_state(self, buf: np.ndarray):
         axp_load_state(self.h, buf.ctypes.data, buf.nbytes)
+
+    # -- macroparticles (perturbed-particle current) --
+    def attach_particles(self, q, m, w, x0, u0, x1=None, u1=None):
+        """One species: weights w (count,), positions x0, x1 and momenta u0, u1
+        (3, count) at the present time step; the workspace is a torch tensor."""
+        import torch
+
+        w = np.asarray(w, dtype=np.float64)
+        n = w.shape[0]
+        z = np.zeros((3, n))
+        rows = np.concatenate([w[None], np.asarray(x0, dtype=np.float64).reshape(3, n),
+                               np.asarray(u0, dtype=np.float64).reshape(3, n),
+                               z if x1 is None else np.asarray(x1, dtype=np.float64).reshape(3, n),
+                               z if u1 is None else np.asarray(u1, dtype=np.float64).reshape(3, n)])
+        nbytes = axp_particles_bytes(self.h, n)
+        with torch.cuda.device(self.device):
+            self.particle_ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        axp_attach_particles(self.h, n, q, m, self.particle_ws.data_ptr(), nbytes)
+        self.particle_count = n
+        axp_write_particles(self.h, rows)
+
+    def write_particles(self, rows: np.ndarray):
+        axp_write_particles(self.h, rows)
+
+    def read_particles(self) -> dict:
+        """Positions and momenta at the present time step: w, x0, u0, x1, u1."""
+        r = axp_read_particles(self.h, self.particle_count)
+        return {"w": r[0], "x0": r[1:4], "u0": r[4:7], "x1": r[7:10], "u1": r[10:13]}
+
+    def particle_current(self, order):
+        """j^n of order 0 or 1, shape (3, nz, ny, nx)."""
+        return axp_read_particle_current(self.h, order, self.cells).reshape((3,) + self.shape)
+
+    def detach_particles(self):
+        axp_detach_particles(self.h)
+        self.particle_ws = None

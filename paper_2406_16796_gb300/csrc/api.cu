@@ -311,6 +311,9 @@ View<T> make_view_eset(axp_grid *g, int eset)
     v.g = (T)d.g;
     v.m2 = (T)(d.m * d.m);
     set_reciprocals(v);
+    if (g->parts && sizeof(T) == sizeof(double))
+        for (int o = 0; o < 2; o++)
+            for (int a = 0; a < 3; a++) v.jp[o][a] = (T *)g->parts->j[o][a];
     return v;
 }
 
@@ -496,6 +499,7 @@ axp_status axp_destroy_grid(axp_grid *grid)
     if (!grid) return AXP_E_INVAL;
     if (grid->group) return AXP_E_STATE;
     release_step_graphs(grid, true);
+    delete grid->parts;
     delete grid;
     return AXP_OK;
 }
@@ -863,6 +867,122 @@ static axp_status ghost_io(axp_grid *g, int32_t axis, int32_t side, int32_t leve
     for (int64_t c = 0; c < P; c++) tmp[c] = (float)src[c];
     g->J_valid = false;
     return cuda_status(cudaMemcpy(dev, tmp.data(), P * 4, cudaMemcpyHostToDevice));
+}
+
+// ---- macroparticles (Sec. 2.2) ----
+
+axp_status axp_particles_bytes(const axp_grid *g, int64_t count, size_t *bytes)
+{
+    if (!g || !bytes || count < 0) return AXP_E_INVAL;
+    *bytes = particles_bytes(g->desc, count);
+    return AXP_OK;
+}
+
+axp_status axp_attach_particles(axp_grid *g, int64_t count, double q, double m, void *ws, size_t bytes)
+{
+    axp::TraceRange trace_("axp_attach_particles");
+    if (!g || !ws || count < 0 || !std::isfinite(q) || !std::isfinite(m) || !(m > 0.0)) return AXP_E_INVAL;
+    if (g->group || g->parts) return AXP_E_STATE;
+    if (is_fp32(g) || (uintptr_t)ws % kAlign) return AXP_E_INVAL;
+    for (int a = 0; a < 3; a++)
+        if (g->desc.n[a] > 1 && (g->desc.em_bc[a][0] != AXP_BC_PERIODIC || g->desc.em_bc[a][1] != AXP_BC_PERIODIC))
+            return AXP_E_INVAL;
+    const size_t need = particles_bytes(g->desc, count);
+    if (bytes < need) return AXP_E_NOMEM;
+    cudaError_t e = ensure_integer(g);
+    if (e != cudaSuccess) return cuda_status(e);
+    Particles *P = new (std::nothrow) Particles();
+    if (!P) return AXP_E_NOMEM;
+    P->count = count;
+    P->q = q;
+    P->m = m;
+    P->ws = (char *)ws;
+    P->bytes = bytes;
+    particles_layout(g->desc, P);
+    e = cudaMemsetAsync(ws, 0, need, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) {
+        delete P;
+        return cuda_status(e);
+    }
+    g->parts = P;
+    g->active = (1u << kFields) - 1;  // the currents can drive every component
+    g->cfg_version++;
+    return AXP_OK;
+}
+
+axp_status axp_detach_particles(axp_grid *g)
+{
+    if (!g) return AXP_E_INVAL;
+    if (g->group) return AXP_E_STATE;
+    if (!g->parts) return AXP_OK;
+    const cudaError_t e = cudaStreamSynchronize(g->stream);
+    delete g->parts;
+    g->parts = nullptr;
+    g->cfg_version++;
+    return cuda_status(e);
+}
+
+// rows of the host image: w, x0 xyz, u0 xyz, x1 xyz, u1 xyz
+static double *particle_row(Particles *P, int r)
+{
+    if (r == 0) return P->w;
+    if (r < 4) return P->x0[r - 1];
+    if (r < 7) return P->u0[r - 4];
+    if (r < 10) return P->x1[r - 7];
+    return P->u1[r - 10];
+}
+
+axp_status axp_write_particles(axp_grid *g, const double *src, size_t bytes)
+{
+    axp::TraceRange trace_("axp_write_particles");
+    if (!g || !src) return AXP_E_INVAL;
+    if (g->group || !g->parts) return AXP_E_STATE;
+    Particles *P = g->parts;
+    if (bytes != (size_t)P->count * 13 * sizeof(double)) return AXP_E_INVAL;
+    for (int64_t i = 0; i < P->count * 13; i++)
+        if (!std::isfinite(src[i])) return AXP_E_NONFINITE;
+    cudaError_t e = ensure_integer(g);
+    for (int r = 0; r < 13 && e == cudaSuccess && P->count > 0; r++)
+        e = cudaMemcpyAsync(particle_row(P, r), src + (size_t)r * P->count, (size_t)P->count * sizeof(double),
+                            cudaMemcpyHostToDevice, g->stream);
+    if (e == cudaSuccess) e = particles_start(g);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    g->cfg_version++;
+    return cuda_status(e);
+}
+
+axp_status axp_read_particles(axp_grid *g, double *dst, size_t bytes)
+{
+    if (!g || !dst) return AXP_E_INVAL;
+    if (g->group || !g->parts) return AXP_E_STATE;
+    Particles *P = g->parts;
+    if (bytes != (size_t)P->count * 13 * sizeof(double)) return AXP_E_INVAL;
+    cudaError_t e = ensure_integer(g);
+    if (e == cudaSuccess) e = particles_now(g);
+    for (int r = 0; r < 13 && e == cudaSuccess && P->count > 0; r++) {
+        const double *from = particle_row(P, r);
+        if (r >= 1 && r < 4) from = P->scratch[r - 1];
+        if (r >= 7 && r < 10) from = P->scratch[3 + r - 7];
+        e = cudaMemcpyAsync(dst + (size_t)r * P->count, from, (size_t)P->count * sizeof(double), cudaMemcpyDeviceToHost,
+                            g->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    return cuda_status(e);
+}
+
+axp_status axp_read_particle_current(axp_grid *g, int32_t order, double *dst, size_t bytes)
+{
+    if (!g || !dst || order < 0 || order > 1) return AXP_E_INVAL;
+    if (!g->parts) return AXP_E_STATE;
+    const int64_t N = cells(g->desc);
+    if (bytes != (size_t)N * 3 * sizeof(double)) return AXP_E_INVAL;
+    cudaError_t e = cudaSuccess;
+    for (int a = 0; a < 3 && e == cudaSuccess; a++)
+        e = cudaMemcpyAsync(dst + (size_t)a * N, g->parts->j[order][a], (size_t)N * sizeof(double),
+                            cudaMemcpyDeviceToHost, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    return cuda_status(e);
 }
 
 axp_status axp_read_ghost(axp_grid *g, int32_t axis, int32_t side, int32_t level, double *dst, size_t bytes)

@@ -50,6 +50,23 @@ struct View {
     // vaxis lies in [vlo, vhi); Nv of them
     int vaxis;
     int64_t vlo, vhi, Nv;
+    // current density j^n of the attached macroparticles, order 0 and order 1, at
+    // the E locations (null without particles)
+    T *jp[2][3];
+};
+
+// Macroparticles of one species attached to a FP64 grid (perturbed-particle
+// current, Sec. 2.2).  All arrays sit in the caller's particle workspace.
+// Positions x0, x1 are at t_{n+1/2}, momenta u0, u1 (u = gamma v) at t_n, and
+// j[order] holds the current density j^n deposited by the last push.
+struct Particles {
+    int64_t count;
+    double q, m;
+    char *ws;
+    size_t bytes;
+    double *w, *x0[3], *u0[3], *x1[3], *u1[3];
+    double *j[2][3];
+    double *scratch[6];  // read-back of the positions at t_n (x0, x1)
 };
 
 // A named NVTX range over one entry point of the C ABI: a span on a profiler's
@@ -166,6 +183,9 @@ struct axp_grid {
     // half_prev_cfg), so E^n follows cell by cell from the two levels
     bool half_prev;
     int64_t half_prev_cfg;
+    // attached macroparticles (Sec. 2.2), or null; a grid with particles takes the
+    // general path
+    axp::Particles *parts;
 };
 
 namespace axp {
@@ -194,6 +214,14 @@ template <typename T>
 cudaError_t inject_axion(axp_grid *g, const axp_axion_desc &A);
 template <typename T>
 cudaError_t fused_step(axp_grid *g, int64_t nsteps, bool *handled);
+// macroparticles: workspace size and layout, the deposit of j^n with the move of
+// the positions to t_{n+1/2}, the push between the field half-steps (fields of the
+// view at t_{n+1/2}), and the positions at t_n into the read-back scratch
+size_t particles_bytes(const axp_grid_desc &d, int64_t count);
+void particles_layout(const axp_grid_desc &d, Particles *P);
+cudaError_t particles_start(axp_grid *g);
+cudaError_t particles_push(axp_grid *g, const View<double> &v);
+cudaError_t particles_now(axp_grid *g);
 // time-blocked 1D kernel (FP64, periodic): eligibility and steps on the integer-time state
 bool block1d_supported(const axp_grid *g);
 cudaError_t block1d_step(axp_grid *g, int64_t nsteps);

@@ -759,7 +759,7 @@ template <typename T>
 int32_t fused_path(axp_grid *g)
 {
     const int32_t k = g->kernel_choice;
-    if (k == AXP_KERNEL_GENERAL) return AXP_KERNEL_GENERAL;
+    if (k == AXP_KERNEL_GENERAL || g->parts) return AXP_KERNEL_GENERAL;
     const bool b1 = block1d_supported(g);
     if (k == AXP_KERNEL_BLOCK1D) return b1 ? AXP_KERNEL_BLOCK1D : AXP_KERNEL_GENERAL;
     if (k == AXP_KERNEL_AUTO && b1) return AXP_KERNEL_BLOCK1D;

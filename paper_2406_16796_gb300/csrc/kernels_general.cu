@@ -247,6 +247,7 @@ __device__ __forceinline__ void e_half_at(const View<T> &v, int orders, const Sh
         for (int a = 0; a < 3; a++) {
             T X = curl_b(v, B, a, i, j, k);
             if (i == s.plane && a > 0) X = X + s.w[a - 1][j + v.n[1] * k] * s.tau;
+            if (v.jp[0][a]) X = X - v.jp[0][a][c];  // macroparticle current j0 (Ampere's law)
             v.f[kE0 + a][c] = half_update(v.f[kE0 + a][c], X, sig, v.h);
         }
     }
@@ -255,6 +256,7 @@ __device__ __forceinline__ void e_half_at(const View<T> &v, int orders, const Sh
         for (int a = 0; a < 3; a++) {
             T X = curl_b(v, B, a, i, j, k);
             X = X - v.g * v.J[a][c];
+            if (v.jp[1][a]) X = X - v.jp[1][a][c];  // first-order particle current j1
             v.f[kE1 + a][c] = half_update(v.f[kE1 + a][c], X, sig, v.h);
         }
     }
@@ -511,6 +513,11 @@ cudaError_t general_step(axp_grid *g, int64_t nsteps)
                                                                            gnew.p[a][s]);
                 g->launches++;
             }
+        // macroparticles pushed by the fields of both orders at t_{n+1/2}; they
+        // deposit j^{n+1}, which the second E half-steps (and the next step's first) read
+        if constexpr (sizeof(T) == sizeof(double)) {
+            if (g->parts && (e = particles_push(g, v)) != cudaSuccess) return e;
+        }
         k_b_half<T><<<nb, kThreads, 0, g->stream>>>(v, sb);
         k_e_half<T><<<nb, kThreads, 0, g->stream>>>(v, 1, se1);
         g->launches += 2;

@@ -291,3 +291,89 @@ def random_state(grid: GridSpec, seed: int, scale0=1.0, scale1=1e-3, scale_phi=1
     out["phi_cur"] = rng.uniform(-scale_phi, scale_phi, size=shape)
     out["phi_old"] = out["phi_cur"] + rng.uniform(-scale_phi, scale_phi, size=shape) * 0.1
     return out
+
+
+# ---------------------------------------------------------------------------
+# Macroparticles for the perturbed-particle current (Sec. 2.2) and the weak
+# laser in a magnetised plasma (Sec. 3.4).
+# ---------------------------------------------------------------------------
+
+
+@dataclass
+class PlasmaSpec:
+    """One species of macroparticles: charge q, mass m, weights w (count,) and
+    positions/momenta (3, count) of both orders at t = 0 (u = gamma v)."""
+
+    q: float
+    m: float
+    w: np.ndarray
+    x0: np.ndarray
+    u0: np.ndarray
+    x1: np.ndarray
+    u1: np.ndarray
+
+    @property
+    def count(self) -> int:
+        return int(self.w.shape[0])
+
+
+def plasma_particles(grid: GridSpec, ppc: int, density: float, seed: int, q=-1.0, m=1.0, u0_spread=0.0,
+                     x1_spread=0.0, u1_spread=0.0) -> PlasmaSpec:
+    """ppc particles in every cell at seeded uniform positions inside the cell,
+    weights giving the number density `density`, Gaussian momenta of spread
+    u0_spread (order 0) and u1_spread, and displacements of spread x1_spread
+    (first order; zero for a plasma that only the fields perturb)."""
+    rng = np.random.default_rng(seed)
+    n = grid.cells * ppc
+    cell = np.repeat(np.arange(grid.cells, dtype=np.int64), ppc)
+    idx = (cell % grid.n[0], (cell // grid.n[0]) % grid.n[1], cell // (grid.n[0] * grid.n[1]))
+    x0 = np.zeros((3, n))
+    for a in range(3):
+        if grid.n[a] > 1:
+            x0[a] = grid.lo[a] + (idx[a] + rng.uniform(0.0, 1.0, n)) * grid.d[a]
+        else:
+            x0[a] = grid.lo[a] + 0.5 * grid.d[a]
+    dV = grid.d[0] * grid.d[1] * grid.d[2]
+    w = np.full(n, density * dV / ppc)
+    u0 = rng.normal(size=(3, n)) * u0_spread
+    x1 = rng.normal(size=(3, n)) * x1_spread
+    for a in range(3):
+        if grid.n[a] == 1:
+            x1[a] = 0.0
+    u1 = rng.normal(size=(3, n)) * u1_spread
+    return PlasmaSpec(q, m, w, x0, u0, x1, u1)
+
+
+def magnetised_plasma_2d(nx=12000, ny=100, ppc=4, n_over_nc=3e-3, amplitude_over_Bc=1e-20, cfl=0.95,
+                         seed=SEED_BASE + 5):
+    """Weak laser in a transversely magnetised plasma (Sec. 3.4): a box of
+    40 x 100 wavelengths on 12000 x 100 cells (finer along the propagation
+    axis x), electrons of density n0 = 3e-3 n_c at rest, B_ext = m w_p/|q| along
+    z, and a laser pulse of B amplitude 1e-20 B_ext in the first-order fields
+    (E1_y, B1_z, propagating along +x).  Both axes periodic (the particles'
+    boundary).  n_c = m w0^2/q^2 in these units (eps0 = 1, w0 = 2 pi).
+
+    Returns (grid, plasma, fields): fields maps E1y and B1z to their arrays."""
+    Lx, Ly = 40.0, 100.0
+    dx, dy = Lx / nx, Ly / ny
+    dt = cfl / math.sqrt(1.0 / (dx * dx) + 1.0 / (dy * dy))
+    n0 = n_over_nc * K0 * K0
+    wp = math.sqrt(n0)
+    Bc = wp
+    grid = GridSpec(n=(nx, ny, 1), d=(dx, dy, dy), dt=dt, lo=(-Lx / 2.0, -Ly / 2.0, 0.0), m=0.0, g=0.0,
+                    B_ext=(0.0, 0.0, Bc))
+    plasma = plasma_particles(grid, ppc, n0, seed)
+    A = amplitude_over_Bc * Bc
+    xc, L, waist = -10.0, 3.0, 20.0
+    # E_y at (x_i + dx/2, y_j + dy), B_z at (x_i + dx, y_j + dy) relative to the low faces
+    xs_e = grid.lo[0] + (np.arange(nx) + 0.5) * dx
+    xs_b = grid.lo[0] + (np.arange(nx) + 1.0) * dx
+    ys = grid.lo[1] + (np.arange(ny) + 1.0) * dy
+
+    def pulse(x):
+        return A * np.exp(-((x - xc) / L) ** 2) * np.cos(K0 * (x - xc))
+
+    trans = np.exp(-(ys / waist) ** 2)
+    fields = {"E1y": (trans[:, None] * pulse(xs_e)[None, :])[None],
+              "B1z": (trans[:, None] * pulse(xs_b)[None, :])[None]}
+    return grid, plasma, fields
