@@ -35,7 +35,7 @@ UNITS = {
     "kernels_fused_f32.cu": [],
     "batch1d.cu": [],
     "group2d.cu": [],
-    "particles.cu": ["--fmad=false"],
+    "particles.cu": [],
 }
 
 
