@@ -486,6 +486,10 @@ def group_measurement(members, steps, hbm_peak, hbm_src):
 # one push of a macroparticle reads its weight, positions and momenta of both
 # orders (13 doubles) and writes the positions and momenta back (12 doubles)
 BYTES_PER_PARTICLE = (13 + 12) * 8
+# k_particles_push on the magnetised plasma (4.8M particles, 2D), one-pass ncu
+# capture of one launch: FP64-pipe warp instructions and DRAM bytes
+PUSH_FP64_WARP_INST_PER_PARTICLE = 110118800 / 4800000
+PUSH_TRAFFIC_PER_PARTICLE = (843438848 + 531257856) / 4800000
 
 
 def plasma_measurement(steps, warmup, hbm_peak, hbm_src, world):
@@ -502,18 +506,31 @@ def plasma_measurement(steps, warmup, hbm_peak, hbm_src, world):
     for k, v in fields.items():
         g.write(k, v)
     g.attach_particles(plasma.q, plasma.m, plasma.w, plasma.x0, plasma.u0, plasma.x1, plasma.u1)
+    cs = ClockSampler(torch.cuda.current_device())
+    cs.start()
     el, launches = timed_run(g, steps, warmup, g.stream)
+    clk = cs.stop().get("sm_mhz")
     per = el / steps
     ach = BYTES_PER_PARTICLE * plasma.count / per / 1e9
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz = clk if clk else 2070.0
+    fp64_peak = 2.0 * sms * mhz * 1e6 / 1e9  # Gop/s: 1/16 warp instruction per cycle per SM
+    fp64_ach = PUSH_FP64_WARP_INST_PER_PARTICLE * 32 * plasma.count / per / 1e9
     out = {"workload": "magnetised_plasma_2d_%dx%d_ppc4" % (grid.n[0], grid.n[1]), "cells": grid.cells,
            "particles": plasma.count, "precision": "fp64", "steps": steps, "ms_per_step": per * 1e3,
            "value": plasma.count * steps * world / el, "unit": "particle-steps/s",
            "cell_updates_per_s": grid.cells * steps * world / el, "gpu_launches": launches,
            "kernel": "k_particles_push and the general field kernels",
-           "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
-                        "peak_source": hbm_src, "algorithmic_bytes_per_particle": BYTES_PER_PARTICLE,
-                        "what": "the particle arrays only, over the whole step (the field passes, gathers and "
-                                "the current deposit come on top)", "traffic": None}}
+           "roofline": {"bound": "alu", "achieved": fp64_ach, "peak": fp64_peak, "unit": "Gop/s (FP64 pipe)",
+                        "frac": fp64_ach / fp64_peak, "kernel": "k_particles_push",
+                        "executed_fp64_ops_per_particle": PUSH_FP64_WARP_INST_PER_PARTICLE * 32,
+                        "what": "the push kernel's executed FP64 operations (ncu count per particle) over the whole "
+                                "step's time, so a lower bound of the kernel's own fraction",
+                        "peak_source": "1/16 warp instruction per cycle per SM x %d SMs x %.0f MHz sampled"
+                                       % (sms, mhz),
+                        "traffic": PUSH_TRAFFIC_PER_PARTICLE * plasma.count,
+                        "hbm": {"achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+                                "peak_source": hbm_src, "algorithmic_bytes_per_particle": BYTES_PER_PARTICLE}}}
     g.close()
     torch.cuda.synchronize()
     return out
