@@ -68,3 +68,34 @@ def test_serving_stream_mix_and_arrivals():
     assert all(1024 <= x.n[0] <= 65536 and x.n[1:] == (1, 1) for x in one)
     gaps = np.diff([0.0] + [x.arrival for x in r])
     assert np.all(gaps > 0) and abs(np.mean(gaps) - 1 / 100.0) < 0.05 / 100.0  # Poisson at 100 per second
+
+
+def test_magnetised_plasma_has_the_papers_parameters():
+    """Sec. 3.4: a 40 x 100 wavelength box on 12000 x 100 cells, n0 = 3e-3 n_c,
+    B_ext = m w_p/|q| along z, laser B amplitude 1e-20 B_ext in the first-order
+    fields; 4 particles per cell inside their own cells; seeded."""
+    grid, plasma, fields = W.magnetised_plasma_2d()
+    assert grid.n == (12000, 100, 1)
+    assert math.isclose(grid.n[0] * grid.d[0], 40.0, rel_tol=1e-14) and math.isclose(grid.n[1] * grid.d[1], 100.0)
+    inv2 = 1.0 / grid.d[0] ** 2 + 1.0 / grid.d[1] ** 2
+    assert grid.dt * math.sqrt(inv2) <= 0.95 + 1e-12
+    nc = plasma.m * W.K0 ** 2 / plasma.q ** 2
+    dV = grid.d[0] * grid.d[1] * grid.d[2]
+    density = plasma.w.sum() / (grid.cells * dV)
+    assert math.isclose(density / nc, 3e-3, rel_tol=1e-12)
+    wp = math.sqrt(density * plasma.q ** 2 / plasma.m)
+    assert grid.B_ext[:2] == (0.0, 0.0) and math.isclose(grid.B_ext[2], plasma.m * wp / abs(plasma.q), rel_tol=1e-12)
+    assert plasma.q == -1.0 and plasma.count == 4 * grid.cells
+    assert np.all(plasma.u0 == 0) and np.all(plasma.u1 == 0) and np.all(plasma.x1 == 0)
+    # every particle lies inside the cell it was drawn for
+    cell = np.repeat(np.arange(grid.cells), 4)
+    ix = np.floor((plasma.x0[0] - grid.lo[0]) / grid.d[0]).astype(np.int64)
+    iy = np.floor((plasma.x0[1] - grid.lo[1]) / grid.d[1]).astype(np.int64)
+    assert np.array_equal(ix, cell % grid.n[0]) and np.array_equal(iy, cell // grid.n[0])
+    # the laser is first order, at 1e-20 of the background field
+    Bz = fields["B1z"]
+    assert set(fields) == {"E1y", "B1z"}
+    assert 0.9e-20 < np.max(np.abs(Bz)) / grid.B_ext[2] <= 1e-20
+    # seeded
+    _, again, _ = W.magnetised_plasma_2d()
+    assert np.array_equal(again.x0, plasma.x0)
