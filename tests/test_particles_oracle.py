@@ -356,3 +356,67 @@ def test_coupled_run_first_order_is_the_derivative_of_order_zero():
     assert np.max(np.abs(fdj - st["j1"])) < 2e-6 * (1 + np.max(np.abs(st["j1"])))
     # the run is not trivial: first-order fields and currents grew from the particles
     assert np.max(np.abs(st["j1"])) > 1e-3 and np.max(np.abs(st["u1"] - U1)) > 1e-3
+
+
+def test_magnetised_plasma_x_and_o_mode_dispersion():
+    """Sec. 3.4's set-up in miniature: the first-order fields and particles of a
+    cold electron plasma at rest in B along z (k along x) carry the cold-plasma
+    modes.  The exact one-step map of a periodic 64-cell box (fields and particle
+    momenta, built column by column from oracle steps) is diagonalised; at each
+    of the box's lowest wave numbers the field-carrying frequencies are the
+    O mode w^2 = w_p^2 + k^2 (E along B) and the two X-mode branches,
+    k^2 = w^2 - w_p^2 (w^2 - w_p^2)/(w^2 - w_UH^2), w_UH^2 = w_p^2 + w_c^2
+    (E across B).  k enters through its Yee form (2/dx) sin(k dx/2); what
+    remains is the time discretisation's O((w dt)^2) (w dt <= 0.12 here) and
+    the spline's O((k dx)^2) filtering of the plasma response, so the bound
+    widens with k."""
+    n, d, ppc = 64, 0.02, 2
+    wp, wc = 5.0, 4.0
+    dt = 0.5 * d
+    grid = grid1d(n=n, d=d, dt=dt, B_ext=(0.0, 0.0, wc))
+    npart = n * ppc
+    X = np.zeros((3, npart))
+    X[0] = (np.arange(npart) + 0.5) * d / ppc
+    w = np.full(npart, wp ** 2 * d ** 3 / ppc)  # density w_p^2 (q = -1, m = 1)
+    names = ["E1x", "E1y", "E1z", "B1x", "B1y", "B1z"]
+    D = 6 * n + 3 * npart
+    M = np.zeros((D, D))
+    for i in range(D):
+        vec = np.zeros(D)
+        vec[i] = 1.0
+        og = O.OracleGrid(grid)
+        for c, k in enumerate(names):
+            og.f[k][0, 0, :] = vec[c * n:(c + 1) * n]
+        og.attach_particles(-1.0, 1.0, w, X, np.zeros((3, npart)), None, vec[6 * n:].reshape(3, npart))
+        og.step(1)
+        M[:, i] = np.concatenate([og.f[k][0, 0, :] for k in names] + [og.particles_now()["u1"].ravel()])
+    ev, V = np.linalg.eig(M)
+    assert np.max(np.abs(np.abs(ev) - 1.0)) < 1e-12  # no growth, no damping
+    found = {}
+    for j in range(D):
+        om = abs(np.angle(ev[j])) / dt
+        v = V[:, j]
+        fld = v[:6 * n].reshape(6, n)
+        if om < 1e-6 or np.linalg.norm(fld) < 1e-2 * np.linalg.norm(v):
+            continue
+        F = np.abs(np.fft.fft(fld, axis=1)) ** 2
+        Fm = F.sum(axis=0)
+        folded = Fm[: n // 2 + 1] + np.r_[Fm[0], Fm[:0:-1]][: n // 2 + 1]
+        m = int(np.argmax(folded))
+        found.setdefault(m, []).append((om, names[int(F[:, m].argmax())]))
+    L = n * d
+    for m, tol in ((0, 3e-4), (1, 1e-3), (2, 4e-3)):
+        ke = 2.0 / d * math.sin(math.pi * m / L * d)
+        U = wp ** 2 + wc ** 2
+        b, c = U + wp ** 2 + ke ** 2, wp ** 4 + ke ** 2 * U
+        x_lo, x_hi = math.sqrt((b - math.sqrt(b * b - 4 * c)) / 2), math.sqrt((b + math.sqrt(b * b - 4 * c)) / 2)
+        o_mode = math.sqrt(wp ** 2 + ke ** 2)
+        got = found[m]
+        for target, across in ((x_lo, True), (o_mode, False), (x_hi, True)):
+            best = min(got, key=lambda t: abs(t[0] - target))
+            assert abs(best[0] - target) <= tol * target, (m, target, best)
+            # the O mode's field lies along B, the X modes' across it
+            assert (best[1] != "E1z") == across, (m, target, best)
+        # nothing else carries fields at this wave number
+        for wv, _ in got:
+            assert min(abs(wv - t) for t in (x_lo, o_mode, x_hi)) <= tol * wv, (m, wv)
