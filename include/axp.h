@@ -360,7 +360,8 @@ axp_status axp_load_state(axp_grid *grid, const void *host_src, size_t bytes);
  * representation (integer time, or the staggered state of the single-pass
  * kernels) must be the same on both sides: slabs that exchange rows take the
  * same kernel path and the same steps.  AXP_E_INVAL for rows outside the
- * grid.
+ * grid; AXP_E_STATE for a grid with macroparticles (they do not move between
+ * slabs).
  *
  * axp_compute_diagnostics_rows: the record of axp_compute_diagnostics
  * restricted to the cells whose row lies in [row0, row1) (and in the physical

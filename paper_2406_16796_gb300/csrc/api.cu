@@ -1217,11 +1217,13 @@ static axp_status rows_copy(axp_grid *g, int64_t row0, int64_t nrows, char *dev,
 
 axp_status axp_pack_rows(axp_grid *g, int64_t row0, int64_t nrows, void *dev_dst, size_t bytes)
 {
+    if (g && g->parts) return AXP_E_STATE;  // particles do not move between slabs
     return rows_copy(g, row0, nrows, (char *)dev_dst, bytes, true);
 }
 
 axp_status axp_unpack_rows(axp_grid *g, int64_t row0, int64_t nrows, const void *dev_src, size_t bytes)
 {
+    if (g && g->parts) return AXP_E_STATE;
     return rows_copy(g, row0, nrows, (char *)const_cast<void *>(dev_src), bytes, false);
 }
 
