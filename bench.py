@@ -492,7 +492,28 @@ PUSH_FP64_WARP_INST_PER_PARTICLE = 110118800 / 4800000
 PUSH_TRAFFIC_PER_PARTICLE = (843438848 + 531257856) / 4800000
 
 
-def plasma_measurement(steps, warmup, hbm_peak, hbm_src, world):
+def plasma_oracle_rate(nx=1200, steps=2):
+    """The CPU oracle on a sample of the magnetised plasma: the same box and
+    particle density on nx x 100 cells (4 particles per cell), `steps` coupled
+    steps; particle-steps/s.  The oracle's field passes use OpenMP, its particle
+    loop one thread."""
+    import oracle
+
+    from paper_2406_16796_gb300 import workloads as W
+
+    grid, plasma, fields = W.magnetised_plasma_2d(nx=nx)
+    og = oracle.OracleGrid(grid)
+    og.load(fields)
+    og.attach_particles(plasma.q, plasma.m, plasma.w, plasma.x0, plasma.u0, plasma.x1, plasma.u1)
+    t0 = time.perf_counter()
+    og.step(steps)
+    el = time.perf_counter() - t0
+    return {"value": plasma.count * steps / el, "unit": "particle-steps/s", "cores": omp_threads(), "kind": "oracle",
+            "sample": "%d x %d cells, %d particles, %d steps (the particle loop runs on one thread)"
+                      % (grid.n[0], grid.n[1], plasma.count, steps)}
+
+
+def plasma_measurement(steps, warmup, hbm_peak, hbm_src, world, cpu=False):
     """Weak laser in a magnetised plasma (perturbed-particle current): 12000 x
     100 cells, 4 electrons per cell (4.8M), the laser in the first-order fields;
     FP64, one grid per GPU.  Each step is the general field kernels plus one
@@ -533,6 +554,8 @@ def plasma_measurement(steps, warmup, hbm_peak, hbm_src, world):
                                 "peak_source": hbm_src, "algorithmic_bytes_per_particle": BYTES_PER_PARTICLE}}}
     g.close()
     torch.cuda.synchronize()
+    if cpu:
+        out["cpu_baseline"] = plasma_oracle_rate()
     return out
 
 
@@ -836,7 +859,8 @@ def gpu_arm(args):
         srv = serve_measurement(args.serve_requests, rank, world, open_count=args.serve_open_requests)
     plasma = None
     if not args.no_plasma:
-        plasma = plasma_measurement(20, 3, hbm_peak, hbm_src, world)
+        plasma = plasma_measurement(20, 3, hbm_peak, hbm_src, world,
+                                    cpu=(rank == 0 and world == 1 and not args.no_cpu_baseline))
     grp = None
     if not args.no_group:
         grp = group_measurement(args.group_members, 50, hbm_peak, hbm_src)
