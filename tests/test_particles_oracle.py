@@ -420,3 +420,23 @@ def test_magnetised_plasma_x_and_o_mode_dispersion():
         # nothing else carries fields at this wave number
         for wv, _ in got:
             assert min(abs(wv - t) for t in (x_lo, o_mode, x_hi)) <= tol * wv, (m, wv)
+
+
+def test_boris_e_cross_b_drift():
+    """Crossed uniform fields (E along y, B along z, |E| << |B|): a particle
+    starting at rest gyrates about a guide centre drifting at E x B / B^2; over
+    whole gyration periods its mean velocity is the drift, to the scheme's
+    O((w_c dt)^2) and the relativistic O((E/B)^2)."""
+    q, m, dt, B, E = -1.0, 1.0, 0.05, 2.0, 0.01
+    h_rot = 2.0 * math.atan(abs(q) * B * dt / (2.0 * m))  # Boris turn per step
+    steps = int(round(200 * 2.0 * math.pi / h_rot))  # about 200 gyrations
+    u = np.zeros(3)
+    z = np.zeros(3)
+    vsum = np.zeros(3)
+    for _ in range(steps):
+        u, _ = O.kick(q / m, dt, u, z, np.array([0.0, E, 0.0]), np.array([0.0, 0.0, B]), z, z)
+        vsum += u / math.sqrt(1.0 + u @ u)
+    v = vsum / steps
+    drift = E / B  # (E x B)_x / B^2 for E = E y-hat, B = B z-hat
+    assert abs(v[0] - drift) < 5e-3 * drift
+    assert abs(v[1]) < 5e-3 * drift and v[2] == 0.0
