@@ -498,8 +498,10 @@ class Grid:
                                z if u1 is None else np.asarray(u1, dtype=np.float64).reshape(3, n)])
         nbytes = axp_particles_bytes(self.h, n)
         with torch.cuda.device(self.device):
-            self.particle_ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
-        axp_attach_particles(self.h, n, q, m, self.particle_ws.data_ptr(), nbytes)
+            ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        # the workspace of particles already attached stays referenced when this is refused
+        axp_attach_particles(self.h, n, q, m, ws.data_ptr(), nbytes)
+        self.particle_ws = ws
         self.particle_count = n
         axp_write_particles(self.h, rows)
 
