@@ -74,15 +74,23 @@ def test_magnetised_plasma_has_the_papers_parameters():
     """Sec. 3.4: a 40 x 100 wavelength box on 12000 x 100 cells, n0 = 3e-3 n_c,
     B_ext = m w_p/|q| along z, laser B amplitude 1e-20 B_ext in the first-order
     fields; 4 particles per cell inside their own cells; seeded."""
+    import json
+    import os
+
+    golden = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_numbers.json")))
+    ref = golden["magnetised_plasma"]
     grid, plasma, fields = W.magnetised_plasma_2d()
-    assert grid.n == (12000, 100, 1)
-    assert math.isclose(grid.n[0] * grid.d[0], 40.0, rel_tol=1e-14) and math.isclose(grid.n[1] * grid.d[1], 100.0)
+    assert grid.n[:2] == tuple(ref["cells"]) and grid.n[2] == 1
+    bx, by = ref["box_lambda"]["x"], ref["box_lambda"]["y"]
+    assert math.isclose(grid.lo[0], bx[0]) and math.isclose(grid.lo[1], by[0])
+    assert math.isclose(grid.n[0] * grid.d[0], bx[1] - bx[0], rel_tol=1e-14)
+    assert math.isclose(grid.n[1] * grid.d[1], by[1] - by[0], rel_tol=1e-14)
     inv2 = 1.0 / grid.d[0] ** 2 + 1.0 / grid.d[1] ** 2
     assert grid.dt * math.sqrt(inv2) <= 0.95 + 1e-12
     nc = plasma.m * W.K0 ** 2 / plasma.q ** 2
     dV = grid.d[0] * grid.d[1] * grid.d[2]
     density = plasma.w.sum() / (grid.cells * dV)
-    assert math.isclose(density / nc, 3e-3, rel_tol=1e-12)
+    assert math.isclose(density / nc, ref["n0_over_nc"], rel_tol=1e-12)
     wp = math.sqrt(density * plasma.q ** 2 / plasma.m)
     assert grid.B_ext[:2] == (0.0, 0.0) and math.isclose(grid.B_ext[2], plasma.m * wp / abs(plasma.q), rel_tol=1e-12)
     assert plasma.q == -1.0 and plasma.count == 4 * grid.cells
@@ -95,7 +103,8 @@ def test_magnetised_plasma_has_the_papers_parameters():
     # the laser is first order, at 1e-20 of the background field
     Bz = fields["B1z"]
     assert set(fields) == {"E1y", "B1z"}
-    assert 0.9e-20 < np.max(np.abs(Bz)) / grid.B_ext[2] <= 1e-20
+    ratio = ref["laser_B_over_B_ext"]
+    assert 0.9 * ratio < np.max(np.abs(Bz)) / grid.B_ext[2] <= ratio
     # seeded
     _, again, _ = W.magnetised_plasma_2d()
     assert np.array_equal(again.x0, plasma.x0)
